@@ -1,0 +1,353 @@
+"""Throughput of the static-autotuning hot path on GB300.
+
+One step = tune_eval over the whole workload: every point of every kernel's
+tuning space gets occupancy + cost, then each kernel's top-k is selected.
+Default workload: 100,000 synthetic kernels x 16,384-point dense spaces
+(threads 32..1024/32 x grid 2^0..2^15 x unroll 1..8 x carveout {0,25,50,100}%),
+top-10 per kernel, sm_103 architecture row.
+
+Prints one JSON line (rank 0). Under torchrun each rank evaluates its own
+100,000 kernels (weak scaling, no data-path collective); the timing is the
+max over ranks.
+
+--impl reference times the CPU oracle (the plain FP64 + FP32-mirror C
+implementation) on a bounded sample of the same workload, on the host cores.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import archs, gen  # noqa: E402
+
+METRIC = "tuning points evaluated/sec + top-k"
+WORKLOADS = {
+    # name: (n_kernels per rank, space, k, seed)
+    "dense": (100_000, "dense", 10, 2),
+    "dense128": (64, "dense128", 5, 1),
+}
+ISSUE_LANES_PER_SM_CLK = 4 * 32  # 4 schedulers x 32 lanes per SM and clock
+L2_FLUSH_BYTES = 256 << 20       # larger than the 126.5 MB L2
+
+
+def algorithmic_instructions(descs, axes):
+    """Thread-instructions the factored evaluation needs (the per-point minimum):
+    per point 1 FMUL (cost = X * ipar(B*, G)) + 1 FSETP (compare with the k-th best);
+    per (T, U, C) triple 5 (min for B*, IMUL for W*, hide lookup, FFMA + FMUL for X).
+    """
+    sizes = gen.space_sizes(descs)
+    m = np.asarray(descs["space_mask"], dtype=np.uint64)
+    n_g = np.zeros(len(m), np.int64)
+    for b in range(16):
+        n_g += ((m >> np.uint64(32 + b)) & np.uint64(1)).astype(np.int64)
+    triples = np.where(n_g > 0, sizes // np.maximum(n_g, 1), 0)
+    return int(2 * sizes.sum() + 5 * triples.sum())
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1701_08547_gb300", "csrc", "tune_eval.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"tune_eval_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("bench-traffic:"):
+                for kv in line.split(":", 1)[1].split():
+                    k, v = kv.split("=")
+                    vals[k] = v
+    if vals.get("source_sha256") != kernel_source_hash():
+        return None
+    return float(vals["bytes_per_launch"]) if "bytes_per_launch" in vals else None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1701_08547_gb300 as T
+    from paper_1701_08547_gb300 import build as B
+
+    rank, world, local = dist_env()
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    n, space, k, seed = WORKLOADS[args.workload]
+    n = args.kernels or n
+    a, ax = archs.arch("sm_103"), gen.axes()
+    descs = gen.descriptors(n, seed, space, first=rank * n)
+    points = int(gen.space_sizes(descs).sum())
+    algo_instr = algorithmic_instructions(descs, ax)
+
+    d_dev = T.descs_to_device(descs, dev)
+    ws = T.workspace(0, n, k, dev)
+    topi = torch.empty((n, k), dtype=torch.int32, device=dev)
+    topc = torch.empty((n, k), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        T.tune_eval(a, ax, d_dev, k, topk_idx=topi, topk_cost=topc, workspace_buf=ws, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    T.tune_check(ws)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the event pair)
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    T.tune_check(ws)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end through the public API with host buffers (pinned), copies timed.
+    host_d = torch.from_numpy(np.ascontiguousarray(descs).view(np.uint8).reshape(-1, 64)).pin_memory()
+    host_i = torch.empty((n, k), dtype=torch.int32).pin_memory()
+    host_c = torch.empty((n, k), dtype=torch.float32).pin_memory()
+    e_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    d_e2e = torch.empty_like(d_dev)
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        if i >= args.warmup:
+            e_start[i - args.warmup].record(stream)
+        d_e2e.copy_(host_d, non_blocking=True)
+        T.tune_eval(a, ax, d_e2e, k, topk_idx=topi, topk_cost=topc, workspace_buf=ws, stream=stream)
+        host_i.copy_(topi, non_blocking=True)
+        host_c.copy_(topc, non_blocking=True)
+        if i >= args.warmup:
+            e_end[i - args.warmup].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_start, e_end)) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+
+    peaks, peak_kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * ISSUE_LANES_PER_SM_CLK * peaks["sm_max_mhz"] * 1e6 / 1e12  # Tinstr/s
+    achieved = algo_instr / (ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC,
+        "value": world * points / (ms * 1e-3),
+        "unit": "points/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32+f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {n} kernels x {points // n} points, top-{k}, sm_103 row",
+                   "kernels_per_gpu": n, "points_per_gpu": points, "k": k,
+                   "l2": "flushed between timed steps (256 MB write outside the timed events)",
+                   "parallelism": f"replicas x{world} (kernel ranges)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
+                     "peak_source": f"{sms} SMs x 128 lanes x {peaks['sm_max_mhz']} MHz ({peak_kind})",
+                     "algorithmic_instr_per_point": algo_instr / points},
+        "e2e": {"value": world * points / (e2e_ms * 1e-3), "unit": "points/s",
+                "h2d_bytes_per_step": n * 64, "d2h_bytes_per_step": n * k * 8,
+                "ms_per_step": e2e_ms},
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample)
+    return line
+
+
+def cpu_baseline(workload, sample):
+    from oracle import oracle as O
+
+    n, space, k, seed = WORKLOADS[workload]
+    sample = min(sample, n)
+    descs = gen.descriptors(sample, seed, space)
+    a, ax = archs.arch("sm_103"), gen.axes()
+    threads = O.threads_available()
+    O.evaluate(a, ax, descs[:8], k, nthreads=threads)  # load + warm
+    t0 = time.perf_counter()
+    O.evaluate(a, ax, descs, k, nthreads=threads)
+    dt = time.perf_counter() - t0
+    pts = int(gen.space_sizes(descs).sum())
+    return {"value": pts / dt, "unit": "points/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {sample} kernels of the {workload} workload ({pts} points), "
+                      f"{dt:.2f} s wall on {threads} threads"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+
+    n, space, k, seed = WORKLOADS[args.workload]
+    a, ax = archs.arch("sm_103"), gen.axes()
+    sample = min(args.cpu_sample, n)
+    descs = gen.descriptors(sample, seed, space)
+    pts = int(gen.space_sizes(descs).sum())
+    threads = O.threads_available()
+    for _ in range(args.warmup):
+        O.evaluate(a, ax, descs[: max(1, sample // 8)], k, nthreads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.evaluate(a, ax, descs, k, nthreads=threads)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = pts / (ms * 1e-3)
+    sample_desc = f"first {sample} kernels of the {args.workload} workload ({pts} points) per step"
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "points/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int64+f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {n} kernels x {pts // sample} points, top-{k}, sm_103 row",
+                   "kernels_per_gpu": n, "k": k},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": threads, "kind": "oracle",
+                         "sample": sample_desc},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=list(WORKLOADS), default="dense")
+    p.add_argument("--cpu-sample", type=int, default=16000)
+    p.add_argument("--kernels", type=int, default=0, help="override the kernel count (small ncu cases)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    args = p.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * tune.h — C ABI of the GB300 static-autotuning library (libtune.so).
+ *
+ * The library evaluates, for every point of many kernels' tuning spaces
+ * (threads per block x grid size x unroll x shared-memory carveout), the
+ * occupancy calculation of Lim, Norris & Malony, "Autotuning GPU Kernels
+ * via Static and Predictive Analysis" (Section III-A, Eqs. 1-5) and its
+ * instruction-mix cost (Section III-B, Eq. 6, extended with launch-shape
+ * terms), then selects each kernel's k cheapest configurations.
+ *
+ * Conventions for every entry point:
+ *  - Pointers marked "device" are CUDA device pointers owned by the caller;
+ *    the library never frees or retains them after the call returns.
+ *    Pointers marked "host" are read during the call only.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and the call returns without synchronising. Errors found on
+ *    the host are returned at once; errors found by a kernel (malformed
+ *    descriptor contents) are written to the status word in `workspace`
+ *    and returned by tune_check().
+ *  - Return value: TUNE_OK (0) or a negative TUNE_E* code; a message for the
+ *    last error on the calling thread is available from tune_last_error().
+ *  - The library never allocates device memory in these calls: scratch
+ *    space is the caller's `workspace` of at least tune_workspace_bytes().
+ */
+#ifndef TUNE_H
+#define TUNE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* tune_stream_t; /* identical to cudaStream_t */
+
+enum {
+    TUNE_OK = 0,
+    TUNE_EINVAL = -1,   /* bad argument or malformed input record */
+    TUNE_ENOMEM = -2,   /* workspace too small */
+    TUNE_ECUDA = -3,    /* a CUDA runtime call failed */
+    TUNE_ETIMEOUT = -4, /* a bounded device-side wait gave up */
+    TUNE_ECOMPILE = -5, /* run-time compilation failed */
+    TUNE_EUNSUPPORTED = -6
+};
+
+enum { TUNE_NCLASS = 7 }; /* FP32, FP64, INT, GLDST, SLDST, BRANCH, SFU */
+
+/*
+ * Architecture row: the limits of Table "GPUs used in this experiment"
+ * (Section III-A) and the per-class throughputs of Table "Instruction
+ * throughput per number of cycles" (Section III-B), plus the allocation
+ * details the occupancy calculation needs on current GPUs. Host memory.
+ * Limits: warp_size = 32, max_warps_sm <= 64, max_blocks_sm <= 32,
+ * 1 <= n_smem_caps <= 16 with smem_caps ascending, ipc[c] > 0.
+ */
+typedef struct tune_arch {
+    int32_t cc;                  /* compute capability x 10 */
+    int32_t n_sm;                /* multiprocessors */
+    int32_t warp_size;           /* T_W */
+    int32_t max_threads_block;   /* T_B */
+    int32_t max_warps_sm;        /* W_mp */
+    int32_t max_blocks_sm;       /* B_mp */
+    int32_t regs_sm;             /* register file per SM */
+    int32_t regs_block_max;      /* registers per block, maximum */
+    int32_t regs_thread_max;     /* R_T */
+    int32_t reg_alloc_unit;      /* register allocation unit */
+    int32_t reg_alloc_mode;      /* 0: per warp, 1: per block */
+    int32_t warp_alloc_gran;     /* warps per register-allocation group */
+    int32_t smem_block_max;      /* S_B, bytes */
+    int32_t smem_reserved_block; /* bytes reserved per block by the runtime */
+    int32_t smem_alloc_unit;     /* shared-memory allocation unit, bytes */
+    int32_t n_smem_caps;         /* supported per-SM shared-memory capacities */
+    int32_t smem_caps[16];       /* bytes, ascending */
+    float ipc[TUNE_NCLASS];      /* instructions per cycle per SM, per class */
+    int32_t w_sat;               /* warps per SM that hide memory latency */
+    int32_t work_scale;          /* K: work items per instruction count */
+} tune_arch;
+
+/*
+ * Tuning axes: the values that descriptor space-mask bits select. Host
+ * memory. 1 <= n_t <= 32, 1 <= n_g <= 16, 1 <= n_u <= 8, 1 <= n_c <= 4;
+ * t in [1, 4096], g >= 1 with n_sm * g < 2^24, u in [1, 64], c in [0, 100].
+ */
+typedef struct tune_axes {
+    int32_t n_t, n_g, n_u, n_c;
+    int32_t t[32]; /* threads per block */
+    int32_t g[16]; /* grid size, blocks */
+    int32_t u[8];  /* unroll factor; registers/thread = r0 + 4 (u - 1) */
+    int32_t c[4];  /* preferred shared-memory carveout, percent of the largest capacity */
+} tune_axes;
+
+/*
+ * Kernel descriptor, 64 bytes, 16-byte aligned: the static facts the
+ * paper's front end extracts (Section III, "Static Analysis": registers and
+ * shared memory from ptxas, instruction counts from the binary).
+ * space_mask bits 0..31 select t[], 32..47 g[], 48..55 u[], 56..59 c[];
+ * bits 60..63 and bits beyond each axis length must be zero.
+ */
+typedef struct tune_kernel_desc {
+    float n[TUNE_NCLASS]; /* static instruction counts per class, >= 0 */
+    int32_t r0;           /* registers per thread at unroll 1 */
+    int32_t s0;           /* shared memory per block, bytes */
+    float d;              /* branch-divergence fraction, >= 0 */
+    uint64_t space_mask;
+    int32_t reserved[4];
+} tune_kernel_desc;
+
+/* tune_eval flags */
+#define TUNE_EMIT_POINTS 0x1u /* also write per-point B*, W*, cost (pt_* arrays) */
+
+/* Calls for tune_workspace_bytes(). */
+enum { TUNE_CALL_EVAL = 0, TUNE_CALL_TOPK = 1 };
+
+/*
+ * tune_eval — evaluate every point of every kernel's space and select each
+ * kernel's k best.
+ *
+ * For kernel i and each point (T, G, U, C) of its space, in canonical order
+ * (row-major over T, G, U, C restricted to the mask, C fastest):
+ *   R  = r0 + 4 (U - 1)
+ *   B* = min(G_W, G_R, G_S)  (Eqs. 1, 3, 4, 5), W* = B* ceil(T/32)  (Eq. 2);
+ *   invalid if B* = 0 or T > max_threads_block.
+ *   cost = (C_nm + C_m hide) lane / par  (Eq. 6 with c_x = 1 / IPC_x, plus
+ *   the library's launch-shape terms hide, lane, par), computed in FP32 in
+ *   a fixed operation order with compensated sums.
+ * Outputs (device):
+ *   topk_idx  int32[n_kernels * k]  canonical point indices, best first;
+ *                                   equal costs -> lower index first;
+ *                                   -1 past the last valid point
+ *   topk_cost float[n_kernels * k]  their costs (+inf for padding)
+ *   pt_blocks, pt_warps (int32), pt_cost (float): optional, only with
+ *   TUNE_EMIT_POINTS; indexed pt_offsets[i] + canonical index, where
+ *   pt_offsets (device int64[n_kernels + 1]) is the exclusive scan of space
+ *   sizes. Invalid points get B* = W* = 0, cost = +inf. Any of the three may
+ *   be NULL.
+ * Arguments: arch, axes (host); descs (device, 16-byte aligned,
+ * n_kernels records); 1 <= k <= 16; workspace (device) of at least
+ * tune_workspace_bytes(TUNE_CALL_EVAL, n_kernels, k) bytes.
+ * n_kernels = 0 is valid and enqueues only the status reset.
+ * A descriptor whose mask selects values outside the axes gets padding
+ * outputs and sets TUNE_EINVAL in the status word.
+ */
+int tune_eval(const tune_arch* arch, const tune_axes* axes, const tune_kernel_desc* descs,
+              int64_t n_kernels, int32_t k, uint32_t flags, int32_t* topk_idx, float* topk_cost,
+              int32_t* pt_blocks, int32_t* pt_warps, float* pt_cost, const int64_t* pt_offsets,
+              void* workspace, size_t ws_bytes, tune_stream_t stream);
+
+/*
+ * tune_topk — segmented top-k over an external score array (device).
+ * For segment s = [seg_offsets[s], seg_offsets[s+1]) of `scores`, the k
+ * smallest scores that are not +inf or NaN, equal scores -> lower index;
+ * topk_idx holds indices within the segment (-1 for padding), topk_score
+ * the scores (+inf for padding). seg_offsets: device int64[n_seg + 1],
+ * non-decreasing, segment lengths < 2^31. 1 <= k <= 16.
+ */
+int tune_topk(const float* scores, const int64_t* seg_offsets, int64_t n_seg, int32_t k,
+              int32_t* topk_idx, float* topk_score, void* workspace, size_t ws_bytes,
+              tune_stream_t stream);
+
+/* Bytes of device workspace the call needs (at least 256). */
+size_t tune_workspace_bytes(int call, int64_t n, int32_t k);
+
+/*
+ * tune_check — wait for `stream`, then return the status word the last
+ * call on this workspace left (TUNE_OK, TUNE_EINVAL, TUNE_ETIMEOUT).
+ */
+int tune_check(const void* workspace, tune_stream_t stream);
+
+/* Message for the last error returned on the calling thread ("" if none). */
+const char* tune_last_error(void);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int tune_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TUNE_H */

@@ -1,0 +1,101 @@
+"""GB300-native static autotuning: occupancy + instruction-mix cost over whole
+tuning spaces, and per-kernel top-k (Lim, Norris & Malony, Section III).
+
+The functions here mirror the C ABI of libtune.so (include/tune.h) with the
+same names; they marshal PyTorch tensors (device memory) and the current
+CUDA stream into the C calls and nothing else.
+"""
+
+import ctypes as C
+
+from . import native
+from .native import TUNE_EMIT_POINTS, TuneError  # noqa: F401
+
+__all__ = ["tune_eval", "tune_topk", "tune_workspace_bytes", "tune_check", "descs_to_device",
+           "TUNE_EMIT_POINTS", "TuneError"]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def tune_workspace_bytes(call, n, k):
+    return native.load().tune_workspace_bytes(int(call), int(n), int(k))
+
+
+def workspace(call, n, k, device="cuda"):
+    torch = _torch()
+    nbytes = tune_workspace_bytes(call, n, k)
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def descs_to_device(descs, device="cuda"):
+    """Copy a numpy descriptor array (64-byte records) to a uint8 device tensor [n, 64]."""
+    torch = _torch()
+    import numpy as np
+
+    raw = np.ascontiguousarray(descs).view(np.uint8).reshape(-1, 64)
+    return torch.from_numpy(raw).to(device)
+
+
+def tune_eval(arch, axes, descs, k, flags=0, topk_idx=None, topk_cost=None, pt_blocks=None,
+              pt_warps=None, pt_cost=None, pt_offsets=None, workspace_buf=None, stream=None):
+    """Evaluate every point of every kernel's space and select each kernel's top-k.
+
+    descs: contiguous device tensor holding n 64-byte descriptor records.
+    Returns (topk_idx int32 [n, k], topk_cost float32 [n, k]).
+    """
+    torch = _torch()
+    L = native.load()
+    assert descs.is_cuda and descs.is_contiguous() and descs.numel() * descs.element_size() % 64 == 0
+    n = descs.numel() * descs.element_size() // 64
+    dev = descs.device
+    if topk_idx is None:
+        topk_idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+    if topk_cost is None:
+        topk_cost = torch.empty((n, k), dtype=torch.float32, device=dev)
+    if workspace_buf is None:
+        workspace_buf = workspace(native.TUNE_CALL_EVAL, n, k, dev)
+    a = native.make_arch(arch)
+    x = native.make_axes(axes)
+    rc = L.tune_eval(C.byref(a), C.byref(x), _ptr(descs), n, int(k), int(flags), _ptr(topk_idx),
+                     _ptr(topk_cost), _ptr(pt_blocks), _ptr(pt_warps), _ptr(pt_cost),
+                     _ptr(pt_offsets), _ptr(workspace_buf), workspace_buf.numel(), _stream(stream))
+    native.check(rc)
+    return topk_idx, topk_cost
+
+
+def tune_topk(scores, seg_offsets, k, topk_idx=None, topk_score=None, workspace_buf=None,
+              stream=None):
+    """Segmented top-k (smallest scores, ties -> lower index) over device float32 scores."""
+    torch = _torch()
+    L = native.load()
+    n_seg = seg_offsets.numel() - 1
+    dev = scores.device
+    if topk_idx is None:
+        topk_idx = torch.empty((n_seg, k), dtype=torch.int32, device=dev)
+    if topk_score is None:
+        topk_score = torch.empty((n_seg, k), dtype=torch.float32, device=dev)
+    if workspace_buf is None:
+        workspace_buf = workspace(native.TUNE_CALL_TOPK, n_seg, k, dev)
+    rc = L.tune_topk(_ptr(scores), _ptr(seg_offsets), n_seg, int(k), _ptr(topk_idx),
+                     _ptr(topk_score), _ptr(workspace_buf), workspace_buf.numel(), _stream(stream))
+    native.check(rc)
+    return topk_idx, topk_score
+
+
+def tune_check(workspace_buf, stream=None):
+    """Wait for the stream and raise if a kernel flagged malformed input."""
+    return native.check(native.load().tune_check(_ptr(workspace_buf), _stream(stream)))

@@ -1,0 +1,74 @@
+// C-ABI glue: error reporting, workspace sizing, status check, version.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "tune_internal.h"
+
+namespace tune {
+
+static thread_local char g_msg[512];
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(TUNE_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+void clear_error() { g_msg[0] = 0; }
+
+int device_sm_count()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (cached[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
+}  // namespace tune
+
+extern "C" {
+
+const char* tune_last_error(void) { return tune::g_msg; }
+
+int tune_version(void) { return 100; }
+
+size_t tune_workspace_bytes(int call, int64_t n, int32_t k)
+{
+    (void)call;
+    (void)n;
+    (void)k;
+    return tune::kWorkspaceHeader;
+}
+
+int tune_check(const void* workspace, tune_stream_t stream)
+{
+    tune::clear_error();
+    if (!workspace) return tune::fail(TUNE_EINVAL, "tune_check: workspace is NULL");
+    int status = 0;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    TUNE_CUDA_TRY(cudaMemcpyAsync(&status, workspace, sizeof(int), cudaMemcpyDeviceToHost, s),
+                  "tune_check: cudaMemcpyAsync");
+    TUNE_CUDA_TRY(cudaStreamSynchronize(s), "tune_check: cudaStreamSynchronize");
+    if (status & tune::kStatusTimeout)
+        return tune::fail(TUNE_ETIMEOUT, "a bounded device-side wait gave up");
+    if (status & tune::kStatusInvalid)
+        return tune::fail(TUNE_EINVAL, "a descriptor was malformed (mask outside the axes, "
+                                       "negative count, register or shared-memory field)");
+    return TUNE_OK;
+}
+
+}  // extern "C"

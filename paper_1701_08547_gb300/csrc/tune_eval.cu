@@ -1,0 +1,593 @@
+// tune_eval: occupancy (Eqs. 1-5) + instruction-mix cost (Eq. 6 with launch-shape
+// terms) over every point of every kernel's tuning space, then per-kernel top-k.
+//
+// Work decomposition (GB300, CUDA cores only; the path is integer/FP32 issue-bound):
+//  * one warp evaluates one kernel descriptor; CTAs of 8 warps stride over the
+//    descriptors (grid = SMs x resident CTAs);
+//  * per CTA, once: tables that depend only on the architecture row and the
+//    axes (W_B, G_W, lane by thread count; hide by W*; waves/slots factor by
+//    (B*, G); floor(w / W_B) for the register limit);
+//  * per kernel, lane-parallel: the per-unroll cost sums C_nm(U), C_m(U)
+//    (compensated FP32 sums), register-limited warps, per-carveout G_S, and
+//    the (T, U) block limit min(G_W, G_R);
+//  * hot loop: a lane walks (T, U, C) triples; occupancy B*, W* come from
+//    two table lookups and a min (grid size does not enter Eqs. 1-5), then
+//    all grid sizes G of that triple cost one FP32 multiply each:
+//    cost(T,G,U,C) = X(T,U,C) * ipar(B*, G);
+//  * each lane keeps a sorted register list of its k best (cost, index);
+//    lanes visit points in increasing canonical index, so a strict "<"
+//    keeps lower indices first among equal costs;
+//  * a k-round warp merge (two redux.sync minima per round) emits the
+//    kernel's top-k.
+#include <math.h>
+#include <stdint.h>
+
+#include "tune_internal.h"
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kMaxB = 32;  // blocks per SM supported by the tables
+constexpr int kMaxW = 64;  // warps per SM supported by the tables
+constexpr unsigned kFull = 0xffffffffu;
+
+enum { CL_FP32 = 0, CL_FP64, CL_INT, CL_GLDST, CL_SLDST, CL_BRANCH, CL_SFU };
+
+struct EvalParams {
+    tune_arch a;
+    tune_axes x;
+    int64_t n_kernels;
+    int k;
+};
+
+struct CtaTables {
+    float ipar[kMaxB][16];           // (waves*slots)/(n_sm*G) by (B*-1, g position); +inf padding
+    float rcp[8];                    // 1 / IPC per class
+    float hide[kMaxW + 1];           // max(1, W_sat / W*)
+    float lane[32];                  // (32 * W_B) / T by t position
+    int wb[32];                      // W_B = ceil(T / 32) by t position
+    int gw[32];                      // G_W by t position (0 if T > max threads per block)
+    unsigned char divt[kMaxW + 1][32];  // floor(w / W_B) by (w, t position)
+    unsigned char perm[kMaxB][16];   // g positions of ipar row b in increasing (value, g) order
+    float iparmin[kMaxB];            // min of ipar row b over all axis grid sizes
+};
+
+struct WarpTables {
+    float iparc[kMaxB][16];  // ipar rows compacted to the kernel's grid sizes
+    float iparmin[kMaxB];    // min over the kernel's grid sizes of ipar(b, G)
+    float4 uc[32];           // by (u rank * n_C + c rank): C_nm, C_m, u rank, G_S
+    unsigned char gwr[32][8];  // min(G_W, G_R) by (t rank, u rank)
+    float cnm[8], cm[8];     // by u rank
+    int warps_r[8];          // register-limited warps (clamped to kMaxW) by u rank
+    int wb_max[8];           // largest W_B whose block fits the per-block register limit
+    int regs[8];             // R by u rank
+    int gs[4];               // G_S by c rank
+    int tpos[32];            // t position by t rank
+    int gpos[16];            // g position by g rank
+    int upos[8];
+};
+
+__device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Compensated (Neumaier) FP32 sum, explicit round-to-nearest operations.
+template <int M>
+__device__ __forceinline__ float neumaier(const float (&x)[M])
+{
+    float s = 0.0f, comp = 0.0f;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        float t = __fadd_rn(s, x[i]);
+        if (fabsf(s) >= fabsf(x[i]))
+            comp = __fadd_rn(comp, __fadd_rn(__fsub_rn(s, t), x[i]));
+        else
+            comp = __fadd_rn(comp, __fadd_rn(__fsub_rn(x[i], t), s));
+        s = t;
+    }
+    return __fadd_rn(s, comp);
+}
+
+__device__ void build_cta_tables(const EvalParams& p, CtaTables& ct)
+{
+    const tune_arch& a = p.a;
+    const tune_axes& x = p.x;
+    for (int i = threadIdx.x; i < kMaxB * 16; i += blockDim.x) {
+        int b = i >> 4, g = i & 15;
+        float v = __int_as_float(0x7f800000);
+        if (b < a.max_blocks_sm && g < x.n_g) {
+            int slots = a.n_sm * (b + 1);
+            int G = x.g[g];
+            int waves = ceil_div(G, slots);
+            v = __fdiv_rn((float)(waves * slots), (float)(a.n_sm * G));
+        }
+        ct.ipar[b][g] = v;
+    }
+    for (int i = threadIdx.x; i < (kMaxW + 1) * 32; i += blockDim.x) {
+        int w = i >> 5, t = i & 31;
+        int wb = t < x.n_t ? ceil_div(x.t[t], 32) : 1;
+        ct.divt[w][t] = (unsigned char)(w / wb);
+    }
+    int tid = threadIdx.x;
+    __syncthreads();
+    if (tid < kMaxB) {  // insertion sort of row tid by (ipar value, g position), in place
+        float mn = __int_as_float(0x7f800000);
+        for (int g = 0; g < x.n_g; ++g) mn = fminf(mn, ct.ipar[tid][g]);
+        ct.iparmin[tid] = mn;
+        unsigned char* ord = ct.perm[tid];
+        for (int g = 0; g < x.n_g; ++g) {
+            const float v = ct.ipar[tid][g];
+            int j = g;
+            while (j > 0 && ct.ipar[tid][ord[j - 1]] > v) {
+                ord[j] = ord[j - 1];
+                --j;
+            }
+            ord[j] = (unsigned char)g;
+        }
+    }
+    if (tid < 32) {
+        int wb = 1, gw = 0;
+        float ln = 1.0f;
+        if (tid < x.n_t) {
+            int T = x.t[tid];
+            wb = ceil_div(T, 32);
+            gw = T <= a.max_threads_block ? min(a.max_blocks_sm, a.max_warps_sm / wb) : 0;
+            ln = __fdiv_rn((float)(32 * wb), (float)T);
+        }
+        ct.wb[tid] = wb;
+        ct.gw[tid] = gw;
+        ct.lane[tid] = ln;
+    } else if (tid < 32 + kMaxW + 1) {
+        int w = tid - 32;
+        float h = w > 0 ? __fdiv_rn((float)a.w_sat, (float)w) : 1.0f;
+        ct.hide[w] = fmaxf(1.0f, h);
+    } else if (tid < 32 + kMaxW + 1 + 8) {
+        int c = tid - 32 - kMaxW - 1;
+        ct.rcp[c] = c < TUNE_NCLASS ? __fdiv_rn(1.0f, a.ipc[c]) : 0.0f;
+    }
+}
+
+// Sorted insert of (c, i) into a lane's register list (ascending; strict "<"
+// keeps earlier = lower-index entries first among equal costs).
+// (cost, index) keys ordered lexicographically; costs are >= 0, so their bit
+// patterns order like the values.
+__device__ __forceinline__ bool key_less(float c, int i, float c2, int i2)
+{
+    return c < c2 || (c == c2 && i < i2);
+}
+
+// Warp-wide top-k list: lane j < k holds the j-th best (cost, index), ascending.
+// Inserts one key (the same on every lane); returns nothing, updates the list
+// and the k-th key (tau) on every lane.
+__device__ __forceinline__ void warp_list_insert(float& lc, int& li, float& tau_c, int& tau_i, float c,
+                                                 int i, int k, int lane)
+{
+    const unsigned below = __ballot_sync(kFull, lane < k && key_less(lc, li, c, i));
+    const int pos = __popc(below);
+    const float up_c = __shfl_up_sync(kFull, lc, 1);
+    const int up_i = __shfl_up_sync(kFull, li, 1);
+    if (lane < k) {
+        if (lane == pos) {
+            lc = c;
+            li = i;
+        } else if (lane > pos) {
+            lc = up_c;
+            li = up_i;
+        }
+    }
+    tau_c = __shfl_sync(kFull, lc, k - 1);
+    tau_i = __shfl_sync(kFull, li, k - 1);
+}
+
+template <bool EMIT>
+__global__ void __maxnreg__(64)
+    tune_eval_kernel(const __grid_constant__ EvalParams p, const int4* __restrict__ descs,
+                     int32_t* __restrict__ topk_idx, float* __restrict__ topk_cost,
+                     int32_t* __restrict__ pt_b, int32_t* __restrict__ pt_w,
+                     float* __restrict__ pt_c, const int64_t* __restrict__ pt_off,
+                     int* __restrict__ status)
+{
+    __shared__ CtaTables ct;
+    __shared__ WarpTables wts[kWarps];
+    build_cta_tables(p, ct);
+    __syncthreads();
+
+    const tune_arch& a = p.a;
+    const tune_axes& x = p.x;
+    const int lane = threadIdx.x & 31;
+    WarpTables& w = wts[threadIdx.x >> 5];
+    const float kInf = __int_as_float(0x7f800000);
+    const int k = p.k;
+    const uint32_t t_ok = x.n_t == 32 ? 0xffffffffu : ((1u << x.n_t) - 1u);
+    const uint32_t g_ok = (1u << x.n_g) - 1u, u_ok = (1u << x.n_u) - 1u, c_ok = (1u << x.n_c) - 1u;
+
+    for (int64_t kid = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); kid < p.n_kernels;
+         kid += (int64_t)gridDim.x * kWarps) {
+        // ---- descriptor: lanes 0..3 load the four 16-byte words, then broadcast.
+        int4 v = __ldg(descs + kid * 4 + (lane & 3));
+        float n[7];
+        n[0] = __int_as_float(__shfl_sync(kFull, v.x, 0));
+        n[1] = __int_as_float(__shfl_sync(kFull, v.y, 0));
+        n[2] = __int_as_float(__shfl_sync(kFull, v.z, 0));
+        n[3] = __int_as_float(__shfl_sync(kFull, v.w, 0));
+        n[4] = __int_as_float(__shfl_sync(kFull, v.x, 1));
+        n[5] = __int_as_float(__shfl_sync(kFull, v.y, 1));
+        n[6] = __int_as_float(__shfl_sync(kFull, v.z, 1));
+        const int r0 = __shfl_sync(kFull, v.w, 1);
+        const int s0 = __shfl_sync(kFull, v.x, 2);
+        const float d = __int_as_float(__shfl_sync(kFull, v.y, 2));
+        const uint32_t mlo = (uint32_t)__shfl_sync(kFull, v.z, 2);
+        const uint32_t mhi = (uint32_t)__shfl_sync(kFull, v.w, 2);
+
+        const uint32_t tm = mlo, gm = mhi & 0xffffu, um = (mhi >> 16) & 0xffu, cm = (mhi >> 24) & 0xfu;
+        bool bad = (mhi >> 28) != 0 || (tm & ~t_ok) || (gm & ~g_ok) || (um & ~u_ok) ||
+                   (cm & ~c_ok) || r0 < 0 || r0 >= (1 << 24) || s0 < 0 || s0 >= (1 << 30) ||
+                   !(d >= 0.0f);
+#pragma unroll
+        for (int c = 0; c < 7; ++c) bad = bad || !(n[c] >= 0.0f);
+        const int nT = __popc(tm), nG = __popc(gm), nU = __popc(um), nC = __popc(cm);
+        if (bad || nT * nG * nU * nC == 0) {
+            if (bad && lane == 0) atomicOr(status, tune::kStatusInvalid);
+            if (lane < k) {
+                topk_idx[kid * k + lane] = -1;
+                topk_cost[kid * k + lane] = kInf;
+            }
+            continue;
+        }
+        const int nUC = nU * nC;
+
+        // ---- per-axis compaction: lane = axis position.
+        const uint32_t below = (1u << lane) - 1u;
+        if ((tm >> lane) & 1u) w.tpos[__popc(tm & below)] = lane;
+        if (lane < 16 && ((gm >> lane) & 1u)) w.gpos[__popc(gm & below)] = lane;
+        if (lane < 8 && ((um >> lane) & 1u)) {
+            const int ur = __popc(um & below);
+            const int U = x.u[lane];
+            const int R = r0 + 4 * (U - 1);
+            float vv[7];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                float nc = c == CL_BRANCH ? __fdiv_rn(n[c], (float)U) : n[c];
+                vv[c] = __fmul_rn(nc, ct.rcp[c]);
+            }
+            const float nm[5] = {vv[CL_FP32], vv[CL_FP64], vv[CL_INT], vv[CL_BRANCH], vv[CL_SFU]};
+            const float mm[2] = {vv[CL_GLDST], vv[CL_SLDST]};
+            const float dk = __fmul_rn(__fadd_rn(1.0f, d), (float)a.work_scale);
+            w.cnm[ur] = __fmul_rn(neumaier(nm), dk);
+            w.cm[ur] = __fmul_rn(neumaier(mm), dk);
+            w.regs[ur] = R;
+            w.upos[ur] = lane;
+            int warps = 0, wbmax = 0;
+            if (a.reg_alloc_mode == 0 && R > 0 && R <= a.regs_thread_max) {
+                const int rpw = ceil_div(R * 32, a.reg_alloc_unit) * a.reg_alloc_unit;
+                wbmax = a.regs_block_max / rpw;
+                warps = (a.regs_sm / rpw) / a.warp_alloc_gran * a.warp_alloc_gran;
+                warps = min(warps, kMaxW);
+            }
+            w.warps_r[ur] = warps;
+            w.wb_max[ur] = wbmax;
+        }
+        if (lane < 4 && ((cm >> lane) & 1u)) {
+            const int C = x.c[lane];
+            int gs = 0;
+            if (s0 <= a.smem_block_max) {
+                const int s_alloc =
+                    ceil_div(s0 + a.smem_reserved_block, a.smem_alloc_unit) * a.smem_alloc_unit;
+                const int max_cap = a.smem_caps[a.n_smem_caps - 1];
+                int cap = -1;
+                for (int i = 0; i < a.n_smem_caps; ++i) {
+                    const int ci = a.smem_caps[i];
+                    if (100LL * ci >= (long long)C * max_cap && ci >= s_alloc) {
+                        cap = ci;
+                        break;
+                    }
+                }
+                if (s_alloc == 0) gs = a.max_blocks_sm;
+                else if (cap >= 0) gs = cap / s_alloc;
+            }
+            w.gs[__popc(cm & below)] = gs;
+        }
+        __syncwarp();
+        // ---- (T, U) block limit min(G_W, G_R); lane = t rank.
+        if (lane < nT) {
+            const int tp = w.tpos[lane];
+            const int wb = ct.wb[tp];
+            const int gw = ct.gw[tp];
+            for (int ur = 0; ur < nU; ++ur) {
+                const int R = w.regs[ur];
+                int gr;
+                if (R > a.regs_thread_max) gr = 0;
+                else if (R <= 0) gr = a.max_blocks_sm;
+                else if (a.reg_alloc_mode == 0) gr = wb > w.wb_max[ur] ? 0 : ct.divt[w.warps_r[ur]][tp];
+                else {
+                    const long long rpb = (long long)ceil_div(R * 32 * wb, a.reg_alloc_unit) * a.reg_alloc_unit;
+                    gr = rpb > a.regs_block_max ? 0 : (int)(a.regs_sm / rpb);
+                }
+                w.gwr[lane][ur] = (unsigned char)min(gw, gr);
+            }
+        }
+        // ---- (U, C) pair table; lane = pair rank.
+        if (lane < nUC) {
+            const int ur = lane / nC, cr = lane - (lane / nC) * nC;
+            w.uc[lane] = make_float4(w.cnm[ur], w.cm[ur], __int_as_float(ur), __int_as_float(w.gs[cr]));
+        }
+        // ---- waves/slots factor rows, compacted to this kernel's grid sizes.
+        const bool g_dense = gm == g_ok;
+        if (!g_dense && lane < kMaxB) {
+            float mn = kInf;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float v = j < nG ? ct.ipar[lane][w.gpos[j]] : kInf;
+                w.iparc[lane][j] = v;
+                mn = fminf(mn, v);
+            }
+            w.iparmin[lane] = mn;
+        }
+        __syncwarp();
+        const float* ipar_rows = g_dense ? &ct.ipar[0][0] : &w.iparc[0][0];
+        const float* iparmin = g_dense ? ct.iparmin : w.iparmin;
+
+        // ---- (T, U, C) triples of this lane: t rank advances by 32 / nUC per step.
+        const int t0 = lane / nUC, uc0 = lane - (lane / nUC) * nUC;
+        const int dq = 32 / nUC, dr = 32 - (32 / nUC) * nUC;
+        const int g_stride = nG * nUC;
+        const int n_iter = (nT * nUC + 31) >> 5;
+        // B* and the grid-independent cost factor X of one triple.
+        auto triple = [&](int t_r, int uc_r, int& B, int& W, float& X) {
+            const float4 ucv = w.uc[uc_r];
+            const int ur = __float_as_int(ucv.z);
+            const int tp = w.tpos[t_r];
+            B = min((int)w.gwr[t_r][ur], __float_as_int(ucv.w));
+            W = B * ct.wb[tp];
+            X = __fmul_rn(__fmaf_rn(ucv.y, ct.hide[W], ucv.x), ct.lane[tp]);
+        };
+
+        // ---- pre-pass: each triple's cheapest grid size costs X * min_G ipar(B*, G).
+        // Each lane keeps its four smallest; the k-th smallest over the warp is a
+        // valid starting bound tau0 (k distinct triples each own a point <= tau0).
+        float tau0 = kInf;
+        if (!EMIT) {
+            float m0 = kInf, m1 = kInf, m2 = kInf, m3 = kInf;
+            int t_r = t0, uc_r = uc0;
+            for (int it = 0; it < n_iter; ++it) {
+                if (t_r < nT) {
+                    int B, W;
+                    float X;
+                    triple(t_r, uc_r, B, W, X);
+                    if (B > 0) {
+                        float v = __fmul_rn(X, iparmin[B - 1]);
+                        float lo;
+                        lo = fminf(m0, v); v = fmaxf(m0, v); m0 = lo;
+                        lo = fminf(m1, v); v = fmaxf(m1, v); m1 = lo;
+                        lo = fminf(m2, v); v = fmaxf(m2, v); m2 = lo;
+                        m3 = fminf(m3, v);
+                    }
+                    t_r += dq;
+                    uc_r += dr;
+                    if (uc_r >= nUC) {
+                        uc_r -= nUC;
+                        ++t_r;
+                    }
+                }
+            }
+            for (int r = 0; r < k; ++r) {
+                const unsigned mb = __reduce_min_sync(kFull, __float_as_uint(m0));
+                tau0 = __uint_as_float(mb);
+                if (mb >= 0x7f800000u) break;
+                const unsigned who = __ballot_sync(kFull, __float_as_uint(m0) == mb);
+                if (lane == __ffs(who) - 1) {
+                    m0 = m1;
+                    m1 = m2;
+                    m2 = m3;
+                    m3 = kInf;
+                }
+            }
+        }
+
+        // ---- main pass. The warp keeps one exact top-k list (lane j = j-th best)
+        // and its k-th key tau. Every point's cost is computed and folded into its
+        // triple's minimum; only when some lane's minimum can still enter the list
+        // does the warp merge the lanes' candidates in increasing (cost, index).
+        float lc = kInf;  // this lane's list entry (lanes < k)
+        int li = -1;
+        float tau_c = kInf;
+        int tau_i = -1;
+        const int64_t off = EMIT ? pt_off[kid] : 0;
+        int t_r = t0, uc_r = uc0;
+        for (int it = 0; it < n_iter; ++it) {
+            bool any = false;
+            float X = 0.0f;
+            int B = 0, base = 0;
+            if (t_r < nT) {
+                int W;
+                triple(t_r, uc_r, B, W, X);
+                base = t_r * g_stride + uc_r;
+                if (B > 0) {
+                    const float4* row = reinterpret_cast<const float4*>(ipar_rows + (B - 1) * 16);
+                    float c[16];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (q * 4 < nG) {
+                            const float4 f = row[q];
+                            c[4 * q + 0] = __fmul_rn(X, f.x);
+                            c[4 * q + 1] = __fmul_rn(X, f.y);
+                            c[4 * q + 2] = __fmul_rn(X, f.z);
+                            c[4 * q + 3] = __fmul_rn(X, f.w);
+                        } else {
+                            c[4 * q + 0] = c[4 * q + 1] = c[4 * q + 2] = c[4 * q + 3] = kInf;
+                        }
+                    }
+                    // min over the triple's costs (padding entries are +inf or NaN; fminf
+                    // drops NaN)
+                    float m01 = fminf(fminf(c[0], c[1]), fminf(c[2], c[3]));
+                    float m23 = fminf(fminf(c[4], c[5]), fminf(c[6], c[7]));
+                    float m45 = fminf(fminf(c[8], c[9]), fminf(c[10], c[11]));
+                    float m67 = fminf(fminf(c[12], c[13]), fminf(c[14], c[15]));
+                    const float cmin = fminf(fminf(m01, m23), fminf(m45, m67));
+                    any = cmin <= fminf(tau_c, tau0);
+                    if (EMIT) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (j < nG) {
+                                const int64_t at = off + base + j * nUC;
+                                if (pt_b) pt_b[at] = B;
+                                if (pt_w) pt_w[at] = W;
+                                if (pt_c) pt_c[at] = c[j];
+                            }
+                        }
+                    }
+                } else if (EMIT) {
+                    for (int j = 0; j < nG; ++j) {
+                        const int64_t at = off + base + j * nUC;
+                        if (pt_b) pt_b[at] = 0;
+                        if (pt_w) pt_w[at] = 0;
+                        if (pt_c) pt_c[at] = kInf;
+                    }
+                }
+                t_r += dq;
+                uc_r += dr;
+                if (uc_r >= nUC) {
+                    uc_r -= nUC;
+                    ++t_r;
+                }
+            }
+            if (__ballot_sync(kFull, any) == 0u) continue;
+
+            // Merge: each candidate lane walks its triple's grid sizes in increasing
+            // cost (the order of X * ipar(B*, G) over G depends on B* only); the warp
+            // repeatedly inserts the smallest head until no head can enter the list.
+            int r = 0;
+            float hc = kInf;
+            int hi = 0x7fffffff;
+            auto advance = [&]() {
+                hc = kInf;
+                hi = 0x7fffffff;
+                while (r < x.n_g) {
+                    const int g = ct.perm[B - 1][r++];
+                    if ((gm >> g) & 1u) {
+                        hc = __fmul_rn(X, ct.ipar[B - 1][g]);
+                        hi = base + __popc(gm & ((1u << g) - 1u)) * nUC;
+                        break;
+                    }
+                }
+            };
+            if (any) advance();
+            for (;;) {
+                const unsigned mc = __reduce_min_sync(kFull, __float_as_uint(hc));
+                const float mcf = __uint_as_float(mc);
+                const unsigned mi = __reduce_min_sync(kFull, hc == mcf ? (unsigned)hi : 0xffffffffu);
+                if (mc >= 0x7f800000u || mcf > tau0 || !key_less(mcf, (int)mi, tau_c, tau_i)) break;
+                warp_list_insert(lc, li, tau_c, tau_i, mcf, (int)mi, k, lane);
+                if (hc == mcf && hi == (int)mi) advance();
+            }
+        }
+
+        if (lane < k) {
+            topk_idx[kid * k + lane] = li;
+            topk_cost[kid * k + lane] = lc;
+        }
+        __syncwarp();  // the warp's tables are rewritten for the next kernel
+    }
+}
+
+template <bool EMIT>
+int launch(const EvalParams& p, const tune_kernel_desc* descs, int32_t* ti, float* tc, int32_t* pb,
+           int32_t* pw, float* pc, const int64_t* po, int* status, cudaStream_t s)
+{
+    auto kern = tune_eval_kernel<EMIT>;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        TUNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0),
+                      "tune_eval: occupancy query");
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int sms = tune::device_sm_count();
+    if (sms <= 0) return tune::fail(TUNE_ECUDA, "tune_eval: cannot query the SM count");
+    const int64_t need = (p.n_kernels + kWarps - 1) / kWarps;
+    const int64_t cap = (int64_t)sms * per_sm;
+    const int grid = (int)(need < cap ? need : cap);
+    kern<<<grid, kThreads, 0, s>>>(p, reinterpret_cast<const int4*>(descs), ti, tc, pb, pw, pc, po,
+                                   status);
+    TUNE_CUDA_TRY(cudaGetLastError(), "tune_eval: kernel launch");
+    return TUNE_OK;
+}
+
+int validate(const tune_arch* a, const tune_axes* x, int32_t k)
+{
+    using tune::fail;
+    if (!a || !x) return fail(TUNE_EINVAL, "arch and axes must be non-NULL host pointers");
+    if (k < 1 || k > 16) return fail(TUNE_EINVAL, "k = %d outside [1, 16]", k);
+    if (a->warp_size != 32) return fail(TUNE_EINVAL, "warp_size must be 32");
+    if (a->n_sm < 1 || a->max_threads_block < 1 || a->max_warps_sm < 1 || a->max_warps_sm > kMaxW ||
+        a->max_blocks_sm < 1 || a->max_blocks_sm > kMaxB)
+        return fail(TUNE_EINVAL, "arch: n_sm, max_threads_block, max_warps_sm (<=64) or "
+                                 "max_blocks_sm (<=32) out of range");
+    if (a->regs_sm < 1 || a->regs_block_max < 1 || a->regs_thread_max < 1 ||
+        a->regs_thread_max > 65536 || a->reg_alloc_unit < 1 || a->reg_alloc_unit > 65536 ||
+        a->warp_alloc_gran < 1 || (a->reg_alloc_mode != 0 && a->reg_alloc_mode != 1))
+        return fail(TUNE_EINVAL, "arch: register fields out of range");
+    if (a->smem_block_max < 0 || a->smem_block_max > (1 << 24) || a->smem_reserved_block < 0 ||
+        a->smem_reserved_block > (1 << 24) || a->smem_alloc_unit < 1 || a->smem_alloc_unit > (1 << 20) ||
+        a->n_smem_caps < 1 || a->n_smem_caps > 16)
+        return fail(TUNE_EINVAL, "arch: shared-memory fields out of range");
+    for (int i = 0; i < a->n_smem_caps; ++i)
+        if (a->smem_caps[i] < 0 || (i > 0 && a->smem_caps[i] < a->smem_caps[i - 1]) ||
+            a->smem_caps[i] > (1 << 24))
+            return fail(TUNE_EINVAL, "arch: smem_caps must be ascending, in [0, 16 MB]");
+    for (int c = 0; c < TUNE_NCLASS; ++c)
+        if (!(a->ipc[c] > 0.0f) || !isfinite(a->ipc[c])) return fail(TUNE_EINVAL, "arch: ipc[%d] must be > 0", c);
+    if (a->w_sat < 1 || a->w_sat > (1 << 20) || a->work_scale < 1 || a->work_scale > (1 << 24))
+        return fail(TUNE_EINVAL, "arch: w_sat or work_scale out of range");
+    if (x->n_t < 1 || x->n_t > 32 || x->n_g < 1 || x->n_g > 16 || x->n_u < 1 || x->n_u > 8 ||
+        x->n_c < 1 || x->n_c > 4)
+        return fail(TUNE_EINVAL, "axes: lengths out of range");
+    for (int i = 0; i < x->n_t; ++i)
+        if (x->t[i] < 1 || x->t[i] > 4096) return fail(TUNE_EINVAL, "axes: t[%d] outside [1, 4096]", i);
+    for (int i = 0; i < x->n_g; ++i) {
+        if (x->g[i] < 1 || (int64_t)a->n_sm * x->g[i] >= (1 << 24) ||
+            (int64_t)x->g[i] + (int64_t)a->n_sm * a->max_blocks_sm >= (1 << 24))
+            return fail(TUNE_EINVAL, "axes: g[%d] must be >= 1 with n_sm * g < 2^24", i);
+    }
+    for (int i = 0; i < x->n_u; ++i)
+        if (x->u[i] < 1 || x->u[i] > 64) return fail(TUNE_EINVAL, "axes: u[%d] outside [1, 64]", i);
+    for (int i = 0; i < x->n_c; ++i)
+        if (x->c[i] < 0 || x->c[i] > 100) return fail(TUNE_EINVAL, "axes: c[%d] outside [0, 100]", i);
+    return TUNE_OK;
+}
+
+}  // namespace
+
+extern "C" int tune_eval(const tune_arch* arch, const tune_axes* axes, const tune_kernel_desc* descs,
+                         int64_t n_kernels, int32_t k, uint32_t flags, int32_t* topk_idx,
+                         float* topk_cost, int32_t* pt_blocks, int32_t* pt_warps, float* pt_cost,
+                         const int64_t* pt_offsets, void* workspace, size_t ws_bytes,
+                         tune_stream_t stream)
+{
+    tune::clear_error();
+    int rc = validate(arch, axes, k);
+    if (rc) return rc;
+    if (n_kernels < 0) return tune::fail(TUNE_EINVAL, "n_kernels < 0");
+    if (!workspace) return tune::fail(TUNE_EINVAL, "workspace is NULL");
+    if (ws_bytes < tune_workspace_bytes(TUNE_CALL_EVAL, n_kernels, k))
+        return tune::fail(TUNE_ENOMEM, "workspace of %zu bytes is smaller than %zu", ws_bytes,
+                          tune_workspace_bytes(TUNE_CALL_EVAL, n_kernels, k));
+    if (n_kernels > 0 && (!descs || !topk_idx || !topk_cost))
+        return tune::fail(TUNE_EINVAL, "descs, topk_idx and topk_cost must be non-NULL");
+    if ((reinterpret_cast<uintptr_t>(descs) & 15) != 0)
+        return tune::fail(TUNE_EINVAL, "descs must be 16-byte aligned");
+    if (flags & ~TUNE_EMIT_POINTS) return tune::fail(TUNE_EINVAL, "unknown flags 0x%x", flags);
+    const bool emit = (flags & TUNE_EMIT_POINTS) != 0;
+    if (emit && !pt_offsets) return tune::fail(TUNE_EINVAL, "TUNE_EMIT_POINTS needs pt_offsets");
+
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int* status = static_cast<int*>(workspace);
+    TUNE_CUDA_TRY(cudaMemsetAsync(workspace, 0, tune::kWorkspaceHeader, s), "tune_eval: status reset");
+    if (n_kernels == 0) return TUNE_OK;
+
+    EvalParams p;
+    p.a = *arch;
+    p.x = *axes;
+    p.n_kernels = n_kernels;
+    p.k = k;
+    return emit ? launch<true>(p, descs, topk_idx, topk_cost, pt_blocks, pt_warps, pt_cost, pt_offsets, status, s)
+                : launch<false>(p, descs, topk_idx, topk_cost, nullptr, nullptr, nullptr, nullptr, status, s);
+}

@@ -1,0 +1,33 @@
+// Internal helpers shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tune.h"
+
+namespace tune {
+
+// Record an error message for tune_last_error() and return `code`.
+int fail(int code, const char* fmt, ...);
+// Map a CUDA error to TUNE_ECUDA with a message naming the call site.
+int cuda_fail(cudaError_t e, const char* what);
+// Clear the thread's last-error message.
+void clear_error();
+
+// Status word bits written by kernels into the first word of the workspace.
+enum : int { kStatusInvalid = 1, kStatusTimeout = 2 };
+
+// Workspace header: status word and counters, 256 bytes, zeroed per call.
+constexpr size_t kWorkspaceHeader = 256;
+
+// Number of SMs of the current device (cached per device).
+int device_sm_count();
+
+}  // namespace tune
+
+#define TUNE_CUDA_TRY(call, what)                                         \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return ::tune::cuda_fail(e_, what);        \
+    } while (0)

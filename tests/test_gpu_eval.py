@@ -1,0 +1,190 @@
+"""GPU parity of tune_eval against the CPU oracle, through the C ABI.
+
+Occupancy (B*, W*) and top-k indices must match bit for bit; FP32 costs must
+equal the oracle's FP32 evaluation bit for bit (both follow the same fixed
+operation order) and stay within 1e-5 relative of its FP64 cost.
+"""
+
+import numpy as np
+import pytest
+
+from workloads import archs, gen
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL_FP64 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+
+    from paper_1701_08547_gb300 import build
+
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch.device("cuda:0")
+
+
+def gpu_eval(dev, arch, axes, descs, k, emit=False):
+    import torch
+
+    import paper_1701_08547_gb300 as T
+
+    d = T.descs_to_device(descs, dev)
+    ws = T.workspace(0, len(descs), k, dev)
+    out = {}
+    kw = {}
+    if emit:
+        off = gen.point_offsets(descs)
+        total = int(off[-1])
+        kw = dict(pt_blocks=torch.empty(total, dtype=torch.int32, device=dev),
+                  pt_warps=torch.empty(total, dtype=torch.int32, device=dev),
+                  pt_cost=torch.empty(total, dtype=torch.float32, device=dev),
+                  pt_offsets=torch.from_numpy(off).to(dev))
+    idx, cost = T.tune_eval(arch, axes, d, k, flags=T.TUNE_EMIT_POINTS if emit else 0,
+                            workspace_buf=ws, **kw)
+    T.tune_check(ws)
+    out["idx"] = idx.cpu().numpy()
+    out["cost"] = cost.cpu().numpy()
+    if emit:
+        out["B"] = kw["pt_blocks"].cpu().numpy()
+        out["W"] = kw["pt_warps"].cpu().numpy()
+        out["cost32"] = kw["pt_cost"].cpu().numpy()
+    return out
+
+
+def assert_same_topk(g, o):
+    assert np.array_equal(g["idx"], o["idx"]), np.argwhere(g["idx"] != o["idx"])[:5]
+    assert np.array_equal(g["cost"].view(np.uint32), o["cost"].view(np.uint32))
+
+
+def assert_same_points(g, o):
+    assert np.array_equal(g["B"], o["B"])
+    assert np.array_equal(g["W"], o["W"])
+    assert np.array_equal(g["cost32"].view(np.uint32), o["cost32"].view(np.uint32))
+    ok = np.isfinite(o["cost64"])
+    rel = np.abs(g["cost32"][ok].astype(np.float64) - o["cost64"][ok]) / o["cost64"][ok]
+    assert rel.max(initial=0.0) <= REL_TOL_FP64
+
+
+def test_dense128_all_points(dev, oracle):
+    """64 kernels x 128 points (threads x unroll {1,2,4,8}, grid 1024, carveout 100 %), top-5."""
+    a, ax = archs.arch("sm_103"), gen.axes()
+    d = gen.descriptors(64, 1, "dense128")
+    g = gpu_eval(dev, a, ax, d, 5, emit=True)
+    o = oracle.evaluate(a, ax, d, 5, emit=True, offsets=gen.point_offsets(d))
+    assert_same_topk(g, o)
+    assert_same_points(g, o)
+
+
+@pytest.mark.parametrize("k", [1, 8, 10, 16])
+def test_dense_spaces_all_points(dev, oracle, k):
+    """Dense 16,384-point spaces (32 x 16 x 8 x 4), several k (both register-list sizes)."""
+    a, ax = archs.arch("sm_103"), gen.axes()
+    d = gen.descriptors(48, 2, "dense")
+    g = gpu_eval(dev, a, ax, d, k, emit=True)
+    o = oracle.evaluate(a, ax, d, k, emit=True, offsets=gen.point_offsets(d))
+    assert_same_topk(g, o)
+    assert_same_points(g, o)
+
+
+@pytest.mark.parametrize("k", [1, 5, 13])
+def test_uneven_spaces(dev, oracle, k):
+    """Random subsets of the four axes (sizes 48 .. 16,384)."""
+    a, ax = archs.arch("sm_103"), gen.axes()
+    d = gen.descriptors(400, 3, "uneven")
+    g = gpu_eval(dev, a, ax, d, k, emit=True)
+    o = oracle.evaluate(a, ax, d, k, emit=True, offsets=gen.point_offsets(d))
+    assert_same_topk(g, o)
+    assert_same_points(g, o)
+
+
+@pytest.mark.parametrize("name", list(archs.ARCHS))
+def test_every_arch_row(dev, oracle, name):
+    """The paper's four GPUs (including Fermi's per-block register allocation) and sm_100/sm_103."""
+    a, ax = archs.arch(name), gen.axes()
+    d = gen.descriptors(96, 5, "uneven")
+    d["r0"] = np.minimum(d["r0"], 60)  # keep Fermi (63 registers) partly valid
+    g = gpu_eval(dev, a, ax, d, 7, emit=True)
+    o = oracle.evaluate(a, ax, d, 7, emit=True, offsets=gen.point_offsets(d))
+    assert_same_topk(g, o)
+    assert_same_points(g, o)
+
+
+def test_short_axes_and_orio_space(dev, oracle):
+    """Non-default axes: Orio's thread counts, 8 grid sizes 24..192 (BC), unroll 1..5,
+    two carveouts (Fig. "Performance tuning specification")."""
+    a = archs.arch("sm_60")
+    ax = {"t": list(range(32, 1025, 32)), "g": list(range(24, 193, 24)), "u": [1, 2, 3, 4, 5],
+          "c": [33, 100]}
+    d = gen.descriptors(40, 6, "dense")
+    d["space_mask"] = np.uint64(gen.mask_bits(range(32), range(8), range(5), range(2)))
+    g = gpu_eval(dev, a, ax, d, 6, emit=True)
+    o = oracle.evaluate(a, ax, d, 6, emit=True, offsets=gen.point_offsets(d))
+    assert_same_topk(g, o)
+    assert_same_points(g, o)
+
+
+def test_edge_cases(dev, oracle):
+    """Empty space, all-invalid space, fewer valid points than k, one-point space."""
+    a, ax = archs.arch("sm_103"), gen.axes()
+    d = gen.descriptors(5, 7, "dense128")
+    d["space_mask"][0] = np.uint64(0)                                # empty
+    d["r0"][1] = 300                                                 # nothing fits
+    d["r0"][2] = 254                                                 # 8 valid points
+    d["space_mask"][3] = np.uint64(gen.mask_bits([3], [2], [0], [1]))  # one point
+    g = gpu_eval(dev, a, ax, d, 16)
+    o = oracle.evaluate(a, ax, d, 16)
+    assert_same_topk(g, o)
+    assert np.all(g["idx"][0] == -1) and np.all(g["idx"][1] == -1)
+    assert np.sum(g["idx"][2] >= 0) == 8 and np.sum(g["idx"][3] >= 0) == 1
+
+
+def test_zero_kernels(dev):
+    import torch
+
+    import paper_1701_08547_gb300 as T
+
+    d = torch.empty((0, 64), dtype=torch.uint8, device=dev)
+    idx, cost = T.tune_eval(archs.arch("sm_103"), gen.axes(), d, 4)
+    assert idx.shape == (0, 4)
+
+
+def test_malformed_descriptor_sets_status(dev):
+    """A mask bit outside the axes: that kernel gets padding, the status word reports
+    TUNE_EINVAL, the other kernels are unaffected."""
+    import torch
+
+    import paper_1701_08547_gb300 as T
+
+    ax = gen.axes()
+    ax["u"] = ax["u"][:4]
+    d = gen.descriptors(3, 8, "dense128")
+    d["space_mask"] = np.uint64(gen.mask_bits(range(32), [10], [0, 1, 3], [3]))
+    d["space_mask"][1] = np.uint64(gen.mask_bits([0], [0], [6], [0]))  # u position 6 >= 4
+    dd = T.descs_to_device(d, dev)
+    ws = T.workspace(0, 3, 4, dev)
+    idx, cost = T.tune_eval(archs.arch("sm_103"), ax, dd, 4, workspace_buf=ws)
+    with pytest.raises(T.TuneError) as e:
+        T.tune_check(ws)
+    assert e.value.code == -1
+    assert np.all(idx[1].cpu().numpy() == -1)
+    assert np.all(idx[0].cpu().numpy() >= 0)
+
+
+def test_full_size_dense_sampled(dev, oracle):
+    """100,000 kernels x 16,384 points, top-10, in the launch the bench times;
+    300 sampled kernels checked against the oracle."""
+    import paper_1701_08547_gb300 as T
+
+    a, ax = archs.arch("sm_103"), gen.axes()
+    n = 100_000
+    d = gen.descriptors(n, 2, "dense")
+    dd = T.descs_to_device(d, dev)
+    idx, cost = T.tune_eval(a, ax, dd, 10)
+    idx, cost = idx.cpu().numpy(), cost.cpu().numpy()
+    pick = np.sort(np.random.default_rng(0).choice(n, 300, replace=False))
+    o = oracle.evaluate(a, ax, d[pick], 10)
+    assert np.array_equal(idx[pick], o["idx"])
+    assert np.array_equal(cost[pick].view(np.uint32), o["cost"].view(np.uint32))
