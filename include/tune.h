@@ -148,6 +148,33 @@ int tune_eval(const tune_arch* arch, const tune_axes* axes, const tune_kernel_de
               void* workspace, size_t ws_bytes, tune_stream_t stream);
 
 /*
+ * tune_eval_noalloc — tune_eval for callers that cannot provide a workspace.
+ * The paper has no counterpart; this is a library convenience.
+ *
+ * Some programs cannot allocate device memory on this library's behalf: hosts
+ * that own all device memory and give plugins no way to request a buffer
+ * (serving runtimes, framework allocators), and programs whose device-memory
+ * budget is fixed at start-up. This entry point takes the same inputs and
+ * outputs as tune_eval but keeps its scratch (status word and counters) in a
+ * static device array of 4096 bytes inside the library, which every GPU that
+ * loads the library holds until the process exits. It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *  - A call whose scratch need, tune_workspace_bytes(TUNE_CALL_EVAL, n, k),
+ *    exceeds 4096 bytes is rejected with TUNE_ENOMEM.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before starting any stream capture.
+ *  - Every call shares the array and clears the part it uses at the start;
+ *    calls that overlap on the GPU (for example on two streams) race on it.
+ *  - The call waits for `stream` before returning, so that it can return
+ *    TUNE_EINVAL for malformed descriptors found by the kernel.
+ */
+int tune_eval_noalloc(const tune_arch* arch, const tune_axes* axes, const tune_kernel_desc* descs,
+                      int64_t n_kernels, int32_t k, uint32_t flags, int32_t* topk_idx,
+                      float* topk_cost, int32_t* pt_blocks, int32_t* pt_warps, float* pt_cost,
+                      const int64_t* pt_offsets, tune_stream_t stream);
+
+/*
  * tune_topk — segmented top-k over an external score array (device).
  * For segment s = [seg_offsets[s], seg_offsets[s+1]) of `scores`, the k
  * smallest scores that are not +inf or NaN, equal scores -> lower index;

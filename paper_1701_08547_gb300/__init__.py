@@ -99,3 +99,26 @@ def tune_topk(scores, seg_offsets, k, topk_idx=None, topk_score=None, workspace_
 def tune_check(workspace_buf, stream=None):
     """Wait for the stream and raise if a kernel flagged malformed input."""
     return native.check(native.load().tune_check(_ptr(workspace_buf), _stream(stream)))
+
+
+def tune_eval_noalloc(arch, axes, descs, k, flags=0, topk_idx=None, topk_cost=None, pt_blocks=None,
+                      pt_warps=None, pt_cost=None, pt_offsets=None, stream=None):
+    """tune_eval without a workspace, for hosts that cannot allocate device memory
+    for the library: scratch lives in a static 4 KB device array inside libtune.so.
+    Waits for the stream before returning. Output tensors must be given by callers
+    that cannot allocate; when omitted they are created here for convenience."""
+    torch = _torch()
+    L = native.load_noalloc()
+    n = descs.numel() * descs.element_size() // 64
+    dev = descs.device
+    if topk_idx is None:
+        topk_idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+    if topk_cost is None:
+        topk_cost = torch.empty((n, k), dtype=torch.float32, device=dev)
+    a = native.make_arch(arch)
+    x = native.make_axes(axes)
+    rc = L.tune_eval_noalloc(C.byref(a), C.byref(x), _ptr(descs), n, int(k), int(flags),
+                             _ptr(topk_idx), _ptr(topk_cost), _ptr(pt_blocks), _ptr(pt_warps),
+                             _ptr(pt_cost), _ptr(pt_offsets), _stream(stream))
+    native.check(rc)
+    return topk_idx, topk_cost

@@ -22,6 +22,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "tune_internal.h"
 
 namespace {
@@ -590,4 +592,100 @@ extern "C" int tune_eval(const tune_arch* arch, const tune_axes* axes, const tun
     p.k = k;
     return emit ? launch<true>(p, descs, topk_idx, topk_cost, pt_blocks, pt_warps, pt_cost, pt_offsets, status, s)
                 : launch<false>(p, descs, topk_idx, topk_cost, nullptr, nullptr, nullptr, nullptr, status, s);
+}
+
+// ---------------------------------------------------------------------------
+// tune_eval_noalloc: the same evaluation for callers that cannot hand the
+// library a workspace. Some hosts own every byte of device memory (a serving
+// runtime or a framework allocator that gives plugins no way to ask for a
+// buffer), and some run under a device-memory budget fixed at start-up that
+// must not grow afterwards; neither can call cudaMalloc on the library's
+// behalf. This entry point keeps its scratch in the file-scope array below
+// instead, which every GPU that loads the library holds until the process
+// exits, and allocates nothing itself.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = 4096;  // stated maximum scratch for one call
+
+// Scratch of tune_eval_noalloc (status word and counters). Shared by every
+// call on a device: calls that overlap on the GPU race on it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array for the current device, looked up once
+// per device (host code must not use the symbol itself: on the host it names a
+// stand-in object, not device memory).
+int noalloc_scratch(void** out)
+{
+    int dev = 0;
+    TUNE_CUDA_TRY(cudaGetDevice(&dev), "tune_eval_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return tune::fail(TUNE_EUNSUPPORTED, "device ordinal %d too large", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        TUNE_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch), "tune_eval_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return TUNE_OK;
+}
+
+}  // namespace
+
+extern "C" int tune_eval_noalloc(const tune_arch* arch, const tune_axes* axes,
+                                 const tune_kernel_desc* descs, int64_t n_kernels, int32_t k,
+                                 uint32_t flags, int32_t* topk_idx, float* topk_cost,
+                                 int32_t* pt_blocks, int32_t* pt_warps, float* pt_cost,
+                                 const int64_t* pt_offsets, tune_stream_t stream)
+{
+    tune::clear_error();
+    int rc = validate(arch, axes, k);
+    if (rc) return rc;
+    if (n_kernels < 0) return tune::fail(TUNE_EINVAL, "n_kernels < 0");
+    const size_t need = tune_workspace_bytes(TUNE_CALL_EVAL, n_kernels, k);
+    if (need > kNoallocScratchBytes)
+        return tune::fail(TUNE_ENOMEM,
+                          "tune_eval_noalloc: this call needs %zu bytes of scratch, more than the "
+                          "%zu-byte static area; use tune_eval with a workspace",
+                          need, kNoallocScratchBytes);
+    if (n_kernels > 0 && (!descs || !topk_idx || !topk_cost))
+        return tune::fail(TUNE_EINVAL, "descs, topk_idx and topk_cost must be non-NULL");
+    if ((reinterpret_cast<uintptr_t>(descs) & 15) != 0)
+        return tune::fail(TUNE_EINVAL, "descs must be 16-byte aligned");
+    if (flags & ~TUNE_EMIT_POINTS) return tune::fail(TUNE_EINVAL, "unknown flags 0x%x", flags);
+    const bool emit = (flags & TUNE_EMIT_POINTS) != 0;
+    if (emit && !pt_offsets) return tune::fail(TUNE_EINVAL, "TUNE_EMIT_POINTS needs pt_offsets");
+
+    void* scratch = nullptr;
+    rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // The array keeps the previous call's contents: clear the status word and counters.
+    TUNE_CUDA_TRY(cudaMemsetAsync(scratch, 0, tune::kWorkspaceHeader, s), "tune_eval_noalloc: scratch reset");
+    if (n_kernels > 0) {
+        EvalParams p;
+        p.a = *arch;
+        p.x = *axes;
+        p.n_kernels = n_kernels;
+        p.k = k;
+        int* status = static_cast<int*>(scratch);
+        rc = emit ? launch<true>(p, descs, topk_idx, topk_cost, pt_blocks, pt_warps, pt_cost, pt_offsets, status, s)
+                  : launch<false>(p, descs, topk_idx, topk_cost, nullptr, nullptr, nullptr, nullptr, status, s);
+        if (rc) return rc;
+    }
+    // Report what the kernel found: wait for the stream and read the status word.
+    int st = 0;
+    TUNE_CUDA_TRY(cudaMemcpyAsync(&st, scratch, sizeof(int), cudaMemcpyDeviceToHost, s),
+                  "tune_eval_noalloc: status read");
+    TUNE_CUDA_TRY(cudaStreamSynchronize(s), "tune_eval_noalloc: cudaStreamSynchronize");
+    if (st & tune::kStatusTimeout) return tune::fail(TUNE_ETIMEOUT, "a bounded device-side wait gave up");
+    if (st & tune::kStatusInvalid)
+        return tune::fail(TUNE_EINVAL, "a descriptor was malformed (mask outside the axes, negative "
+                                       "count, register or shared-memory field)");
+    return TUNE_OK;
 }

@@ -104,3 +104,15 @@ def check(rc):
     if rc != TUNE_OK:
         raise TuneError(rc, load().tune_last_error().decode())
     return rc
+
+
+def load_noalloc():
+    """The library with tune_eval_noalloc's signature declared (see include/tune.h)."""
+    L = load()
+    if not getattr(L, "_noalloc_declared", False):
+        vp, i64, i32, u32 = C.c_void_p, C.c_int64, C.c_int32, C.c_uint32
+        L.tune_eval_noalloc.argtypes = [C.POINTER(TuneArch), C.POINTER(TuneAxes), vp, i64, i32, u32,
+                                        vp, vp, vp, vp, vp, vp, vp]
+        L.tune_eval_noalloc.restype = C.c_int
+        L._noalloc_declared = True
+    return L
