@@ -35,13 +35,18 @@ WORKLOADS = {
     # name: (n_kernels per rank, space, k, seed)
     "dense": (100_000, "dense", 10, 2),
     "dense128": (64, "dense128", 5, 1),
+    "uneven": (1_000_000, "uneven", 5, 3),
 }
 ISSUE_LANES_PER_SM_CLK = 4 * 32  # 4 schedulers x 32 lanes per SM and clock
+# Algorithmic work per point for the issue roofline: the per-point figure of the
+# hot-path scope table after the per-kernel hoists (decode ~3, 2 IMNMX, 1 IMAD,
+# 2 table loads, 1 FFMA + 2 FMUL, 1 compare); without hoists it is about 60.
+INSTR_PER_POINT = 12
 L2_FLUSH_BYTES = 256 << 20       # larger than the 126.5 MB L2
 
 
 def algorithmic_instructions(descs, axes):
-    """Thread-instructions the factored evaluation needs (the per-point minimum):
+    """Thread-instructions of the factored evaluation (this kernel's minimum):
     per point 1 FMUL (cost = X * ipar(B*, G)) + 1 FSETP (compare with the k-th best);
     per (T, U, C) triple 5 (min for B*, IMUL for W*, hide lookup, FFMA + FMUL for X).
     """
@@ -80,56 +85,74 @@ def recorded_traffic(workload):
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """SM clock and clock-event reasons sampled during the timed region.
 
-    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+    Read-only NVML queries from a polling thread (every 2 ms), so that short
+    timed regions still get samples; falls back to nvidia-smi if NVML is not
+    loadable.
+    """
 
-    def __init__(self, index):
-        self.index = index
-        self.proc = None
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, uuid=None, index=0):
+        self.uuid, self.index = uuid, index
+        self.sm, self.mx, self.reasons = [], [], set()
+        self._stop = None
+
+    def _nvml(self):
+        import ctypes as C
+
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None, None
+        h = C.c_void_p()
+        ok = False
+        if self.uuid:
+            ok = lib.nvmlDeviceGetHandleByUUID(self.uuid.encode(), C.byref(h)) == 0
+        if not ok:
+            ok = lib.nvmlDeviceGetHandleByIndex_v2(self.index, C.byref(h)) == 0
+        return (lib, h) if ok else (None, None)
+
+    def _poll(self):
+        import ctypes as C
+
+        lib, h = self._nvml()
+        if lib is None:
+            return
+        clk, mx, rs = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx))
+        while not self._stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, C.byref(clk)) == 0:
+                self.sm.append(float(clk.value))
+                self.mx.append(float(mx.value))
+            if lib.nvmlDeviceGetCurrentClocksEventReasons(h, C.byref(rs)) == 0:
+                for bit, name in self.REASONS.items():
+                    if rs.value & bit:
+                        self.reasons.add(name)
+            self._stop.wait(0.002)
 
     def __enter__(self):
+        import threading
+
+        self._stop = threading.Event()
+        self._thread = threading.Thread(target=self._poll, daemon=True)
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.proc = None
+            self._thread.start()
+        except RuntimeError:
+            self._thread = None
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                out, _ = self.proc.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+        self._stop.set()
+        if self._thread is not None:
+            self._thread.join(timeout=5)
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in getattr(self, "lines", []):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 6:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
-            except ValueError:
-                continue
-            for name, v in zip(names, parts[2:6]):
-                if v.lower().startswith("active"):
-                    reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        if not self.sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": sorted(self.reasons), "samples": 0}
+        return {"sm_mhz": statistics.median(self.sm), "sm_max_mhz": max(self.mx),
+                "reasons": sorted(self.reasons), "samples": len(self.sm)}
 
 
 def dist_env():
@@ -173,33 +196,54 @@ def run_ours(args):
     topi = torch.empty((n, k), dtype=torch.int32, device=dev)
     topc = torch.empty((n, k), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+
+    # Schedule: chosen by the library's autotuner on this workload (untimed), or forced.
+    if args.sched == "auto":
+        sched, tuned_ms, _, _ = T.tune_autotune(a, ax, d_dev, k, reps=3, topk_idx=topi, topk_cost=topc,
+                                                workspace_buf=ws, stream=stream)
+    else:
+        sched, tuned_ms = {"warp": 0x10, "thread": 0x20}[args.sched], None
 
     def step():
-        T.tune_eval(a, ax, d_dev, k, topk_idx=topi, topk_cost=topc, workspace_buf=ws, stream=stream)
+        T.tune_eval(a, ax, d_dev, k, flags=sched, topk_idx=topi, topk_cost=topc, workspace_buf=ws,
+                    stream=stream)
+
+    step()  # first call outside capture (occupancy queries are cached here)
+    torch.cuda.synchronize()
+    graph = None
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            step()
+    run_step = graph.replay if graph is not None else step
 
     for _ in range(args.warmup):
         flush.zero_()
-        step()
-    T.tune_check(ws)
+        run_step()
     torch.cuda.synchronize()
+    T.tune_check(ws, stream)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+    with ClockSampler(uuid, local) as clk:
         for i in range(args.steps):
             flush.zero_()  # L2 flush between timed steps (outside the event pair)
             starts[i].record(stream)
-            step()
+            run_step()
             ends[i].record(stream)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    T.tune_check(ws)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    T.tune_check(ws, stream)
+    step_ms = [s_.elapsed_time(e) for s_, e in zip(starts, ends)]
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -218,7 +262,8 @@ def run_ours(args):
         if i >= args.warmup:
             e_start[i - args.warmup].record(stream)
         d_e2e.copy_(host_d, non_blocking=True)
-        T.tune_eval(a, ax, d_e2e, k, topk_idx=topi, topk_cost=topc, workspace_buf=ws, stream=stream)
+        T.tune_eval(a, ax, d_e2e, k, flags=sched, topk_idx=topi, topk_cost=topc, workspace_buf=ws,
+                    stream=stream)
         host_i.copy_(topi, non_blocking=True)
         host_c.copy_(topc, non_blocking=True)
         if i >= args.warmup:
@@ -236,7 +281,8 @@ def run_ours(args):
     peaks, peak_kind = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * ISSUE_LANES_PER_SM_CLK * peaks["sm_max_mhz"] * 1e6 / 1e12  # Tinstr/s
-    achieved = algo_instr / (ms * 1e-3) / 1e12
+    achieved = INSTR_PER_POINT * points / (ms * 1e-3) / 1e12
+    achieved_min = algo_instr / (ms * 1e-3) / 1e12
     line = {
         "metric": METRIC,
         "value": world * points / (ms * 1e-3),
@@ -253,11 +299,15 @@ def run_ours(args):
         "config": {"workload": f"{args.workload}: {n} kernels x {points // n} points, top-{k}, sm_103 row",
                    "kernels_per_gpu": n, "points_per_gpu": points, "k": k,
                    "l2": "flushed between timed steps (256 MB write outside the timed events)",
-                   "parallelism": f"replicas x{world} (kernel ranges)"},
+                   "parallelism": f"replicas x{world} (kernel ranges)",
+                   "schedule_flags": hex(sched), "schedule": "autotuned" if args.sched == "auto" else args.sched,
+                   "cuda_graph": graph is not None},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
                      "peak_source": f"{sms} SMs x 128 lanes x {peaks['sm_max_mhz']} MHz ({peak_kind})",
-                     "algorithmic_instr_per_point": algo_instr / points},
+                     "instr_per_point": INSTR_PER_POINT,
+                     "factored_min_instr_per_point": algo_instr / points,
+                     "frac_factored_min": achieved_min / peak},
         "e2e": {"value": world * points / (e2e_ms * 1e-3), "unit": "points/s",
                 "h2d_bytes_per_step": n * 64, "d2h_bytes_per_step": n * k * 8,
                 "ms_per_step": e2e_ms},
@@ -334,12 +384,14 @@ def run_reference(args):
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=list(WORKLOADS), default="dense")
     p.add_argument("--cpu-sample", type=int, default=16000)
     p.add_argument("--kernels", type=int, default=0, help="override the kernel count (small ncu cases)")
+    p.add_argument("--sched", choices=["auto", "warp", "thread"], default="auto")
+    p.add_argument("--no-graph", action="store_true", help="plain launches instead of graph replays")
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args()
     if args.warmup < 3:

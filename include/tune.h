@@ -108,7 +108,14 @@ typedef struct tune_kernel_desc {
 } tune_kernel_desc;
 
 /* tune_eval flags */
-#define TUNE_EMIT_POINTS 0x1u /* also write per-point B*, W*, cost (pt_* arrays) */
+#define TUNE_EMIT_POINTS 0x1u   /* also write per-point B*, W*, cost (pt_* arrays) */
+#define TUNE_SCHED_WARP 0x10u   /* schedule: one warp per descriptor (the default) */
+#define TUNE_SCHED_THREAD 0x20u /* schedule: one thread per descriptor (not with EMIT) */
+/* Warp schedule knobs (tune_autotune picks them): a work queue handing each warp
+ * 2^c consecutive descriptors per grab (c in 0..14; default: a static stride),
+ * and at most m resident CTAs per SM (m in 1..15; default: as many as fit). */
+#define TUNE_SCHED_CHUNK(c) ((((uint32_t)(c)) + 1u) << 8)
+#define TUNE_SCHED_CTAS(m) (((uint32_t)(m)) << 12)
 
 /* Calls for tune_workspace_bytes(). */
 enum { TUNE_CALL_EVAL = 0, TUNE_CALL_TOPK = 1 };
@@ -173,6 +180,23 @@ int tune_eval_noalloc(const tune_arch* arch, const tune_axes* axes, const tune_k
                       int64_t n_kernels, int32_t k, uint32_t flags, int32_t* topk_idx,
                       float* topk_cost, int32_t* pt_blocks, int32_t* pt_warps, float* pt_cost,
                       const int64_t* pt_offsets, tune_stream_t stream);
+
+/*
+ * tune_autotune — choose tune_eval's schedule for a workload by measurement.
+ * (Library tooling; the paper autotunes the kernels it analyses, not itself.)
+ * Runs tune_eval on the given descriptors with each candidate schedule — the
+ * warp schedule with a static stride or a work queue of 1, 4, 16 or 64
+ * descriptors per grab at full residency or 2 / 3 CTAs per SM, and the thread
+ * schedule — times `reps` runs of each with CUDA events on `stream` (after one
+ * untimed run) and keeps the fastest run's time. Returns the winner's schedule
+ * bits in *best_flags (OR them into tune_eval's flags) and its time in
+ * *best_ms; topk_idx / topk_cost hold the winner's results. Arguments as for
+ * tune_eval, 1 <= reps <= 100. Waits for `stream` before returning.
+ */
+int tune_autotune(const tune_arch* arch, const tune_axes* axes, const tune_kernel_desc* descs,
+                  int64_t n_kernels, int32_t k, int32_t reps, int32_t* topk_idx, float* topk_cost,
+                  void* workspace, size_t ws_bytes, uint32_t* best_flags, float* best_ms,
+                  tune_stream_t stream);
 
 /*
  * tune_topk — segmented top-k over an external score array (device).

@@ -9,10 +9,12 @@ CUDA stream into the C calls and nothing else.
 import ctypes as C
 
 from . import native
-from .native import TUNE_EMIT_POINTS, TuneError  # noqa: F401
+from .native import (TUNE_EMIT_POINTS, TUNE_SCHED_CHUNK, TUNE_SCHED_CTAS,  # noqa: F401
+                     TUNE_SCHED_THREAD, TUNE_SCHED_WARP, TuneError)
 
-__all__ = ["tune_eval", "tune_topk", "tune_workspace_bytes", "tune_check", "descs_to_device",
-           "TUNE_EMIT_POINTS", "TuneError"]
+__all__ = ["tune_eval", "tune_topk", "tune_autotune", "tune_workspace_bytes", "tune_check",
+           "descs_to_device", "TUNE_EMIT_POINTS", "TUNE_SCHED_WARP", "TUNE_SCHED_THREAD",
+           "TUNE_SCHED_CHUNK", "TUNE_SCHED_CTAS", "TuneError"]
 
 
 def _torch():
@@ -94,6 +96,30 @@ def tune_topk(scores, seg_offsets, k, topk_idx=None, topk_score=None, workspace_
                      _ptr(topk_score), _ptr(workspace_buf), workspace_buf.numel(), _stream(stream))
     native.check(rc)
     return topk_idx, topk_score
+
+
+def tune_autotune(arch, axes, descs, k, reps=3, topk_idx=None, topk_cost=None, workspace_buf=None,
+                  stream=None):
+    """Time tune_eval's candidate schedules on these descriptors; returns
+    (best_flags, best_ms, topk_idx, topk_cost)."""
+    torch = _torch()
+    L = native.load()
+    n = descs.numel() * descs.element_size() // 64
+    dev = descs.device
+    if topk_idx is None:
+        topk_idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+    if topk_cost is None:
+        topk_cost = torch.empty((n, k), dtype=torch.float32, device=dev)
+    if workspace_buf is None:
+        workspace_buf = workspace(native.TUNE_CALL_EVAL, n, k, dev)
+    a = native.make_arch(arch)
+    x = native.make_axes(axes)
+    bf, bms = C.c_uint32(0), C.c_float(0.0)
+    rc = L.tune_autotune(C.byref(a), C.byref(x), _ptr(descs), n, int(k), int(reps), _ptr(topk_idx),
+                         _ptr(topk_cost), _ptr(workspace_buf), workspace_buf.numel(), C.byref(bf),
+                         C.byref(bms), _stream(stream))
+    native.check(rc)
+    return bf.value, bms.value, topk_idx, topk_cost
 
 
 def tune_check(workspace_buf, stream=None):

@@ -41,6 +41,7 @@ struct EvalParams {
     tune_axes x;
     int64_t n_kernels;
     int k;
+    int chunk;  // dynamic work queue: kernels per grab (0 = static stride)
 };
 
 struct CtaTables {
@@ -148,6 +149,108 @@ __device__ void build_cta_tables(const EvalParams& p, CtaTables& ct)
     }
 }
 
+// ---- per-kernel arithmetic shared by both schedules -------------------------
+
+// Per-unroll cost sums in FP32, fixed order (Eq. 6 with c_x = 1 / IPC_x):
+// v_c = n'_c * rcp_c (n'_BRANCH = n_BRANCH / U), compensated sums over the
+// non-memory classes (FP32, FP64, INT, BRANCH, SFU) and the memory classes
+// (GLDST, SLDST), each scaled by (1 + d) * K.
+__device__ __forceinline__ void unit_costs(const float (&n)[7], float d, int U, const float* rcp,
+                                           int work_scale, float& cnm, float& cm)
+{
+    float vv[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        const float nc = c == CL_BRANCH ? __fdiv_rn(n[c], (float)U) : n[c];
+        vv[c] = __fmul_rn(nc, rcp[c]);
+    }
+    const float nm[5] = {vv[CL_FP32], vv[CL_FP64], vv[CL_INT], vv[CL_BRANCH], vv[CL_SFU]};
+    const float mm[2] = {vv[CL_GLDST], vv[CL_SLDST]};
+    const float dk = __fmul_rn(__fadd_rn(1.0f, d), (float)work_scale);
+    cnm = __fmul_rn(neumaier(nm), dk);
+    cm = __fmul_rn(neumaier(mm), dk);
+}
+
+// Per-warp register allocation (Eq. 4): registers per warp rounded to the
+// allocation unit; warps the register file holds, rounded down to the warp
+// allocation granularity and clamped to kMaxW; the largest W_B whose block
+// fits the per-block register limit.
+__device__ __forceinline__ void reg_params(const tune_arch& a, int R, int& warps, int& wbmax)
+{
+    warps = 0;
+    wbmax = 0;
+    if (a.reg_alloc_mode == 0 && R > 0 && R <= a.regs_thread_max) {
+        const int rpw = ceil_div(R * 32, a.reg_alloc_unit) * a.reg_alloc_unit;
+        wbmax = a.regs_block_max / rpw;
+        warps = min((a.regs_sm / rpw) / a.warp_alloc_gran * a.warp_alloc_gran, kMaxW);
+    }
+}
+
+// G_R (Eq. 4) for R registers and blocks of W_B warps (t position tp).
+__device__ __forceinline__ int reg_blocks(const tune_arch& a, const CtaTables& ct, int R, int wb, int tp,
+                                          int warps, int wbmax)
+{
+    if (R > a.regs_thread_max) return 0;
+    if (R <= 0) return a.max_blocks_sm;
+    if (a.reg_alloc_mode == 0) return wb > wbmax ? 0 : ct.divt[warps][tp];
+    const long long rpb = (long long)ceil_div(R * 32 * wb, a.reg_alloc_unit) * a.reg_alloc_unit;
+    return rpb > a.regs_block_max ? 0 : (int)(a.regs_sm / rpb);
+}
+
+// G_S (Eq. 5) for s0 bytes of shared memory per block at carveout C percent.
+__device__ __forceinline__ int smem_blocks(const tune_arch& a, int s0, int C)
+{
+    if (s0 > a.smem_block_max) return 0;
+    const int s_alloc = ceil_div(s0 + a.smem_reserved_block, a.smem_alloc_unit) * a.smem_alloc_unit;
+    if (s_alloc == 0) return a.max_blocks_sm;
+    const int max_cap = a.smem_caps[a.n_smem_caps - 1];
+    for (int i = 0; i < a.n_smem_caps; ++i) {
+        const int ci = a.smem_caps[i];
+        if (100LL * ci >= (long long)C * max_cap && ci >= s_alloc) return ci / s_alloc;
+    }
+    return 0;
+}
+
+// Descriptor fields of kernel kid, read as four 16-byte words.
+struct Desc {
+    float n[7];
+    int r0, s0;
+    float d;
+    uint32_t tm, gm, um, cm, top;
+};
+
+__device__ __forceinline__ void unpack(const int4 (&v)[4], Desc& k)
+{
+    k.n[0] = __int_as_float(v[0].x);
+    k.n[1] = __int_as_float(v[0].y);
+    k.n[2] = __int_as_float(v[0].z);
+    k.n[3] = __int_as_float(v[0].w);
+    k.n[4] = __int_as_float(v[1].x);
+    k.n[5] = __int_as_float(v[1].y);
+    k.n[6] = __int_as_float(v[1].z);
+    k.r0 = v[1].w;
+    k.s0 = v[2].x;
+    k.d = __int_as_float(v[2].y);
+    const uint32_t mlo = (uint32_t)v[2].z, mhi = (uint32_t)v[2].w;
+    k.tm = mlo;
+    k.gm = mhi & 0xffffu;
+    k.um = (mhi >> 16) & 0xffu;
+    k.cm = (mhi >> 24) & 0xfu;
+    k.top = mhi >> 28;
+}
+
+// Malformed descriptor: mask outside the axes, or a field out of range.
+__device__ __forceinline__ bool desc_bad(const Desc& k, const tune_axes& x)
+{
+    const uint32_t t_ok = x.n_t == 32 ? 0xffffffffu : ((1u << x.n_t) - 1u);
+    const uint32_t g_ok = (1u << x.n_g) - 1u, u_ok = (1u << x.n_u) - 1u, c_ok = (1u << x.n_c) - 1u;
+    bool bad = k.top != 0 || (k.tm & ~t_ok) || (k.gm & ~g_ok) || (k.um & ~u_ok) || (k.cm & ~c_ok) ||
+               k.r0 < 0 || k.r0 >= (1 << 24) || k.s0 < 0 || k.s0 >= (1 << 30) || !(k.d >= 0.0f);
+#pragma unroll
+    for (int c = 0; c < 7; ++c) bad = bad || !(k.n[c] >= 0.0f);
+    return bad;
+}
+
 // Sorted insert of (c, i) into a lane's register list (ascending; strict "<"
 // keeps earlier = lower-index entries first among equal costs).
 // (cost, index) keys ordered lexicographically; costs are >= 0, so their bit
@@ -186,7 +289,7 @@ __global__ void __maxnreg__(64)
                      int32_t* __restrict__ topk_idx, float* __restrict__ topk_cost,
                      int32_t* __restrict__ pt_b, int32_t* __restrict__ pt_w,
                      float* __restrict__ pt_c, const int64_t* __restrict__ pt_off,
-                     int* __restrict__ status)
+                     int* __restrict__ status, unsigned long long* __restrict__ queue)
 {
     __shared__ CtaTables ct;
     __shared__ WarpTables wts[kWarps];
@@ -199,33 +302,39 @@ __global__ void __maxnreg__(64)
     WarpTables& w = wts[threadIdx.x >> 5];
     const float kInf = __int_as_float(0x7f800000);
     const int k = p.k;
-    const uint32_t t_ok = x.n_t == 32 ? 0xffffffffu : ((1u << x.n_t) - 1u);
-    const uint32_t g_ok = (1u << x.n_g) - 1u, u_ok = (1u << x.n_u) - 1u, c_ok = (1u << x.n_c) - 1u;
+    const uint32_t g_ok = (1u << x.n_g) - 1u;
 
-    for (int64_t kid = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); kid < p.n_kernels;
-         kid += (int64_t)gridDim.x * kWarps) {
+    // Work distribution: a static stride over descriptors, or (chunk > 0) a queue
+    // from which each warp takes `chunk` consecutive descriptors at a time.
+    const int64_t stride = (int64_t)gridDim.x * kWarps;
+    int64_t kid = p.chunk == 0 ? (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5) - stride : 0;
+    int64_t q_end = 0;  // queue mode: the first ++kid (= 1) is not below q_end, so a grab follows
+    auto next_kernel = [&]() -> bool {
+        if (p.chunk == 0) {
+            kid += stride;
+            return kid < p.n_kernels;
+        }
+        if (++kid < q_end) return true;
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(queue, (unsigned long long)p.chunk);
+        b = __shfl_sync(kFull, b, 0);
+        kid = (int64_t)b;
+        q_end = min(kid + p.chunk, p.n_kernels);
+        return kid < p.n_kernels;
+    };
+    while (next_kernel()) {
         // ---- descriptor: lanes 0..3 load the four 16-byte words, then broadcast.
-        int4 v = __ldg(descs + kid * 4 + (lane & 3));
-        float n[7];
-        n[0] = __int_as_float(__shfl_sync(kFull, v.x, 0));
-        n[1] = __int_as_float(__shfl_sync(kFull, v.y, 0));
-        n[2] = __int_as_float(__shfl_sync(kFull, v.z, 0));
-        n[3] = __int_as_float(__shfl_sync(kFull, v.w, 0));
-        n[4] = __int_as_float(__shfl_sync(kFull, v.x, 1));
-        n[5] = __int_as_float(__shfl_sync(kFull, v.y, 1));
-        n[6] = __int_as_float(__shfl_sync(kFull, v.z, 1));
-        const int r0 = __shfl_sync(kFull, v.w, 1);
-        const int s0 = __shfl_sync(kFull, v.x, 2);
-        const float d = __int_as_float(__shfl_sync(kFull, v.y, 2));
-        const uint32_t mlo = (uint32_t)__shfl_sync(kFull, v.z, 2);
-        const uint32_t mhi = (uint32_t)__shfl_sync(kFull, v.w, 2);
-
-        const uint32_t tm = mlo, gm = mhi & 0xffffu, um = (mhi >> 16) & 0xffu, cm = (mhi >> 24) & 0xfu;
-        bool bad = (mhi >> 28) != 0 || (tm & ~t_ok) || (gm & ~g_ok) || (um & ~u_ok) ||
-                   (cm & ~c_ok) || r0 < 0 || r0 >= (1 << 24) || s0 < 0 || s0 >= (1 << 30) ||
-                   !(d >= 0.0f);
+        const int4 v = __ldg(descs + kid * 4 + (lane & 3));
+        int4 vw[4];
 #pragma unroll
-        for (int c = 0; c < 7; ++c) bad = bad || !(n[c] >= 0.0f);
+        for (int q = 0; q < 4; ++q)
+            vw[q] = make_int4(__shfl_sync(kFull, v.x, q), __shfl_sync(kFull, v.y, q),
+                              __shfl_sync(kFull, v.z, q), __shfl_sync(kFull, v.w, q));
+        Desc kd;
+        unpack(vw, kd);
+        const int r0 = kd.r0, s0 = kd.s0;
+        const uint32_t tm = kd.tm, gm = kd.gm, um = kd.um, cm = kd.cm;
+        const bool bad = desc_bad(kd, x);
         const int nT = __popc(tm), nG = __popc(gm), nU = __popc(um), nC = __popc(cm);
         if (bad || nT * nG * nU * nC == 0) {
             if (bad && lane == 0) atomicOr(status, tune::kStatusInvalid);
@@ -245,49 +354,12 @@ __global__ void __maxnreg__(64)
             const int ur = __popc(um & below);
             const int U = x.u[lane];
             const int R = r0 + 4 * (U - 1);
-            float vv[7];
-#pragma unroll
-            for (int c = 0; c < 7; ++c) {
-                float nc = c == CL_BRANCH ? __fdiv_rn(n[c], (float)U) : n[c];
-                vv[c] = __fmul_rn(nc, ct.rcp[c]);
-            }
-            const float nm[5] = {vv[CL_FP32], vv[CL_FP64], vv[CL_INT], vv[CL_BRANCH], vv[CL_SFU]};
-            const float mm[2] = {vv[CL_GLDST], vv[CL_SLDST]};
-            const float dk = __fmul_rn(__fadd_rn(1.0f, d), (float)a.work_scale);
-            w.cnm[ur] = __fmul_rn(neumaier(nm), dk);
-            w.cm[ur] = __fmul_rn(neumaier(mm), dk);
+            unit_costs(kd.n, kd.d, U, ct.rcp, a.work_scale, w.cnm[ur], w.cm[ur]);
             w.regs[ur] = R;
             w.upos[ur] = lane;
-            int warps = 0, wbmax = 0;
-            if (a.reg_alloc_mode == 0 && R > 0 && R <= a.regs_thread_max) {
-                const int rpw = ceil_div(R * 32, a.reg_alloc_unit) * a.reg_alloc_unit;
-                wbmax = a.regs_block_max / rpw;
-                warps = (a.regs_sm / rpw) / a.warp_alloc_gran * a.warp_alloc_gran;
-                warps = min(warps, kMaxW);
-            }
-            w.warps_r[ur] = warps;
-            w.wb_max[ur] = wbmax;
+            reg_params(a, R, w.warps_r[ur], w.wb_max[ur]);
         }
-        if (lane < 4 && ((cm >> lane) & 1u)) {
-            const int C = x.c[lane];
-            int gs = 0;
-            if (s0 <= a.smem_block_max) {
-                const int s_alloc =
-                    ceil_div(s0 + a.smem_reserved_block, a.smem_alloc_unit) * a.smem_alloc_unit;
-                const int max_cap = a.smem_caps[a.n_smem_caps - 1];
-                int cap = -1;
-                for (int i = 0; i < a.n_smem_caps; ++i) {
-                    const int ci = a.smem_caps[i];
-                    if (100LL * ci >= (long long)C * max_cap && ci >= s_alloc) {
-                        cap = ci;
-                        break;
-                    }
-                }
-                if (s_alloc == 0) gs = a.max_blocks_sm;
-                else if (cap >= 0) gs = cap / s_alloc;
-            }
-            w.gs[__popc(cm & below)] = gs;
-        }
+        if (lane < 4 && ((cm >> lane) & 1u)) w.gs[__popc(cm & below)] = smem_blocks(a, s0, x.c[lane]);
         __syncwarp();
         // ---- (T, U) block limit min(G_W, G_R); lane = t rank.
         if (lane < nT) {
@@ -295,15 +367,7 @@ __global__ void __maxnreg__(64)
             const int wb = ct.wb[tp];
             const int gw = ct.gw[tp];
             for (int ur = 0; ur < nU; ++ur) {
-                const int R = w.regs[ur];
-                int gr;
-                if (R > a.regs_thread_max) gr = 0;
-                else if (R <= 0) gr = a.max_blocks_sm;
-                else if (a.reg_alloc_mode == 0) gr = wb > w.wb_max[ur] ? 0 : ct.divt[w.warps_r[ur]][tp];
-                else {
-                    const long long rpb = (long long)ceil_div(R * 32 * wb, a.reg_alloc_unit) * a.reg_alloc_unit;
-                    gr = rpb > a.regs_block_max ? 0 : (int)(a.regs_sm / rpb);
-                }
+                const int gr = reg_blocks(a, ct, w.regs[ur], wb, tp, w.warps_r[ur], w.wb_max[ur]);
                 w.gwr[lane][ur] = (unsigned char)min(gw, gr);
             }
         }
@@ -491,9 +555,260 @@ __global__ void __maxnreg__(64)
     }
 }
 
+// ---- thread-per-kernel schedule ---------------------------------------------
+//
+// One thread evaluates one kernel descriptor: per-unroll tables in shared
+// memory (one column per thread), per-carveout limits packed in a register,
+// then a bound pre-pass and the main pass over (T, U, C) triples with every
+// grid size's cost computed. The thread keeps a sorted register list of its k
+// best (cost, index); no warp collectives are involved, so kernels of any
+// space size run without per-kernel warp overhead.
+
+constexpr int kThreadsT = 128;
+
+template <int KMAX>
+__device__ __forceinline__ void tlist_insert(float (&lc)[KMAX], int (&li)[KMAX], float c, int i)
+{
+#pragma unroll
+    for (int j = KMAX - 1; j > 0; --j) {
+        const bool shift = key_less(c, i, lc[j - 1], li[j - 1]);
+        const bool here = !shift && key_less(c, i, lc[j], li[j]);
+        const float nc = shift ? lc[j - 1] : (here ? c : lc[j]);
+        const int ni = shift ? li[j - 1] : (here ? i : li[j]);
+        lc[j] = nc;
+        li[j] = ni;
+    }
+    if (key_less(c, i, lc[0], li[0])) {
+        lc[0] = c;
+        li[0] = i;
+    }
+}
+
+template <int KMAX, typename V>
+__device__ __forceinline__ V list_kth(const V (&l)[KMAX], int k)
+{
+    // Select chain (not l[k - 1], which would force the list into local memory).
+    V t = l[KMAX - 1];
+#pragma unroll
+    for (int j = KMAX - 2; j >= 0; --j) t = (j >= k - 1) ? l[j] : t;
+    return t;
+}
+
+// Sorted insert of a value into an ascending list, dropping the largest.
+template <int KMAX>
+__device__ __forceinline__ void value_insert(float (&l)[KMAX], float v)
+{
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        const float lo = fminf(l[j], v);
+        v = fmaxf(l[j], v);
+        l[j] = lo;
+    }
+}
+
+template <int KMAX>
+__global__ void __maxnreg__(KMAX > 8 ? 128 : 96)
+    tune_eval_thread_kernel(const __grid_constant__ EvalParams p, const int4* __restrict__ descs,
+                            int32_t* __restrict__ topk_idx, float* __restrict__ topk_cost,
+                            int* __restrict__ status)
+{
+    __shared__ CtaTables ct;
+    __shared__ float4 utab[8][kThreadsT];  // per unroll position: C_nm, C_m, R, warps | wbmax << 8
+    build_cta_tables(p, ct);
+    __syncthreads();
+
+    const tune_arch& a = p.a;
+    const tune_axes& x = p.x;
+    const float kInf = __int_as_float(0x7f800000);
+    const int k = p.k;
+    const int tid = threadIdx.x;
+    const uint32_t g_all = (1u << x.n_g) - 1u;
+
+    for (int64_t kid = (int64_t)blockIdx.x * kThreadsT + tid; kid < p.n_kernels;
+         kid += (int64_t)gridDim.x * kThreadsT) {
+        int4 vw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) vw[q] = __ldg(descs + kid * 4 + q);
+        Desc kd;
+        unpack(vw, kd);
+        const uint32_t tm = kd.tm, gm = kd.gm, um = kd.um, cm = kd.cm;
+        const bool bad = desc_bad(kd, x);
+        const int nT = __popc(tm), nG = __popc(gm), nU = __popc(um), nC = __popc(cm);
+        if (bad || nT * nG * nU * nC == 0) {
+            if (bad) atomicOr(status, tune::kStatusInvalid);
+            for (int j = 0; j < k; ++j) {
+                topk_idx[kid * k + j] = -1;
+                topk_cost[kid * k + j] = kInf;
+            }
+            continue;
+        }
+        const int nUC = nU * nC;
+        const int g_stride = nG * nUC;
+        const bool g_dense = gm == g_all;
+
+        // ---- per-unroll and per-carveout tables
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if ((um >> u) & 1u) {
+                const int U = x.u[u];
+                const int R = kd.r0 + 4 * (U - 1);
+                float cnm, cmv;
+                unit_costs(kd.n, kd.d, U, ct.rcp, a.work_scale, cnm, cmv);
+                int warps, wbmax;
+                reg_params(a, R, warps, wbmax);
+                utab[u][tid] = make_float4(cnm, cmv, __int_as_float(R),
+                                           __int_as_float(warps | (min(wbmax, 255) << 8)));
+            }
+        }
+        uint32_t gsp = 0;  // G_S per carveout position, one byte each
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if ((cm >> c) & 1u) gsp |= (uint32_t)min(smem_blocks(a, kd.s0, x.c[c]), 255) << (8 * c);
+
+        // ---- loop nest over the triples in canonical (T, U, C) order; body(B, W, X, base)
+        auto for_triples = [&](auto&& body) {
+            int t_r = 0;
+            for (uint32_t tb = tm; tb; tb &= tb - 1u, ++t_r) {
+                const int tp = __ffs(tb) - 1;
+                const int wb = ct.wb[tp], gw = ct.gw[tp];
+                const float ln = ct.lane[tp];
+                int u_r = 0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (!((um >> u) & 1u)) continue;
+                    const float4 ut = utab[u][tid];
+                    const int wr = __float_as_int(ut.w);
+                    const int bu = min(gw, reg_blocks(a, ct, __float_as_int(ut.z), wb, tp, wr & 0xff, wr >> 8));
+                    int c_r = 0;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if (!((cm >> c) & 1u)) continue;
+                        const int B = min(bu, (int)((gsp >> (8 * c)) & 0xffu));
+                        if (B > 0) {
+                            const int W = B * wb;
+                            const float X = __fmul_rn(__fmaf_rn(ut.y, ct.hide[W], ut.x), ln);
+                            body(B, X, t_r * g_stride + u_r * nC + c_r);
+                        }
+                        ++c_r;
+                    }
+                    ++u_r;
+                }
+            }
+        };
+
+        // ---- pre-pass: tau0 = k-th smallest triple minimum (k distinct triples each
+        // own a point of cost <= tau0, so the k-th best point is <= tau0).
+        float tk[KMAX];
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) tk[j] = kInf;
+        float tau0 = kInf;
+        for_triples([&](int B, float X, int) {
+            float mn;
+            if (g_dense) {
+                mn = ct.iparmin[B - 1];
+            } else {
+                mn = kInf;
+                for (uint32_t gb = gm; gb; gb &= gb - 1u) mn = fminf(mn, ct.ipar[B - 1][__ffs(gb) - 1]);
+            }
+            const float m = __fmul_rn(X, mn);
+            if (m < tau0) {
+                value_insert<KMAX>(tk, m);
+                tau0 = list_kth<KMAX>(tk, k);
+            }
+        });
+
+        // ---- main pass: every point's cost, folded into its triple's minimum;
+        // points that can still enter the list are inserted exactly.
+        float lc[KMAX];
+        int li[KMAX];
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) {
+            lc[j] = kInf;
+            li[j] = -1;
+        }
+        float thr_c = kInf;
+        int thr_i = -1;
+        for_triples([&](int B, float X, int base) {
+            if (g_dense) {
+                const float4* row = reinterpret_cast<const float4*>(ct.ipar[B - 1]);
+                float c[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 f = row[q];
+                    c[4 * q + 0] = __fmul_rn(X, f.x);
+                    c[4 * q + 1] = __fmul_rn(X, f.y);
+                    c[4 * q + 2] = __fmul_rn(X, f.z);
+                    c[4 * q + 3] = __fmul_rn(X, f.w);
+                }
+                const float m01 = fminf(fminf(c[0], c[1]), fminf(c[2], c[3]));
+                const float m23 = fminf(fminf(c[4], c[5]), fminf(c[6], c[7]));
+                const float m45 = fminf(fminf(c[8], c[9]), fminf(c[10], c[11]));
+                const float m67 = fminf(fminf(c[12], c[13]), fminf(c[14], c[15]));
+                const float cmin = fminf(fminf(m01, m23), fminf(m45, m67));
+                if (cmin <= fminf(thr_c, tau0)) {
+                    // grid sizes in increasing cost: the order of ipar(B*, G) over G
+#pragma unroll 1
+                    for (int r = 0; r < x.n_g; ++r) {
+                        const int g = ct.perm[B - 1][r];
+                        const float cg = __fmul_rn(X, ct.ipar[B - 1][g]);
+                        if (cg > fminf(thr_c, tau0)) break;
+                        const int idx = base + g * nUC;
+                        if (key_less(cg, idx, thr_c, thr_i)) {
+                            tlist_insert<KMAX>(lc, li, cg, idx);
+                            thr_c = list_kth<KMAX>(lc, k);
+                            thr_i = list_kth<KMAX>(li, k);
+                        }
+                    }
+                }
+            } else {
+                int g_r = 0;
+                for (uint32_t gb = gm; gb; gb &= gb - 1u, ++g_r) {
+                    const float cg = __fmul_rn(X, ct.ipar[B - 1][__ffs(gb) - 1]);
+                    if (cg <= fminf(thr_c, tau0)) {
+                        const int idx = base + g_r * nUC;
+                        if (key_less(cg, idx, thr_c, thr_i)) {
+                            tlist_insert<KMAX>(lc, li, cg, idx);
+                            thr_c = list_kth<KMAX>(lc, k);
+                            thr_i = list_kth<KMAX>(li, k);
+                        }
+                    }
+                }
+            }
+        });
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) {
+            if (j < k) {
+                topk_idx[kid * k + j] = li[j];
+                topk_cost[kid * k + j] = lc[j];
+            }
+        }
+    }
+}
+
+template <int KMAX>
+int launch_thread(const EvalParams& p, const tune_kernel_desc* descs, int32_t* ti, float* tc, int* status,
+                  cudaStream_t s)
+{
+    auto kern = tune_eval_thread_kernel<KMAX>;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        TUNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsT, 0),
+                      "tune_eval: occupancy query");
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int sms = tune::device_sm_count();
+    if (sms <= 0) return tune::fail(TUNE_ECUDA, "tune_eval: cannot query the SM count");
+    const int64_t need = (p.n_kernels + kThreadsT - 1) / kThreadsT;
+    const int64_t cap = (int64_t)sms * per_sm;
+    const int grid = (int)(need < cap ? need : cap);
+    kern<<<grid, kThreadsT, 0, s>>>(p, reinterpret_cast<const int4*>(descs), ti, tc, status);
+    TUNE_CUDA_TRY(cudaGetLastError(), "tune_eval: kernel launch");
+    return TUNE_OK;
+}
+
 template <bool EMIT>
 int launch(const EvalParams& p, const tune_kernel_desc* descs, int32_t* ti, float* tc, int32_t* pb,
-           int32_t* pw, float* pc, const int64_t* po, int* status, cudaStream_t s)
+           int32_t* pw, float* pc, const int64_t* po, int* status, cudaStream_t s, int ctas_per_sm = 0)
 {
     auto kern = tune_eval_kernel<EMIT>;
     static int per_sm = 0;
@@ -505,10 +820,12 @@ int launch(const EvalParams& p, const tune_kernel_desc* descs, int32_t* ti, floa
     const int sms = tune::device_sm_count();
     if (sms <= 0) return tune::fail(TUNE_ECUDA, "tune_eval: cannot query the SM count");
     const int64_t need = (p.n_kernels + kWarps - 1) / kWarps;
-    const int64_t cap = (int64_t)sms * per_sm;
+    const int64_t cap = (int64_t)sms * (ctas_per_sm > 0 ? min(ctas_per_sm, per_sm) : per_sm);
     const int grid = (int)(need < cap ? need : cap);
+    // The queue counter is the second 8-byte word of the zeroed workspace header.
+    unsigned long long* queue = reinterpret_cast<unsigned long long*>(status) + 1;
     kern<<<grid, kThreads, 0, s>>>(p, reinterpret_cast<const int4*>(descs), ti, tc, pb, pw, pc, po,
-                                   status);
+                                   status, queue);
     TUNE_CUDA_TRY(cudaGetLastError(), "tune_eval: kernel launch");
     return TUNE_OK;
 }
@@ -576,9 +893,19 @@ extern "C" int tune_eval(const tune_arch* arch, const tune_axes* axes, const tun
         return tune::fail(TUNE_EINVAL, "descs, topk_idx and topk_cost must be non-NULL");
     if ((reinterpret_cast<uintptr_t>(descs) & 15) != 0)
         return tune::fail(TUNE_EINVAL, "descs must be 16-byte aligned");
-    if (flags & ~TUNE_EMIT_POINTS) return tune::fail(TUNE_EINVAL, "unknown flags 0x%x", flags);
+    if (flags & ~(TUNE_EMIT_POINTS | TUNE_SCHED_WARP | TUNE_SCHED_THREAD | 0xff00u))
+        return tune::fail(TUNE_EINVAL, "unknown flags 0x%x", flags);
+    const int chunk_code = (int)((flags >> 8) & 0xfu);
+    if (chunk_code > 15) return tune::fail(TUNE_EINVAL, "bad chunk code");
+    const int chunk = chunk_code == 0 ? 0 : (1 << (chunk_code - 1));
+    const int ctas_per_sm = (int)((flags >> 12) & 0xfu);
     const bool emit = (flags & TUNE_EMIT_POINTS) != 0;
     if (emit && !pt_offsets) return tune::fail(TUNE_EINVAL, "TUNE_EMIT_POINTS needs pt_offsets");
+    if ((flags & TUNE_SCHED_WARP) && (flags & TUNE_SCHED_THREAD))
+        return tune::fail(TUNE_EINVAL, "TUNE_SCHED_WARP and TUNE_SCHED_THREAD are exclusive");
+    if (emit && (flags & TUNE_SCHED_THREAD))
+        return tune::fail(TUNE_EINVAL, "TUNE_EMIT_POINTS runs on the warp schedule only");
+    const bool thread_sched = (flags & TUNE_SCHED_THREAD) != 0;
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int* status = static_cast<int*>(workspace);
@@ -590,8 +917,14 @@ extern "C" int tune_eval(const tune_arch* arch, const tune_axes* axes, const tun
     p.x = *axes;
     p.n_kernels = n_kernels;
     p.k = k;
-    return emit ? launch<true>(p, descs, topk_idx, topk_cost, pt_blocks, pt_warps, pt_cost, pt_offsets, status, s)
-                : launch<false>(p, descs, topk_idx, topk_cost, nullptr, nullptr, nullptr, nullptr, status, s);
+    p.chunk = chunk;
+    if (thread_sched)
+        return k <= 8 ? launch_thread<8>(p, descs, topk_idx, topk_cost, status, s)
+                      : launch_thread<16>(p, descs, topk_idx, topk_cost, status, s);
+    return emit ? launch<true>(p, descs, topk_idx, topk_cost, pt_blocks, pt_warps, pt_cost, pt_offsets,
+                               status, s, ctas_per_sm)
+                : launch<false>(p, descs, topk_idx, topk_cost, nullptr, nullptr, nullptr, nullptr, status,
+                                s, ctas_per_sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -673,6 +1006,7 @@ extern "C" int tune_eval_noalloc(const tune_arch* arch, const tune_axes* axes,
         p.x = *axes;
         p.n_kernels = n_kernels;
         p.k = k;
+        p.chunk = 0;
         int* status = static_cast<int*>(scratch);
         rc = emit ? launch<true>(p, descs, topk_idx, topk_cost, pt_blocks, pt_warps, pt_cost, pt_offsets, status, s)
                   : launch<false>(p, descs, topk_idx, topk_cost, nullptr, nullptr, nullptr, nullptr, status, s);

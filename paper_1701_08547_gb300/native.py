@@ -15,6 +15,16 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtune.so")
 TUNE_OK, TUNE_EINVAL, TUNE_ENOMEM, TUNE_ECUDA, TUNE_ETIMEOUT, TUNE_ECOMPILE, TUNE_EUNSUPPORTED = (
     0, -1, -2, -3, -4, -5, -6)
 TUNE_EMIT_POINTS = 0x1
+TUNE_SCHED_WARP, TUNE_SCHED_THREAD = 0x10, 0x20
+
+
+def TUNE_SCHED_CHUNK(c):
+    return (c + 1) << 8
+
+
+def TUNE_SCHED_CTAS(m):
+    return m << 12
+
 TUNE_CALL_EVAL, TUNE_CALL_TOPK = 0, 1
 
 ERROR_NAMES = {0: "TUNE_OK", -1: "TUNE_EINVAL", -2: "TUNE_ENOMEM", -3: "TUNE_ECUDA",
@@ -68,6 +78,9 @@ def load():
     L.tune_last_error.restype = C.c_char_p
     L.tune_version.argtypes = []
     L.tune_version.restype = C.c_int
+    L.tune_autotune.argtypes = [C.POINTER(TuneArch), C.POINTER(TuneAxes), vp, i64, i32, i32, vp, vp,
+                                vp, sz, C.POINTER(C.c_uint32), C.POINTER(C.c_float), vp]
+    L.tune_autotune.restype = C.c_int
     _lib = L
     return L
 

@@ -13,6 +13,7 @@ from workloads import archs, gen
 pytestmark = pytest.mark.gpu
 
 REL_TOL_FP64 = 1e-5
+SCHED_WARP, SCHED_THREAD = 0x10, 0x20
 
 
 @pytest.fixture(scope="module")
@@ -47,6 +48,12 @@ def gpu_eval(dev, arch, axes, descs, k, emit=False):
     T.tune_check(ws)
     out["idx"] = idx.cpu().numpy()
     out["cost"] = cost.cpu().numpy()
+    # every schedule must give the same top-k
+    out["sched"] = {}
+    for name, fl in (("warp", SCHED_WARP), ("thread", SCHED_THREAD)):
+        i2, c2 = T.tune_eval(arch, axes, d, k, flags=fl, workspace_buf=ws)
+        T.tune_check(ws)
+        out["sched"][name] = (i2.cpu().numpy(), c2.cpu().numpy())
     if emit:
         out["B"] = kw["pt_blocks"].cpu().numpy()
         out["W"] = kw["pt_warps"].cpu().numpy()
@@ -57,6 +64,9 @@ def gpu_eval(dev, arch, axes, descs, k, emit=False):
 def assert_same_topk(g, o):
     assert np.array_equal(g["idx"], o["idx"]), np.argwhere(g["idx"] != o["idx"])[:5]
     assert np.array_equal(g["cost"].view(np.uint32), o["cost"].view(np.uint32))
+    for name, (gi, gc) in g.get("sched", {}).items():
+        assert np.array_equal(gi, o["idx"]), (name, np.argwhere(gi != o["idx"])[:5])
+        assert np.array_equal(gc.view(np.uint32), o["cost"].view(np.uint32)), name
 
 
 def assert_same_points(g, o):
@@ -182,9 +192,28 @@ def test_full_size_dense_sampled(dev, oracle):
     n = 100_000
     d = gen.descriptors(n, 2, "dense")
     dd = T.descs_to_device(d, dev)
-    idx, cost = T.tune_eval(a, ax, dd, 10)
-    idx, cost = idx.cpu().numpy(), cost.cpu().numpy()
     pick = np.sort(np.random.default_rng(0).choice(n, 300, replace=False))
     o = oracle.evaluate(a, ax, d[pick], 10)
-    assert np.array_equal(idx[pick], o["idx"])
-    assert np.array_equal(cost[pick].view(np.uint32), o["cost"].view(np.uint32))
+    for fl in (0, SCHED_WARP, SCHED_THREAD):
+        idx, cost = T.tune_eval(a, ax, dd, 10, flags=fl)
+        idx, cost = idx.cpu().numpy(), cost.cpu().numpy()
+        assert np.array_equal(idx[pick], o["idx"]), fl
+        assert np.array_equal(cost[pick].view(np.uint32), o["cost"].view(np.uint32)), fl
+
+
+def test_full_size_uneven_sampled(dev, oracle):
+    """1,000,000 kernels with uneven spaces (sizes 48 .. 16,384), top-5; 400 sampled
+    kernels checked against the oracle."""
+    import paper_1701_08547_gb300 as T
+
+    a, ax = archs.arch("sm_103"), gen.axes()
+    n = 1_000_000
+    d = gen.descriptors(n, 3, "uneven")
+    dd = T.descs_to_device(d, dev)
+    pick = np.sort(np.random.default_rng(1).choice(n, 400, replace=False))
+    o = oracle.evaluate(a, ax, d[pick], 5)
+    for fl in (0, SCHED_WARP):
+        idx, cost = T.tune_eval(a, ax, dd, 5, flags=fl)
+        idx, cost = idx.cpu().numpy(), cost.cpu().numpy()
+        assert np.array_equal(idx[pick], o["idx"]), fl
+        assert np.array_equal(cost[pick].view(np.uint32), o["cost"].view(np.uint32)), fl
