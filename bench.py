@@ -36,6 +36,7 @@ WORKLOADS = {
     "dense": (100_000, "dense", 10, 2),
     "dense128": (64, "dense128", 5, 1),
     "uneven": (1_000_000, "uneven", 5, 3),
+    "topk": (100_000, None, 10, 11),
 }
 ISSUE_LANES_PER_SM_CLK = 4 * 32  # 4 schedulers x 32 lanes per SM and clock
 # Algorithmic work per point for the issue roofline: the per-point figure of the
@@ -200,7 +201,9 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
 
     # Schedule: chosen by the library's autotuner on this workload (untimed), or forced.
-    if args.sched == "auto":
+    if args.flags:
+        sched, tuned_ms = int(args.flags, 16), None
+    elif args.sched == "auto":
         sched, tuned_ms, _, _ = T.tune_autotune(a, ax, d_dev, k, reps=3, topk_idx=topi, topk_cost=topc,
                                                 workspace_buf=ws, stream=stream)
     else:
@@ -300,7 +303,8 @@ def run_ours(args):
                    "kernels_per_gpu": n, "points_per_gpu": points, "k": k,
                    "l2": "flushed between timed steps (256 MB write outside the timed events)",
                    "parallelism": f"replicas x{world} (kernel ranges)",
-                   "schedule_flags": hex(sched), "schedule": "autotuned" if args.sched == "auto" else args.sched,
+                   "schedule_flags": hex(sched),
+                   "schedule": "forced" if args.flags else ("autotuned" if args.sched == "auto" else args.sched),
                    "cuda_graph": graph is not None},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
@@ -317,6 +321,60 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample)
     return line
+
+
+def run_topk(args):
+    """Segmented top-k over external scores: 100,000 segments x 16,384 float32
+    scores (the dense workload's point count), top-10; HBM-bound."""
+    import torch
+
+    import paper_1701_08547_gb300 as T
+    from paper_1701_08547_gb300 import build as B
+
+    rank, world, local = dist_env()
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n_seg = args.kernels or 100_000
+    seg, k = 16384, 10
+    total = n_seg * seg
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)  # seeded log-uniform scores in [1, 1e6], made on the device (6.6 GB)
+    scores = torch.rand(total, generator=g, device=dev, dtype=torch.float32)
+    scores.mul_(float(np.log(1e6))).exp_()
+    off = torch.arange(0, total + 1, seg, dtype=torch.int64, device=dev)
+    ws = T.workspace(1, n_seg, k, dev)
+    oi = torch.empty((n_seg, k), dtype=torch.int32, device=dev)
+    ov = torch.empty((n_seg, k), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        T.tune_topk(scores, off, k, oi, ov, ws, stream)
+    torch.cuda.synchronize()
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+    with ClockSampler(uuid, local) as clk:
+        for i in range(args.steps):
+            st[i].record(stream)
+            T.tune_topk(scores, off, k, oi, ov, ws, stream)
+            en[i].record(stream)
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in zip(st, en)) / args.steps
+    peaks, kind = measured_peaks()
+    nbytes = total * 4 + (n_seg + 1) * 8 + n_seg * k * 8
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"metric": "segmented top-k scores/sec", "value": total / (ms * 1e-3), "unit": "scores/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"topk: {n_seg} segments x {seg} scores, top-{k}",
+                       "l2": f"input {nbytes / 1e9:.1f} GB, larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs", 6800.0),
+                         "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                         "peak_source": kind},
+            "clocks": clk.summary(), "gpu_launches": args.steps}
 
 
 def cpu_baseline(workload, sample):
@@ -392,11 +450,17 @@ def main():
     p.add_argument("--kernels", type=int, default=0, help="override the kernel count (small ncu cases)")
     p.add_argument("--sched", choices=["auto", "warp", "thread"], default="auto")
     p.add_argument("--no-graph", action="store_true", help="plain launches instead of graph replays")
+    p.add_argument("--flags", default="", help="tune_eval schedule flags in hex (skips the autotuner)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    elif args.workload == "topk":
+        line = run_topk(args)
+    else:
+        line = run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
 
