@@ -210,6 +210,52 @@ int tune_topk(const float* scores, const int64_t* seg_offsets, int64_t n_seg, in
               int32_t* topk_idx, float* topk_score, void* workspace, size_t ws_bytes,
               tune_stream_t stream);
 
+/* ---- learned surrogate (Section VII: machine learning for the static models) ----
+ *
+ * An ensemble of MLPs predicting ln(runtime in microseconds) of a tuning
+ * point from 48 static features (zero-padded to 128 inputs): 128 -> 256 ->
+ * 256 -> 256 -> 256 -> 1 with exact GELU, BF16 weights and activations, FP32
+ * accumulation, FP32 master weights, Adam, MSE loss. All members are trained
+ * together on the same batches by the library's BF16 tensor-core kernels.
+ * Unlike the tune_* calls, a surrogate handle owns device memory (weights,
+ * optimiser state, activations for one batch), allocated by
+ * surrogate_create and released by surrogate_free. Feature arrays are BF16
+ * (uint16_t bit patterns), [n, 128], row-major, device.
+ *
+ * Parameter layout per member (floats; surrogate_param_count() per member,
+ * members back to back): W1 [256 x 128] at 0, b1 [256] at 32768, W2 at 33024,
+ * b2 at 98560, W3 at 98816, b3 at 164352, W4 at 164608, b4 at 230144,
+ * w5 [256] at 230400, b5 at 230656; W[o][i] row-major (output-major).
+ */
+typedef struct tune_surrogate tune_surrogate;
+typedef struct tune_surrogate_cfg {
+    int32_t members; /* ensemble size, 1..16 */
+    int32_t batch;   /* rows per training step, multiple of 128, <= 65536 */
+    float lr, beta1, beta2, eps; /* Adam */
+} tune_surrogate_cfg;
+
+int surrogate_create(tune_surrogate** h, const tune_surrogate_cfg* cfg);
+void surrogate_free(tune_surrogate* h);
+/* Floats per member in the parameter layout. */
+int surrogate_param_count(void);
+/* Copy master weights (host, members x surrogate_param_count() floats); resets Adam. Synchronous. */
+int surrogate_set_params(tune_surrogate* h, const float* host, int64_t n);
+/* Copy to host: what = 0 master weights, 1 gradients of the last step, 2 Adam m, 3 Adam v
+ * (members x param_count floats), 4 last loss per member (members floats), 5 last
+ * predictions (members x batch). Synchronous. */
+int surrogate_get(tune_surrogate* h, int what, float* host, int64_t n);
+/* pred (device, [members, n]) = each member's output for feats (device bf16 [n, 128]). */
+int surrogate_forward(tune_surrogate* h, const uint16_t* feats, int64_t n, float* pred, tune_stream_t stream);
+/* One step on rows feats[0..n), labels[0..n) (device), 1 <= n <= batch: forward, MSE
+ * loss, backward into the gradient buffer, and (apply_update != 0) one Adam step. */
+int surrogate_train_step(tune_surrogate* h, const uint16_t* feats, const float* labels, int64_t n,
+                         int32_t apply_update, tune_stream_t stream);
+/* `epochs` passes over n rows in the order given (device int32 [epochs, n], a
+ * permutation of 0..n-1 per epoch), batch rows per step; loss_trace (device,
+ * nullable) receives [epochs, steps, members] losses. */
+int surrogate_train(tune_surrogate* h, const uint16_t* feats, const float* labels, int64_t n,
+                    const int32_t* order, int32_t epochs, float* loss_trace, tune_stream_t stream);
+
 /* Bytes of device workspace the call needs (at least 256). */
 size_t tune_workspace_bytes(int call, int64_t n, int32_t k);
 

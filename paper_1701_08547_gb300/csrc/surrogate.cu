@@ -1,0 +1,502 @@
+// Learned surrogate of the static cost: an ensemble of MLPs
+// (128 inputs = 48 features + zero padding -> 256 -> 256 -> 256 -> 256 -> 1, exact GELU),
+// BF16 weights and activations, FP32 accumulation, FP32 master weights, Adam,
+// trained by this file's kernels (forward, backward, optimiser) on the GPU.
+// Members are batched through the grouped GEMM (blockIdx.z = member).
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
+#include "mlp_gemm.cuh"
+#include "tune_internal.h"
+
+using mlp::GemmArgs;
+
+namespace {
+
+constexpr int IN = 128;     // input width (48 features + zeros)
+constexpr int WID = 256;    // hidden width
+constexpr int NL = 4;       // hidden layers
+constexpr int KSPLIT = 8;   // split-K for weight gradients over the batch
+
+// Per-member parameter layout (floats): W1 [256 x 128], b1, W2..W4 [256 x 256], b2..b4, w5 [256], b5.
+__host__ __device__ constexpr long long fan_in(int l) { return l == 0 ? IN : WID; }
+__host__ __device__ constexpr long long OFF_W(int l) { return l == 0 ? 0 : 33024 + (l - 1) * 65792LL; }
+__host__ __device__ constexpr long long OFF_B(int l) { return OFF_W(l) + WID * fan_in(l); }
+constexpr long long OFF_W5 = 230400, OFF_B5 = 230656;
+constexpr long long P_REAL = 230657;
+constexpr long long P = 230720;  // padded per-member stride
+// bf16 copies of W1..W4 per member
+__host__ __device__ constexpr long long BOFF_W(int l) { return l == 0 ? 0 : 32768 + (l - 1) * 65536LL; }
+constexpr long long PB = 229376;
+static_assert(OFF_B(3) == 230144 && OFF_W5 == OFF_B(3) + WID && BOFF_W(3) + 65536 == PB, "layout");
+
+}  // namespace
+
+struct tune_surrogate {
+    int members = 0, batch = 0;
+    float lr = 1e-3f, b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    int step = 0;
+    float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    __nv_bfloat16* wbf = nullptr;
+    __nv_bfloat16* xin = nullptr;       // [batch x IN]
+    float* Z[NL] = {};                  // [members][batch x WID]
+    __nv_bfloat16* H[NL] = {};          // [members][batch x WID]
+    __nv_bfloat16* dZ[2] = {};          // ping-pong [members][batch x WID]
+    float *y = nullptr, *dy = nullptr, *lbl = nullptr, *loss = nullptr;  // [members][batch] / [members]
+    float* part = nullptr;              // [members][KSPLIT][WID x WID]
+    void* block = nullptr;              // the one device allocation
+};
+
+namespace {
+
+template <typename T>
+T* carve(char*& p, size_t count)
+{
+    T* r = reinterpret_cast<T*>(p);
+    p += (count * sizeof(T) + 255) & ~size_t(255);
+    return r;
+}
+
+// ---- small kernels ------------------------------------------------------------
+
+// y[mem][i] = sum_j w5[j] * H4[mem][i][j] + b5   (one warp per row)
+__global__ void head_fwd(const __nv_bfloat16* __restrict__ H4, const float* __restrict__ master, float* y,
+                         int n, int batch)
+{
+    const int mem = blockIdx.y;
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const float* w5 = master + mem * P + OFF_W5;
+    const __nv_bfloat16* h = H4 + (long long)mem * batch * WID + (long long)row * WID;
+    float s = 0.0f;
+    for (int j = lane; j < WID; j += 32) s = fmaf(w5[j], __bfloat162float(h[j]), s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[(long long)mem * batch + row] = s + master[mem * P + OFF_B5];
+}
+
+// dy = 2 (y - t) / n; loss[mem] = mean (y - t)^2 (one block per member, deterministic)
+__global__ void loss_grad(const float* __restrict__ y, const float* __restrict__ t, float* dy, float* loss, int n,
+                          int batch)
+{
+    const int mem = blockIdx.x;
+    __shared__ float red[256];
+    float s = 0.0f;
+    for (int i = threadIdx.x; i < batch; i += blockDim.x) {
+        float g = 0.0f;
+        if (i < n) {
+            const float e = y[(long long)mem * batch + i] - t[i];
+            s += e * e;
+            g = 2.0f * e / (float)n;
+        }
+        dy[(long long)mem * batch + i] = g;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss) loss[mem] = red[0] / (float)n;
+}
+
+// dZ4[i][j] = bf16(dy[i] * w5[j] * gelu'(Z4[i][j]))
+__global__ void head_bwd_act(const float* __restrict__ dy, const float* __restrict__ master,
+                             const float* __restrict__ Z4, __nv_bfloat16* dZ, int batch)
+{
+    const int mem = blockIdx.y;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)batch * WID) return;
+    const int i = (int)(e / WID), j = (int)(e % WID);
+    const long long o = (long long)mem * batch * WID + e;
+    dZ[o] = __float2bfloat16_rn(dy[(long long)mem * batch + i] * master[mem * P + OFF_W5 + j] *
+                                mlp::gelu_grad(Z4[o]));
+}
+
+// grad w5[j] = sum_i dy[i] H4[i][j]; grad b5 = sum_i dy[i]   (one block of 256 threads per member)
+__global__ void head_bwd_params(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ H4, float* grad,
+                                int rows, int batch)
+{
+    const int mem = blockIdx.x, j = threadIdx.x;
+    const float* d = dy + (long long)mem * batch;
+    const __nv_bfloat16* h = H4 + (long long)mem * batch * WID;
+    float s = 0.0f, sb = 0.0f;
+    for (int i = 0; i < rows; ++i) {
+        s = fmaf(d[i], __bfloat162float(h[(long long)i * WID + j]), s);
+        sb += d[i];
+    }
+    grad[mem * P + OFF_W5 + j] = s;
+    if (j == 0) grad[mem * P + OFF_B5] = sb;
+}
+
+// grad b[j] = sum_i dZ[i][j]   (one block of 256 threads per member)
+__global__ void bias_grad(const __nv_bfloat16* __restrict__ dZ, float* grad, long long off_b, int rows, int batch)
+{
+    const int mem = blockIdx.x, j = threadIdx.x;
+    const __nv_bfloat16* d = dZ + (long long)mem * batch * WID;
+    float s = 0.0f;
+    for (int i = 0; i < rows; ++i) s += __bfloat162float(d[(long long)i * WID + j]);
+    grad[mem * P + off_b + j] = s;
+}
+
+// grad W[o][i] = sum over splits of part[split][o][i]
+__global__ void split_reduce(const float* __restrict__ part, float* grad, long long off_w, int cols, int splits)
+{
+    const int mem = blockIdx.y;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= WID * cols) return;
+    const float* p = part + (long long)mem * KSPLIT * WID * WID;
+    float s = 0.0f;
+    for (int q = 0; q < splits; ++q) s += p[(long long)q * WID * WID + e];
+    grad[mem * P + off_w + e] = s;
+}
+
+// Adam on FP32 master weights, then the BF16 copies of W1..W4.
+__global__ void adam_update(float* master, const float* grad, float* m, float* v, __nv_bfloat16* wbf, int members,
+                            float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)members * P) return;
+    const long long p = e % P;
+    if (p >= P_REAL) return;
+    const float g = grad[e];
+    const float mm = b1 * m[e] + (1.0f - b1) * g;
+    const float vv = b2 * v[e] + (1.0f - b2) * g * g;
+    m[e] = mm;
+    v[e] = vv;
+    const float w = master[e] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+    master[e] = w;
+    const long long mem = e / P;
+    for (int l = 0; l < NL; ++l) {
+        const long long len = WID * fan_in(l);
+        if (p >= OFF_W(l) && p < OFF_W(l) + len) wbf[mem * PB + BOFF_W(l) + (p - OFF_W(l))] = __float2bfloat16_rn(w);
+    }
+}
+
+__global__ void cast_weights(const float* master, __nv_bfloat16* wbf, int members)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)members * PB) return;
+    const long long mem = e / PB, q = e % PB;
+    int l = NL - 1;
+    while (l > 0 && q < BOFF_W(l)) --l;
+    wbf[e] = __float2bfloat16_rn(master[mem * P + OFF_W(l) + (q - BOFF_W(l))]);
+}
+
+// Batch gather: xin[r] = feats[order[r]], lbl[r] = labels[order[r]] (rows past n are zero).
+__global__ void gather_batch(const __nv_bfloat16* __restrict__ feats, const float* __restrict__ labels,
+                             const int32_t* __restrict__ order, int n, int batch, __nv_bfloat16* xin, float* lbl)
+{
+    const int r = blockIdx.x;
+    const int c = threadIdx.x;  // 64 threads x 2 elements
+    const __nv_bfloat162 z = __floats2bfloat162_rn(0.0f, 0.0f);
+    __nv_bfloat162 val = z;
+    if (r < n) {
+        const long long src = order ? order[r] : r;
+        val = reinterpret_cast<const __nv_bfloat162*>(feats + src * IN)[c];
+        if (c == 0) lbl[r] = labels[src];
+    } else if (c == 0) {
+        lbl[r] = 0.0f;
+    }
+    reinterpret_cast<__nv_bfloat162*>(xin + (long long)r * IN)[c] = val;
+}
+
+template <bool A_KM, bool B_KN, int EPI>
+int gemm(const GemmArgs& g, int batches, cudaStream_t s)
+{
+    dim3 grid(g.N / mlp::GBN, g.M / mlp::GBM, batches * g.k_split);
+    mlp::gemm_bf16_kernel<A_KM, B_KN, EPI><<<grid, mlp::kGemmThreads, 0, s>>>(g);
+    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: gemm launch");
+    return TUNE_OK;
+}
+
+GemmArgs gargs()
+{
+    GemmArgs g;
+    memset(&g, 0, sizeof(g));
+    g.k_split = 1;
+    return g;
+}
+
+// Forward through all members for rows [0, n_pad) of h->xin (n_pad a multiple of 128).
+int forward(tune_surrogate* h, int n_pad, cudaStream_t s)
+{
+    for (int l = 0; l < NL; ++l) {
+        GemmArgs g = gargs();
+        g.A = l == 0 ? h->xin : h->H[l - 1];
+        g.sA = l == 0 ? 0 : (long long)h->batch * WID;
+        g.lda = l == 0 ? IN : WID;
+        g.B = h->wbf + BOFF_W(l);
+        g.sB = PB;
+        g.ldb = (int)fan_in(l);
+        g.M = n_pad;
+        g.N = WID;
+        g.K = (int)fan_in(l);
+        g.bias = h->master + OFF_B(l);
+        g.sBias = P;
+        g.Z = h->Z[l];
+        g.sZ = (long long)h->batch * WID;
+        g.H = h->H[l];
+        g.sH = (long long)h->batch * WID;
+        g.ldc = WID;
+        int rc = gemm<false, false, mlp::EPI_BIAS_GELU>(g, h->members, s);
+        if (rc) return rc;
+    }
+    head_fwd<<<dim3((n_pad + 7) / 8, h->members), 256, 0, s>>>(h->H[NL - 1], h->master, h->y, n_pad, h->batch);
+    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: head launch");
+    return TUNE_OK;
+}
+
+// Backward for the batch in h->xin / h->lbl (n valid rows, n_pad rows computed); grads into h->grad.
+int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
+{
+    const int B = h->batch;
+    loss_grad<<<h->members, 256, 0, s>>>(h->y, h->lbl, h->dy, h->loss, n, B);
+    head_bwd_params<<<h->members, WID, 0, s>>>(h->dy, h->H[NL - 1], h->grad, n_pad, B);
+    head_bwd_act<<<dim3((unsigned)(((long long)B * WID + 255) / 256), h->members), 256, 0, s>>>(
+        h->dy, h->master, h->Z[NL - 1], h->dZ[0], B);
+    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: head backward launch");
+    int cur = 0;
+    for (int l = NL - 1; l >= 0; --l) {
+        const __nv_bfloat16* dz = h->dZ[cur];
+        const int kin = (int)fan_in(l);
+        // weight gradient: dW[o][i] = sum_r dZ[r][o] * Hprev[r][i]   (split over the batch)
+        GemmArgs g = gargs();
+        g.A = dz;
+        g.sA = (long long)B * WID;
+        g.lda = WID;
+        g.B = l == 0 ? h->xin : h->H[l - 1];
+        g.sB = l == 0 ? 0 : (long long)B * WID;
+        g.ldb = kin;
+        g.M = WID;
+        g.N = kin;
+        g.K = n_pad;
+        g.F = h->part;
+        g.sF = (long long)KSPLIT * WID * WID;
+        g.ldc = kin;
+        // split the batch (K) so every split is a multiple of 32 rows: n_pad / 32 is a multiple of 4
+        int splits = KSPLIT;
+        while ((n_pad / 32) % splits) splits >>= 1;
+        g.k_split = splits;
+        g.sSplit = (long long)WID * WID;
+        int rc = gemm<true, true, mlp::EPI_F32>(g, h->members, s);
+        if (rc) return rc;
+        split_reduce<<<dim3((WID * kin + 255) / 256, h->members), 256, 0, s>>>(h->part, h->grad, OFF_W(l), kin,
+                                                                               splits);
+        bias_grad<<<h->members, WID, 0, s>>>(dz, h->grad, OFF_B(l), n_pad, B);
+        TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: reduce launch");
+        if (l == 0) break;
+        // input gradient of layer l, times gelu' of layer l-1: dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1})
+        GemmArgs d = gargs();
+        d.A = dz;
+        d.sA = (long long)B * WID;
+        d.lda = WID;
+        d.B = h->wbf + BOFF_W(l);
+        d.sB = PB;
+        d.ldb = kin;
+        d.M = n_pad;
+        d.N = kin;
+        d.K = WID;
+        d.Z = h->Z[l - 1];
+        d.sZ = (long long)B * WID;
+        d.H = h->dZ[cur ^ 1];
+        d.sH = (long long)B * WID;
+        d.ldc = WID;
+        rc = gemm<false, true, mlp::EPI_GELU_GRAD>(d, h->members, s);
+        if (rc) return rc;
+        cur ^= 1;
+    }
+    return TUNE_OK;
+}
+
+int adam(tune_surrogate* h, cudaStream_t s)
+{
+    h->step += 1;
+    const float c1 = 1.0f - powf(h->b1, (float)h->step), c2 = 1.0f - powf(h->b2, (float)h->step);
+    const long long total = (long long)h->members * P;
+    adam_update<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h->master, h->grad, h->m, h->v, h->wbf, h->members,
+                                                                 h->lr, h->b1, h->b2, h->eps, c1, c2);
+    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: adam launch");
+    return TUNE_OK;
+}
+
+int load_batch(tune_surrogate* h, const __nv_bfloat16* feats, const float* labels, const int32_t* order, int n,
+               cudaStream_t s)
+{
+    gather_batch<<<h->batch, IN / 2, 0, s>>>(feats, labels, order, n, h->batch, h->xin, h->lbl);
+    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: gather launch");
+    return TUNE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int surrogate_param_count(void) { return (int)P; }
+
+int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
+{
+    tune::clear_error();
+    if (!out || !cfg) return tune::fail(TUNE_EINVAL, "surrogate_create: NULL argument");
+    if (cfg->members < 1 || cfg->members > 16) return tune::fail(TUNE_EINVAL, "members outside [1, 16]");
+    if (cfg->batch < 128 || cfg->batch % 128 || cfg->batch > (1 << 16))
+        return tune::fail(TUNE_EINVAL, "batch must be a multiple of 128 in [128, 65536]");
+    tune_surrogate* h = new tune_surrogate();
+    h->members = cfg->members;
+    h->batch = cfg->batch;
+    h->lr = cfg->lr;
+    h->b1 = cfg->beta1;
+    h->b2 = cfg->beta2;
+    h->eps = cfg->eps;
+    const size_t M = (size_t)h->members, B = (size_t)h->batch;
+    size_t bytes = 0;
+    auto add = [&](size_t n) { bytes += (n + 255) & ~size_t(255); };
+    for (int i = 0; i < 4; ++i) add(M * P * 4);
+    add(M * PB * 2);
+    add(B * IN * 2);
+    for (int l = 0; l < NL; ++l) add(M * B * WID * 4);
+    for (int l = 0; l < NL; ++l) add(M * B * WID * 2);
+    add(M * B * WID * 2);
+    add(M * B * WID * 2);
+    add(M * B * 4);
+    add(M * B * 4);
+    add(B * 4);
+    add(M * 4);
+    add(M * KSPLIT * WID * WID * 4);
+    cudaError_t e = cudaMalloc(&h->block, bytes);
+    if (e != cudaSuccess) {
+        delete h;
+        return tune::cuda_fail(e, "surrogate_create: cudaMalloc");
+    }
+    cudaMemset(h->block, 0, bytes);
+    char* p = static_cast<char*>(h->block);
+    h->master = carve<float>(p, M * P);
+    h->grad = carve<float>(p, M * P);
+    h->m = carve<float>(p, M * P);
+    h->v = carve<float>(p, M * P);
+    h->wbf = carve<__nv_bfloat16>(p, M * PB);
+    h->xin = carve<__nv_bfloat16>(p, B * IN);
+    for (int l = 0; l < NL; ++l) h->Z[l] = carve<float>(p, M * B * WID);
+    for (int l = 0; l < NL; ++l) h->H[l] = carve<__nv_bfloat16>(p, M * B * WID);
+    h->dZ[0] = carve<__nv_bfloat16>(p, M * B * WID);
+    h->dZ[1] = carve<__nv_bfloat16>(p, M * B * WID);
+    h->y = carve<float>(p, M * B);
+    h->dy = carve<float>(p, M * B);
+    h->lbl = carve<float>(p, B);
+    h->loss = carve<float>(p, M);
+    h->part = carve<float>(p, M * KSPLIT * WID * WID);
+    *out = h;
+    return TUNE_OK;
+}
+
+void surrogate_free(tune_surrogate* h)
+{
+    if (!h) return;
+    if (h->block) cudaFree(h->block);
+    delete h;
+}
+
+int surrogate_set_params(tune_surrogate* h, const float* host, int64_t n)
+{
+    tune::clear_error();
+    if (!h || !host || n != (int64_t)h->members * P) return tune::fail(TUNE_EINVAL, "surrogate_set_params: size");
+    TUNE_CUDA_TRY(cudaMemcpy(h->master, host, n * sizeof(float), cudaMemcpyHostToDevice), "set_params: copy");
+    TUNE_CUDA_TRY(cudaMemset(h->m, 0, n * sizeof(float)), "set_params: reset m");
+    TUNE_CUDA_TRY(cudaMemset(h->v, 0, n * sizeof(float)), "set_params: reset v");
+    h->step = 0;
+    const long long tot = (long long)h->members * PB;
+    cast_weights<<<(unsigned)((tot + 255) / 256), 256>>>(h->master, h->wbf, h->members);
+    TUNE_CUDA_TRY(cudaGetLastError(), "set_params: cast");
+    TUNE_CUDA_TRY(cudaDeviceSynchronize(), "set_params: sync");
+    return TUNE_OK;
+}
+
+int surrogate_get(tune_surrogate* h, int what, float* host, int64_t n)
+{
+    tune::clear_error();
+    if (!h || !host) return tune::fail(TUNE_EINVAL, "surrogate_get: NULL argument");
+    const float* src = what == 0 ? h->master : what == 1 ? h->grad : what == 2 ? h->m : what == 3 ? h->v : nullptr;
+    int64_t cnt = (int64_t)h->members * P;
+    if (what == 4) {
+        src = h->loss;
+        cnt = h->members;
+    }
+    if (what == 5) {
+        src = h->y;
+        cnt = (int64_t)h->members * h->batch;
+    }
+    if (!src || n != cnt) return tune::fail(TUNE_EINVAL, "surrogate_get: bad selector or size");
+    TUNE_CUDA_TRY(cudaDeviceSynchronize(), "surrogate_get: sync");
+    TUNE_CUDA_TRY(cudaMemcpy(host, src, n * sizeof(float), cudaMemcpyDeviceToHost), "surrogate_get: copy");
+    return TUNE_OK;
+}
+
+int surrogate_forward(tune_surrogate* h, const uint16_t* feats, int64_t n, float* pred, tune_stream_t stream)
+{
+    tune::clear_error();
+    if (!h || (n > 0 && (!feats || !pred))) return tune::fail(TUNE_EINVAL, "surrogate_forward: NULL argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const auto* f = reinterpret_cast<const __nv_bfloat16*>(feats);
+    for (int64_t r0 = 0; r0 < n; r0 += h->batch) {
+        const int nb = (int)((n - r0) < h->batch ? (n - r0) : h->batch);
+        const int n_pad = (nb + 127) / 128 * 128;
+        int rc = load_batch(h, f + r0 * IN, h->lbl /*unused labels*/, nullptr, nb, s);
+        if (rc) return rc;
+        rc = forward(h, n_pad, s);
+        if (rc) return rc;
+        for (int mem = 0; mem < h->members; ++mem)
+            TUNE_CUDA_TRY(cudaMemcpyAsync(pred + mem * n + r0, h->y + (long long)mem * h->batch, nb * sizeof(float),
+                                          cudaMemcpyDeviceToDevice, s),
+                          "surrogate_forward: copy out");
+    }
+    return TUNE_OK;
+}
+
+int surrogate_train_step(tune_surrogate* h, const uint16_t* feats, const float* labels, int64_t n,
+                         int32_t apply_update, tune_stream_t stream)
+{
+    tune::clear_error();
+    if (!h || !feats || !labels || n < 1 || n > h->batch)
+        return tune::fail(TUNE_EINVAL, "surrogate_train_step: need 1 <= n <= batch and non-NULL data");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int nb = (int)n, n_pad = (nb + 127) / 128 * 128;
+    int rc = load_batch(h, reinterpret_cast<const __nv_bfloat16*>(feats), labels, nullptr, nb, s);
+    if (!rc) rc = forward(h, n_pad, s);
+    if (!rc) rc = backward(h, nb, n_pad, s);
+    if (!rc && apply_update) rc = adam(h, s);
+    return rc;
+}
+
+int surrogate_train(tune_surrogate* h, const uint16_t* feats, const float* labels, int64_t n,
+                    const int32_t* order, int32_t epochs, float* loss_trace, tune_stream_t stream)
+{
+    tune::clear_error();
+    if (!h || !feats || !labels || !order || n < 1 || epochs < 1)
+        return tune::fail(TUNE_EINVAL, "surrogate_train: bad arguments");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const auto* f = reinterpret_cast<const __nv_bfloat16*>(feats);
+    const int64_t steps = (n + h->batch - 1) / h->batch;
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (int64_t st = 0; st < steps; ++st) {
+            const int64_t r0 = st * h->batch;
+            const int nb = (int)((n - r0) < h->batch ? (n - r0) : h->batch);
+            const int n_pad = (nb + 127) / 128 * 128;
+            int rc = load_batch(h, f, labels, order + (int64_t)ep * n + r0, nb, s);
+            if (!rc) rc = forward(h, n_pad, s);
+            if (!rc) rc = backward(h, nb, n_pad, s);
+            if (!rc) rc = adam(h, s);
+            if (rc) return rc;
+            if (loss_trace)
+                TUNE_CUDA_TRY(cudaMemcpyAsync(loss_trace + ((int64_t)ep * steps + st) * h->members, h->loss,
+                                              h->members * sizeof(float), cudaMemcpyDeviceToDevice, s),
+                              "surrogate_train: loss trace");
+        }
+    }
+    return TUNE_OK;
+}
+
+}  // extern "C"

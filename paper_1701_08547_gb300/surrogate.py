@@ -1,0 +1,106 @@
+"""Binding for the surrogate MLP ensemble calls of libtune.so (argument marshalling only)."""
+
+import ctypes as C
+
+from . import native
+
+
+class Cfg(C.Structure):
+    _fields_ = [("members", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float)]
+
+
+def _lib():
+    L = native.load()
+    if not getattr(L, "_surrogate_declared", False):
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+        L.surrogate_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(Cfg)]
+        L.surrogate_create.restype = C.c_int
+        L.surrogate_free.argtypes = [vp]
+        L.surrogate_free.restype = None
+        L.surrogate_param_count.argtypes = []
+        L.surrogate_param_count.restype = C.c_int
+        L.surrogate_set_params.argtypes = [vp, vp, i64]
+        L.surrogate_set_params.restype = C.c_int
+        L.surrogate_get.argtypes = [vp, C.c_int, vp, i64]
+        L.surrogate_get.restype = C.c_int
+        L.surrogate_forward.argtypes = [vp, vp, i64, vp, vp]
+        L.surrogate_forward.restype = C.c_int
+        L.surrogate_train_step.argtypes = [vp, vp, vp, i64, i32, vp]
+        L.surrogate_train_step.restype = C.c_int
+        L.surrogate_train.argtypes = [vp, vp, vp, i64, vp, i32, vp, vp]
+        L.surrogate_train.restype = C.c_int
+        L._surrogate_declared = True
+    return L
+
+
+def _stream(stream):
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class Surrogate:
+    """A handle to an MLP ensemble living on the GPU."""
+
+    GET_PARAMS, GET_GRADS, GET_M, GET_V, GET_LOSS, GET_PRED = range(6)
+
+    def __init__(self, members=5, batch=8192, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.L = _lib()
+        self.members, self.batch = members, batch
+        cfg = Cfg(members, batch, lr, beta1, beta2, eps)
+        h = C.c_void_p()
+        native.check(self.L.surrogate_create(C.byref(h), C.byref(cfg)))
+        self.h = h
+        self.P = self.L.surrogate_param_count()
+
+    def close(self):
+        if self.h:
+            self.L.surrogate_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        import numpy as np
+
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        native.check(self.L.surrogate_set_params(self.h, a.ctypes.data, a.size))
+
+    def get(self, what):
+        import numpy as np
+
+        n = {4: self.members, 5: self.members * self.batch}.get(what, self.members * self.P)
+        out = np.empty(n, dtype=np.float32)
+        native.check(self.L.surrogate_get(self.h, what, out.ctypes.data, n))
+        return out
+
+    def forward(self, feats, pred=None, stream=None):
+        """feats: device bfloat16 [n, 128]; returns device float32 [members, n]."""
+        import torch
+
+        n = feats.shape[0]
+        if pred is None:
+            pred = torch.empty((self.members, n), dtype=torch.float32, device=feats.device)
+        native.check(self.L.surrogate_forward(self.h, C.c_void_p(feats.data_ptr()), n,
+                                              C.c_void_p(pred.data_ptr()), _stream(stream)))
+        return pred
+
+    def train_step(self, feats, labels, apply_update=True, stream=None):
+        n = feats.shape[0]
+        native.check(self.L.surrogate_train_step(self.h, C.c_void_p(feats.data_ptr()),
+                                                 C.c_void_p(labels.data_ptr()), n, int(apply_update),
+                                                 _stream(stream)))
+
+    def train(self, feats, labels, order, epochs, loss_trace=None, stream=None):
+        n = feats.shape[0]
+        lt = None if loss_trace is None else C.c_void_p(loss_trace.data_ptr())
+        native.check(self.L.surrogate_train(self.h, C.c_void_p(feats.data_ptr()),
+                                            C.c_void_p(labels.data_ptr()), n,
+                                            C.c_void_p(order.data_ptr()), int(epochs), lt,
+                                            _stream(stream)))

@@ -1,0 +1,126 @@
+"""GPU parity of the surrogate MLP kernels (through the C ABI) with the FP64
+oracle that rounds to BF16 where the method stores BF16.
+
+Tolerance: the GPU accumulates in FP32 and evaluates erf/exp in FP32 where
+the oracle uses FP64, so a stored BF16 value can land one BF16 step (2^-8
+relative) away from the oracle's; such flips pass through at most four
+layers. Forward outputs are compared with |dy| <= 2e-2 (1 + |y|), gradients
+by relative Frobenius error per tensor <= 3e-2; Adam, given the same
+gradients, to within FP32 rounding.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import surrogate_oracle as S
+from workloads import mlp as L
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+
+    from paper_1701_08547_gb300 import build
+
+    build.build()
+    assert torch.cuda.is_available()
+    return torch.device("cuda:0")
+
+
+def feats(n, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    X = np.zeros((n, L.IN))
+    X[:, :L.FEATURES] = scale * rng.standard_normal((n, L.FEATURES))
+    return S.bf16(X)
+
+
+def to_dev(X, dev):
+    import torch
+
+    return torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).to(dev)
+
+
+def make(members, batch, seed0=5):
+    from paper_1701_08547_gb300.surrogate import Surrogate
+
+    s = Surrogate(members=members, batch=batch)
+    flat = L.init_params(members, [seed0 + m for m in range(members)])
+    rng = np.random.default_rng(seed0)
+    a = flat.reshape(members, L.P)
+    for l in range(4):  # non-zero biases exercise the bias paths
+        a[:, L.OFF_B[l]:L.OFF_B[l] + L.WID] = 0.1 * rng.standard_normal((members, L.WID))
+    a[:, L.OFF_B5] = 0.25
+    s.set_params(a.ravel())
+    return s, a.ravel()
+
+
+def test_forward_matches_oracle(dev):
+    s, flat = make(2, 512)
+    X = feats(700, 1)
+    pred = s.forward(to_dev(X, dev)).cpu().numpy()
+    for m, p in enumerate(L.unpack(flat, 2)):
+        y, _ = S.forward(p, X, bf=True)
+        err = np.abs(pred[m] - y)
+        assert np.all(err <= 2e-2 * (1 + np.abs(y))), err.max()
+        assert np.median(err) < 2e-3
+
+
+def test_gradients_match_oracle(dev):
+    import torch
+
+    s, flat = make(2, 256)
+    X = feats(200, 2)
+    t = np.random.default_rng(3).standard_normal(200)
+    s.train_step(to_dev(X, dev), torch.tensor(t, dtype=torch.float32, device=dev), apply_update=False)
+    g = s.get(s.GET_GRADS).reshape(2, L.P)
+    loss = s.get(s.GET_LOSS)
+    for m, p in enumerate(L.unpack(flat, 2)):
+        lo, _, gr = S.loss_and_grads(p, X, t, bf=True)
+        assert loss[m] == pytest.approx(lo, rel=2e-2)
+        gm = L.unpack(g[m], 1)[0]
+        for name in gr:
+            want = np.asarray(gr[name], np.float64)
+            got = np.asarray(gm[name], np.float64).reshape(want.shape)
+            rel = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30)
+            assert rel <= 3e-2, (m, name, rel)
+
+
+def test_adam_steps_match_oracle(dev):
+    import torch
+
+    s, flat = make(1, 128)
+    w = flat.astype(np.float64)
+    mm = np.zeros_like(w)
+    vv = np.zeros_like(w)
+    for t in (1, 2):
+        X = feats(128, 10 + t)
+        y = np.random.default_rng(t).standard_normal(128)
+        s.train_step(to_dev(X, dev), torch.tensor(y, dtype=torch.float32, device=dev), apply_update=True)
+        g = s.get(s.GET_GRADS).astype(np.float64)
+        w, mm, vv = S.adam(w, g, mm, vv, t, 1e-3, 0.9, 0.999, 1e-8)
+        w[L.P - 63:] = 0.0  # padding past the last parameter is not updated
+        got = s.get(s.GET_PARAMS).astype(np.float64)
+        assert np.max(np.abs(got - w)) <= 2e-6
+
+
+def test_training_reduces_loss(dev):
+    import torch
+
+    n, members = 16384, 2
+    X = feats(n, 7)
+    t = np.sin(X[:, 0]) + 0.5 * X[:, 1] ** 2 - 0.3 * X[:, 2] * X[:, 3]
+    s, _ = make(members, 1024)
+    Xd = to_dev(X, dev)
+    td = torch.tensor(t, dtype=torch.float32, device=dev)
+    epochs = 15
+    rng = np.random.default_rng(0)
+    order = torch.tensor(np.concatenate([rng.permutation(n) for _ in range(epochs)]), dtype=torch.int32,
+                         device=dev)
+    steps = n // 1024
+    trace = torch.zeros(epochs * steps * members, dtype=torch.float32, device=dev)
+    s.train(Xd, td, order, epochs, trace)
+    tr = trace.cpu().numpy().reshape(epochs, steps, members)
+    assert np.all(np.isfinite(tr))
+    assert tr[-1].mean() < 0.1 * tr[0, 0].mean(), (tr[0, 0], tr[-1].mean())
