@@ -256,6 +256,38 @@ int surrogate_train_step(tune_surrogate* h, const uint16_t* feats, const float* 
 int surrogate_train(tune_surrogate* h, const uint16_t* feats, const float* labels, int64_t n,
                     const int32_t* order, int32_t epochs, float* loss_trace, tune_stream_t stream);
 
+/* Ensemble size of a handle (0 for NULL). */
+int surrogate_members(const tune_surrogate* h);
+
+/*
+ * tune_features — the surrogate's 48 input features (zero-padded to 128 BF16
+ * columns) of listed tuning points: sample i is point sample_point[i]
+ * (canonical index) of descriptor sample_kernel[i]. Features are fixed
+ * scalings of the descriptor, the launch parameters and the occupancy and
+ * cost internals of Eqs. 3-6 (see csrc/features.cuh for the list). feats:
+ * device BF16 [n, 128]. Invalid samples set TUNE_EINVAL in the status word.
+ */
+int tune_features(const tune_arch* arch, const tune_axes* axes, const tune_kernel_desc* descs,
+                  const int64_t* sample_kernel, const int32_t* sample_point, int64_t n, uint16_t* feats,
+                  void* workspace, size_t ws_bytes, tune_stream_t stream);
+
+/*
+ * surrogate_infer — rank every point of every kernel's space by the ensemble's
+ * predicted runtime (mean over members of exp(prediction), in microseconds);
+ * per kernel, if any of the surrogate's k best points has a member spread
+ * (std / mean of the predicted runtimes) above `thresh`, return the analytic
+ * top-k instead (tune_eval's cost values) and set used_fallback[kernel] = 1.
+ * pt_offsets_host: host int64 [n_kernels + 1], exclusive scan of space sizes
+ * (each space <= 2^20 points). Outputs (device): topk_idx, topk_score
+ * [n_kernels, k], used_fallback uint8 [n_kernels]. workspace of at least
+ * surrogate_infer_workspace_bytes(members, n_kernels, k). Synchronous.
+ */
+int surrogate_infer(tune_surrogate* h, const tune_arch* arch, const tune_axes* axes,
+                    const tune_kernel_desc* descs, int64_t n_kernels, const int64_t* pt_offsets_host,
+                    int32_t k, float thresh, int32_t* topk_idx, float* topk_score, uint8_t* used_fallback,
+                    void* workspace, size_t ws_bytes, tune_stream_t stream);
+size_t surrogate_infer_workspace_bytes(int members, int64_t n_kernels, int32_t k);
+
 /* Bytes of device workspace the call needs (at least 256). */
 size_t tune_workspace_bytes(int call, int64_t n, int32_t k);
 

@@ -397,3 +397,74 @@ int or_topk(const float* scores, const int64_t* off, int64_t n_seg, int64_t k, i
     }
     return 0;
 }
+
+/*
+ * The surrogate's 48 input features of one point (T, G, U, C) of a kernel,
+ * in FP64: fixed scalings of the descriptor, the launch parameters and the
+ * occupancy and cost terms above (list in the library's features header).
+ */
+int or_features(const or_arch* a, const void* rec, int64_t T, int64_t G, int64_t U, int64_t C, double* f)
+{
+    or_kernel k;
+    decode((const unsigned char*)rec, &k);
+    double tot = 0.0;
+    for (int c = 0; c < OR_NCLASS; ++c) tot += k.n[c];
+    for (int c = 0; c < OR_NCLASS; ++c) {
+        f[c] = log2(k.n[c] + 1.0) / 20.0;
+        f[7 + c] = k.n[c] / (tot + 1.0);
+    }
+    f[14] = log2((k.n[C_FP32] + k.n[C_FP64] + 1.0) / (k.n[C_GLDST] + k.n[C_SLDST] + 1.0)) / 10.0;
+    f[15] = (double)k.r0 / 255.0;
+    f[16] = (double)k.s0 / 65536.0;
+    f[17] = (double)k.d;
+    int64_t R = regs_at(k.r0, U);
+    or_occ o;
+    or_occupancy(a, T, R, k.s0, C, &o);
+    int64_t rpw = 0;
+    if (a->reg_alloc_mode == 0 && R > 0 && R <= a->regs_thread_max) rpw = round_up(R * a->warp_size, a->reg_alloc_unit);
+    int64_t s_alloc = 0;
+    if (k.s0 <= a->smem_block_max) s_alloc = round_up(k.s0 + a->smem_reserved_block, a->smem_alloc_unit);
+    f[18] = log2((double)T) / 10.0;
+    f[19] = (double)o.W_B / 32.0;
+    f[20] = (double)(a->warp_size * o.W_B) / (double)T;
+    f[21] = log2((double)G) / 16.0;
+    f[22] = (double)U / 8.0;
+    f[23] = (double)C / 100.0;
+    f[24] = (double)R / 255.0;
+    f[25] = (double)rpw / 8192.0;
+    f[26] = (double)min2(o.G_W, 64) / 32.0;
+    f[27] = (double)min2(o.G_R, 64) / 32.0;
+    f[28] = (double)min2(o.G_S, 64) / 32.0;
+    f[29] = (double)o.B / 32.0;
+    f[30] = (double)o.W / 64.0;
+    f[31] = (double)o.W / (double)a->max_warps_sm;
+    f[32] = (o.B > 0 && o.G_W == o.B) ? 1.0 : 0.0;
+    f[33] = (o.B > 0 && o.G_R == o.B) ? 1.0 : 0.0;
+    f[34] = (o.B > 0 && o.G_S == o.B) ? 1.0 : 0.0;
+    double delta = 1.0 + (double)k.d, K = (double)a->work_scale, Cc[OR_NCLASS];
+    for (int c = 0; c < OR_NCLASS; ++c) Cc[c] = delta * K * ((c == C_BRANCH) ? k.n[c] / (double)U : k.n[c]) / a->ipc[c];
+    double C_nm = Cc[C_FP32] + Cc[C_FP64] + Cc[C_INT] + Cc[C_BRANCH] + Cc[C_SFU];
+    double C_m = Cc[C_GLDST] + Cc[C_SLDST];
+    double waves = 0.0, par = 0.0, hide = 0.0, cost = 0.0;
+    if (o.valid) {
+        int64_t slots = a->n_sm * o.B;
+        int64_t wv = ceil_div(G, slots);
+        waves = (double)wv;
+        par = (double)(a->n_sm * G) / (double)(wv * slots);
+        hide = (double)a->w_sat / (double)o.W;
+        if (hide < 1.0) hide = 1.0;
+        cost = or_cost64(a, k.n, (double)k.d, U, T, G, o.B, o.W);
+    }
+    f[35] = waves > 0.0 ? log2(waves) / 10.0 : 0.0;
+    f[36] = par / (double)a->n_sm;
+    f[37] = hide / 32.0;
+    f[38] = log2(cost + 1.0) / 40.0;
+    f[39] = log2(C_nm + 1.0) / 40.0;
+    f[40] = log2(C_m + 1.0) / 40.0;
+    f[41] = log2((double)G * (double)T) / 26.0;
+    f[42] = (double)o.cap / 233472.0;
+    f[43] = (double)s_alloc / 65536.0;
+    f[44] = log2(k.n[C_BRANCH] / (double)U + 1.0) / 20.0;
+    f[45] = f[46] = f[47] = 0.0;
+    return 0;
+}

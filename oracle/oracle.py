@@ -73,6 +73,9 @@ def lib():
         L.or_topk.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
                               C.c_void_p, C.c_int]
         L.or_topk.restype = C.c_int
+        L.or_features.argtypes = [P(Arch), C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
+                                  P(C.c_double)]
+        L.or_features.restype = C.c_int
         _lib = L
     return _lib
 
@@ -175,6 +178,28 @@ def topk(scores, offsets, k, nthreads=0):
     lib().or_topk(scores.ctypes.data, offsets.ctypes.data, n_seg, int(k), idx.ctypes.data,
                   val.ctypes.data, int(nthreads))
     return {"idx": idx, "cost": val}
+
+
+def features(row, desc, T, G, U, carveout):
+    """The surrogate's 48 features of one point, FP64 (numpy array)."""
+    import numpy as np
+
+    a = make_arch(row)
+    rec = np.ascontiguousarray(np.asarray(desc).reshape(1))
+    out = (C.c_double * 48)()
+    lib().or_features(C.byref(a), rec.ctypes.data, int(T), int(G), int(U), int(carveout), out)
+    return np.array(out[:], dtype=np.float64)
+
+
+def decode_point(desc, axes, i):
+    """Canonical index -> (T, G, U, carveout) of a descriptor's space (carveout fastest)."""
+    m = int(desc["space_mask"])
+    pos = lambda sh, w: [b for b in range(w) if (m >> (sh + b)) & 1]
+    tp, gp, up, cp = pos(0, 32), pos(32, 16), pos(48, 8), pos(56, 4)
+    i, ic = divmod(int(i), len(cp))
+    i, iu = divmod(i, len(up))
+    it, ig = divmod(i, len(gp))
+    return axes["t"][tp[it]], axes["g"][gp[ig]], axes["u"][up[iu]], axes["c"][cp[ic]]
 
 
 def threads_available():

@@ -12,7 +12,7 @@ from . import native
 from .native import (TUNE_EMIT_POINTS, TUNE_SCHED_CHUNK, TUNE_SCHED_CTAS,  # noqa: F401
                      TUNE_SCHED_THREAD, TUNE_SCHED_WARP, TuneError)
 
-__all__ = ["tune_eval", "tune_topk", "tune_autotune", "tune_workspace_bytes", "tune_check",
+__all__ = ["tune_eval", "tune_topk", "tune_autotune", "tune_features", "tune_workspace_bytes", "tune_check",
            "descs_to_device", "TUNE_EMIT_POINTS", "TUNE_SCHED_WARP", "TUNE_SCHED_THREAD",
            "TUNE_SCHED_CHUNK", "TUNE_SCHED_CTAS", "TuneError"]
 
@@ -120,6 +120,25 @@ def tune_autotune(arch, axes, descs, k, reps=3, topk_idx=None, topk_cost=None, w
                          C.byref(bms), _stream(stream))
     native.check(rc)
     return bf.value, bms.value, topk_idx, topk_cost
+
+
+def tune_features(arch, axes, descs, sample_kernel, sample_point, feats=None, workspace_buf=None,
+                  stream=None):
+    """Surrogate input features (device bfloat16 [n, 128]) of listed (kernel, point) samples."""
+    torch = _torch()
+    L = native.load()
+    n = sample_kernel.numel()
+    dev = descs.device
+    if feats is None:
+        feats = torch.empty((n, 128), dtype=torch.bfloat16, device=dev)
+    if workspace_buf is None:
+        workspace_buf = workspace(native.TUNE_CALL_EVAL, 0, 1, dev)
+    a = native.make_arch(arch)
+    x = native.make_axes(axes)
+    rc = L.tune_features(C.byref(a), C.byref(x), _ptr(descs), _ptr(sample_kernel), _ptr(sample_point), n,
+                         _ptr(feats), _ptr(workspace_buf), workspace_buf.numel(), _stream(stream))
+    native.check(rc)
+    return feats
 
 
 def tune_check(workspace_buf, stream=None):

@@ -338,6 +338,8 @@ extern "C" {
 
 int surrogate_param_count(void) { return (int)P; }
 
+int surrogate_members(const tune_surrogate* h) { return h ? h->members : 0; }
+
 int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
 {
     tune::clear_error();

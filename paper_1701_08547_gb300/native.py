@@ -81,6 +81,8 @@ def load():
     L.tune_autotune.argtypes = [C.POINTER(TuneArch), C.POINTER(TuneAxes), vp, i64, i32, i32, vp, vp,
                                 vp, sz, C.POINTER(C.c_uint32), C.POINTER(C.c_float), vp]
     L.tune_autotune.restype = C.c_int
+    L.tune_features.argtypes = [C.POINTER(TuneArch), C.POINTER(TuneAxes), vp, vp, vp, i64, vp, vp, sz, vp]
+    L.tune_features.restype = C.c_int
     _lib = L
     return L
 

@@ -30,6 +30,11 @@ def _lib():
         L.surrogate_train_step.restype = C.c_int
         L.surrogate_train.argtypes = [vp, vp, vp, i64, vp, i32, vp, vp]
         L.surrogate_train.restype = C.c_int
+        L.surrogate_infer.argtypes = [vp, C.POINTER(native.TuneArch), C.POINTER(native.TuneAxes), vp, i64, vp,
+                                      i32, C.c_float, vp, vp, vp, vp, C.c_size_t, vp]
+        L.surrogate_infer.restype = C.c_int
+        L.surrogate_infer_workspace_bytes.argtypes = [C.c_int, i64, i32]
+        L.surrogate_infer_workspace_bytes.restype = C.c_size_t
         L._surrogate_declared = True
     return L
 
@@ -104,3 +109,25 @@ class Surrogate:
                                             C.c_void_p(labels.data_ptr()), n,
                                             C.c_void_p(order.data_ptr()), int(epochs), lt,
                                             _stream(stream)))
+
+    def infer(self, arch, axes, descs, pt_offsets, k, thresh=0.1, stream=None):
+        """Rank every point of every kernel by predicted runtime with analytic fallback.
+        descs: device descriptor tensor; pt_offsets: numpy int64 [n + 1].
+        Returns (topk_idx, topk_score, used_fallback) device tensors."""
+        import numpy as np
+        import torch
+
+        n = descs.numel() * descs.element_size() // 64
+        dev = descs.device
+        off = np.ascontiguousarray(pt_offsets, dtype=np.int64)
+        idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+        val = torch.empty((n, k), dtype=torch.float32, device=dev)
+        fb = torch.empty(n, dtype=torch.uint8, device=dev)
+        nbytes = self.L.surrogate_infer_workspace_bytes(self.members, n, k)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        a, x = native.make_arch(arch), native.make_axes(axes)
+        native.check(self.L.surrogate_infer(self.h, C.byref(a), C.byref(x), C.c_void_p(descs.data_ptr()), n,
+                                            off.ctypes.data, int(k), float(thresh), C.c_void_p(idx.data_ptr()),
+                                            C.c_void_p(val.data_ptr()), C.c_void_p(fb.data_ptr()),
+                                            C.c_void_p(ws.data_ptr()), nbytes, _stream(stream)))
+        return idx, val, fb

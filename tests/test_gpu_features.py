@@ -1,0 +1,96 @@
+"""GPU features and surrogate ranking, through the C ABI, against the oracle.
+
+Features are BF16 on the GPU (computed in FP32) and FP64 in the oracle: they
+must agree to one BF16 rounding step (2^-8 relative). The ensemble ranking
+is checked for validity against the oracle's predicted runtimes (FP64 forward
+on the same BF16 weights and features): every chosen point must be within 5 %
+of the oracle's k-th best; with a zero threshold every kernel falls back to
+the analytic top-k, which must equal the oracle's bit for bit.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import surrogate_oracle as S
+from workloads import archs, gen
+from workloads import mlp as L
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+
+    from paper_1701_08547_gb300 import build
+
+    build.build()
+    assert torch.cuda.is_available()
+    return torch.device("cuda:0")
+
+
+def test_features_match_oracle(dev, oracle):
+    import torch
+
+    import paper_1701_08547_gb300 as T
+
+    a, ax = archs.arch("sm_103"), gen.axes()
+    d = gen.descriptors(200, 21, "uneven")
+    sizes = gen.space_sizes(d)
+    rng = np.random.default_rng(0)
+    kern = rng.integers(0, 200, 600)
+    pt = np.array([rng.integers(0, sizes[k]) for k in kern])
+    f = T.tune_features(a, ax, T.descs_to_device(d, dev), torch.tensor(kern, dtype=torch.int64, device=dev),
+                        torch.tensor(pt, dtype=torch.int32, device=dev))
+    g = f.float().cpu().numpy().astype(np.float64)
+    assert np.all(g[:, 48:] == 0)
+    for i in range(len(kern)):
+        T_, G_, U_, C_ = oracle.decode_point(d[kern[i]], ax, pt[i])
+        want = S.bf16(oracle.features(a, d[kern[i]], T_, G_, U_, C_))
+        err = np.abs(g[i, :48] - want)
+        assert np.all(err <= 2.0 ** -7 * np.abs(want) + 1e-30), (i, np.argmax(err), g[i, :48], want)
+
+
+def _oracle_scores(oracle, a, ax, desc, flat, members):
+    size = int(gen.space_sizes(desc[None])[0])
+    X = np.zeros((size, L.IN))
+    for p in range(size):
+        T_, G_, U_, C_ = oracle.decode_point(desc, ax, p)
+        X[p, :48] = oracle.features(a, desc, T_, G_, U_, C_)
+    X = S.bf16(X)
+    preds = np.stack([S.forward(prm, X, bf=True)[0] for prm in L.unpack(flat, members)])
+    r = np.exp(preds)
+    mean, std = r.mean(0), r.std(0)
+    valid = X[:, 29] > 0
+    return np.where(valid, mean, np.inf), np.where(valid, std / mean, 0.0)
+
+
+def test_infer_ranking_and_fallback(dev, oracle):
+    from paper_1701_08547_gb300.surrogate import Surrogate
+    import paper_1701_08547_gb300 as T
+
+    a, ax = archs.arch("sm_103"), gen.axes()
+    d = gen.descriptors(24, 31, "dense128")
+    d["space_mask"][::3] = np.uint64(gen.mask_bits(range(0, 32, 3), [4, 9, 15], [0, 2], [0, 3]))
+    off = gen.point_offsets(d)
+    members, k = 2, 5
+    s = Surrogate(members=members, batch=1024)
+    flat = L.init_params(members, [11, 12])
+    s.set_params(flat)
+    dd = T.descs_to_device(d, dev)
+    # thresh 0: every kernel falls back to the analytic top-k
+    idx, val, fb = s.infer(a, ax, dd, off, k, thresh=0.0)
+    o = oracle.evaluate(a, ax, d, k)
+    assert np.all(fb.cpu().numpy() == 1)
+    assert np.array_equal(idx.cpu().numpy(), o["idx"])
+    assert np.array_equal(val.cpu().numpy().view(np.uint32), o["cost"].view(np.uint32))
+    # huge threshold: ranking by the ensemble's mean predicted runtime
+    idx, val, fb = s.infer(a, ax, dd, off, k, thresh=1e30)
+    assert np.all(fb.cpu().numpy() == 0)
+    gi = idx.cpu().numpy()
+    for kk in range(len(d)):
+        score, _ = _oracle_scores(oracle, a, ax, d[kk], flat, members)
+        kth = np.sort(score)[k - 1]
+        chosen = gi[kk]
+        assert len(set(chosen.tolist())) == k and np.all(chosen >= 0)
+        assert np.all(score[chosen] <= kth * 1.05 + 1e-12), (kk, score[chosen], kth)
