@@ -320,7 +320,74 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample)
+    if not args.no_surrogate:
+        line["surrogate"] = surrogate_section(args, dev, a, ax, peaks)
     return line
+
+
+# FLOPs per sample and member of the surrogate MLP (128 -> 256 x 4 -> 1): forward
+# 2 (128*256 + 3*256*256 + 256); training = forward + backward (2x forward).
+MLP_FWD_FLOP = 2 * (128 * 256 + 3 * 256 * 256 + 256)
+MLP_TRAIN_FLOP = 3 * MLP_FWD_FLOP
+
+
+def surrogate_section(args, dev, a, ax, peaks):
+    """Learned surrogate at bounded size: measured labels, training and inference
+    throughput against the BF16 tensor peak, top-5 agreement with the measured best
+    (held-out, fully timed spaces) and with the analytic model (dense points)."""
+    import torch
+
+    import paper_1701_08547_gb300 as T
+    from paper_1701_08547_gb300 import surrogate_data as SD
+
+    members = 5
+    t0 = time.perf_counter()
+    data = SD.build_set(a, ax, gen.descriptors(args.sur_descs, 4, "dense"), 64, 4, dev)
+    gen_s = time.perf_counter() - t0
+    epochs = 20
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sur, trace = SD.train(data, members=members, epochs=epochs, dev=dev)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    samples = data["n"] * epochs
+    train_tflops = samples * members * MLP_TRAIN_FLOP / train_s / 1e12
+    # inference over every point of dense kernels (features, ensemble, ranking, fallback)
+    nk = args.sur_infer_kernels
+    d = gen.descriptors(nk, 2, "dense")
+    off = gen.point_offsets(d)
+    dd = T.descs_to_device(d, dev)
+    inf_sur = SD.Surrogate(members=members, batch=65536)
+    inf_sur.set_params(sur.get(sur.GET_PARAMS))
+    inf_sur.infer(a, ax, dd, off, 5, 0.1)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s_idx, _, fb = inf_sur.infer(a, ax, dd, off, 5, 0.1)
+    torch.cuda.synchronize()
+    infer_s = time.perf_counter() - t0
+    pts = int(off[-1])
+    infer_tflops = pts * members * MLP_FWD_FLOP / infer_s / 1e12
+    a_idx, _ = T.tune_eval(a, ax, dd, 5)
+    si, ai = s_idx.cpu().numpy(), a_idx.cpu().numpy()
+    agree_overlap = float(np.mean([len(set(si[i]) & set(ai[i])) / 5 for i in range(nk)]))
+    agree_hit = float(np.mean([ai[i, 0] in si[i] for i in range(nk)]))
+    held_out = gen.descriptors(args.sur_eval, 40, "dense")
+    ev = SD.evaluate(sur, a, ax, held_out, dev, k=5, thresh=0.1)
+    ev_nofb = SD.evaluate(sur, a, ax, held_out, dev, k=5, thresh=1e30)
+    peak = peaks.get("bf16_tflops", 1900.0)
+    return {
+        "members": members,
+        "labels": {"samples_measured": data["measured"], "samples_kept": data["n"], "seconds": gen_s,
+                   "kind": "this GPU's median-of-3 times of emitted variants"},
+        "train": {"samples_per_s": samples / train_s, "epochs": epochs, "seconds": train_s,
+                  "tflops": train_tflops, "frac_bf16_peak": train_tflops / peak,
+                  "final_mse_ln_us": float(trace[-1].mean())},
+        "infer": {"points_per_s": pts / infer_s, "points": pts, "kernels": nk, "seconds": infer_s,
+                  "tflops": infer_tflops, "frac_bf16_peak": infer_tflops / peak,
+                  "fallback_rate": float(fb.float().mean().item())},
+        "top5_vs_analytic": {"overlap": agree_overlap, "analytic_best_in_surrogate_top5": agree_hit},
+        "top5_vs_measured_best": {"thresh_0.1": ev, "no_fallback": ev_nofb},
+    }
 
 
 def run_topk(args):
@@ -451,6 +518,10 @@ def main():
     p.add_argument("--sched", choices=["auto", "warp", "thread"], default="auto")
     p.add_argument("--no-graph", action="store_true", help="plain launches instead of graph replays")
     p.add_argument("--flags", default="", help="tune_eval schedule flags in hex (skips the autotuner)")
+    p.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate section")
+    p.add_argument("--sur-descs", type=int, default=1000, help="descriptors for surrogate labels (x64 points)")
+    p.add_argument("--sur-infer-kernels", type=int, default=500, help="dense kernels scored by the ensemble")
+    p.add_argument("--sur-eval", type=int, default=150, help="held-out kernels with fully timed spaces")
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args()
     if args.warmup < 3:

@@ -288,6 +288,29 @@ int surrogate_infer(tune_surrogate* h, const tune_arch* arch, const tune_axes* a
                     void* workspace, size_t ws_bytes, tune_stream_t stream);
 size_t surrogate_infer_workspace_bytes(int members, int64_t n_kernels, int32_t k);
 
+/*
+ * tune_emit_measure — the surrogate's labels: run synthetic code variants on
+ * this GPU and time them. (The paper's autotuner times generated variants,
+ * Section IV-A; these variants are the library's own, not Orio's.)
+ * For sample i, descriptor descs[sample_kernel[i]] at point sample_point[i]
+ * (canonical index) becomes a kernel compiled at run time (NVRTC, sm_103a)
+ * that executes `items` work items; per item and instruction class it runs a
+ * dependent loop of round(n_c * count_scale) operations, unrolled U times,
+ * keeps registers live according to r0, uses s0 bytes of dynamic shared
+ * memory, and repeats its FP32 loop on round(32 d) lanes of each warp. It is
+ * launched with G blocks of T threads at carveout C: one untimed launch, then
+ * `reps` launches timed with CUDA events. us[i] = median time in
+ * microseconds (NaN where the launch is not possible, e.g. too many
+ * registers for T); regs[i] = the variant's registers per thread.
+ * descs, sample arrays and outputs are host memory; the call allocates two
+ * 4 MB device buffers for its duration and is synchronous. Returns
+ * TUNE_ECOMPILE if a variant fails to compile.
+ */
+int tune_emit_measure(const tune_axes* axes, const tune_kernel_desc* descs, int64_t n_kernels,
+                      const int32_t* sample_kernel, const int32_t* sample_point, int64_t n_samples,
+                      int32_t items, float count_scale, int32_t reps, float* us, int32_t* regs,
+                      tune_stream_t stream);
+
 /* Bytes of device workspace the call needs (at least 256). */
 size_t tune_workspace_bytes(int call, int64_t n, int32_t k);
 

@@ -49,7 +49,7 @@ def build(verbose=False, extra=()):
         objs = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         cmd = [NVCC, *ARCH, "-shared", "-cudart", "shared", *objs, "-o", LIB + ".tmp",
-               "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
+               "-Xlinker", "-rpath=/usr/local/cuda/lib64", "-lnvrtc"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

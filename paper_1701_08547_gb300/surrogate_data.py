@@ -1,0 +1,158 @@
+"""Surrogate data generation, training and evaluation on the GPU (driver code).
+
+* label generation: tune_emit_measure times synthetic variants of sampled
+  (descriptor, point) pairs on this GPU; the label is ln(median microseconds);
+* features: tune_features (the analyzer's internals for each sample);
+* training: surrogate_train (the library's BF16 kernels) over seeded epochs;
+* evaluation: held-out descriptors whose small spaces are timed completely;
+  hit@5 = the measured-best point is among the 5 a ranking picks, for the
+  ensemble (with its analytic fallback) and for the analytic model alone.
+
+All random choices (descriptors, sampled points, epoch orders, initial
+weights) are seeded; the seeds are arguments.
+"""
+
+import ctypes as C
+
+import numpy as np
+
+from . import native
+from . import descs_to_device, tune_eval, tune_features
+from .surrogate import Surrogate
+
+ITEMS = 65536
+COUNT_SCALE = 1.0 / 1024.0
+# Sub-space sampled for labels: threads >= 64, grid >= 64 blocks (axis positions), so
+# that every variant finishes in tens of microseconds.
+T_MIN_POS, G_MIN_POS = 1, 6
+# Held-out spaces, fully timed: 5 thread counts x 4 grids x unroll {1, 4} x carveout {0, 100}
+EVAL_T, EVAL_G, EVAL_U, EVAL_C = [1, 3, 7, 15, 31], [7, 9, 11, 13], [0, 3], [0, 3]
+
+
+def _emit_lib():
+    L = native.load()
+    if not getattr(L, "_emit_declared", False):
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+        L.tune_emit_measure.argtypes = [C.POINTER(native.TuneAxes), vp, i64, vp, vp, i64, i32, C.c_float, i32,
+                                        vp, vp, vp]
+        L.tune_emit_measure.restype = C.c_int
+        L._emit_declared = True
+    return L
+
+
+def measure(axes, descs, skern, spoint, items=ITEMS, scale=COUNT_SCALE, reps=3, stream=None):
+    """Median runtime (us; NaN where not launchable) and registers of each sample's variant."""
+    import torch
+
+    L = _emit_lib()
+    d = np.ascontiguousarray(descs)
+    sk = np.ascontiguousarray(skern, dtype=np.int32)
+    sp = np.ascontiguousarray(spoint, dtype=np.int32)
+    us = np.empty(len(sk), dtype=np.float32)
+    regs = np.empty(len(sk), dtype=np.int32)
+    s = torch.cuda.current_stream() if stream is None else stream
+    x = native.make_axes(axes)
+    native.check(L.tune_emit_measure(C.byref(x), d.ctypes.data, len(d), sk.ctypes.data, sp.ctypes.data, len(sk),
+                                     int(items), float(scale), int(reps), us.ctypes.data, regs.ctypes.data,
+                                     C.c_void_p(s.cuda_stream)))
+    return us, regs
+
+
+def sample_points(descs, per_desc, seed):
+    """per_desc random canonical point indices per descriptor, restricted to T and G >= 64."""
+    rng = np.random.default_rng(seed)
+    skern, spoint = [], []
+    for i, d in enumerate(descs):
+        m = int(d["space_mask"])
+        tp = [b for b in range(32) if (m >> b) & 1 and b >= T_MIN_POS]
+        gp = [b for b in range(16) if (m >> (32 + b)) & 1 and b >= G_MIN_POS]
+        up = [b for b in range(8) if (m >> (48 + b)) & 1]
+        cp = [b for b in range(4) if (m >> (56 + b)) & 1]
+        if not (tp and gp and up and cp):
+            continue
+        allt = [b for b in range(32) if (m >> b) & 1]
+        allg = [b for b in range(16) if (m >> (32 + b)) & 1]
+        for _ in range(per_desc):
+            t, g = allt.index(rng.choice(tp)), allg.index(rng.choice(gp))
+            u, c = rng.integers(len(up)), rng.integers(len(cp))
+            skern.append(i)
+            spoint.append(((t * len(allg) + g) * len(up) + u) * len(cp) + c)
+    return np.array(skern, dtype=np.int64), np.array(spoint, dtype=np.int32)
+
+
+def build_set(arch, axes, descs, per_desc, seed, dev):
+    """Measured training set: features (device bf16), labels ln(us) (device), kept samples."""
+    import torch
+
+    skern, spoint = sample_points(descs, per_desc, seed)
+    us, _ = measure(axes, descs, skern, spoint)
+    feats = tune_features(arch, axes, descs_to_device(descs, dev), torch.from_numpy(skern).to(dev),
+                          torch.from_numpy(spoint).to(dev))
+    valid = feats[:, 29].float().cpu().numpy() > 0  # B* > 0 under the model
+    keep = np.isfinite(us) & (us > 0) & valid
+    idx = torch.from_numpy(np.nonzero(keep)[0]).to(dev)
+    return {"feats": feats[idx].contiguous(),
+            "labels": torch.from_numpy(np.log(us[keep]).astype(np.float32)).to(dev),
+            "n": int(keep.sum()), "measured": len(us), "us": us}
+
+
+def train(data, members=5, epochs=20, batch=8192, lr=1e-3, seed=5, dev="cuda"):
+    """Train an ensemble on a measured set; returns (Surrogate, loss trace [epochs, steps, members])."""
+    import torch
+
+    from workloads import mlp as L
+
+    n = data["n"]
+    batch = min(batch, max(128, (n // 128) * 128))
+    sur = Surrogate(members=members, batch=batch, lr=lr)
+    sur.set_params(L.init_params(members, [seed + m for m in range(members)]))
+    rng = np.random.default_rng(seed)
+    order = torch.from_numpy(np.concatenate([rng.permutation(n) for _ in range(epochs)]).astype(np.int32)).to(dev)
+    steps = (n + batch - 1) // batch
+    trace = torch.zeros(epochs * steps * members, dtype=torch.float32, device=dev)
+    sur.train(data["feats"], data["labels"], order, epochs, trace)
+    torch.cuda.synchronize()
+    return sur, trace.cpu().numpy().reshape(epochs, steps, members)
+
+
+def eval_spaces(descs):
+    from workloads import gen
+
+    out = descs.copy()
+    out["space_mask"] = np.uint64(gen.mask_bits(EVAL_T, EVAL_G, EVAL_U, EVAL_C))
+    return out
+
+
+def evaluate(sur, arch, axes, descs, dev, k=5, thresh=0.1):
+    """Against the measured best of fully timed held-out spaces: hit@k (best among the k picks),
+    overlap of the k picks with the measured k best, and the median slowdown of the first pick,
+    for the ensemble (with its analytic fallback at `thresh`) and for the analytic model."""
+    from workloads import gen
+
+    d = eval_spaces(descs)
+    size = int(gen.space_sizes(d[:1])[0])
+    skern = np.repeat(np.arange(len(d)), size)
+    spoint = np.tile(np.arange(size), len(d)).astype(np.int32)
+    us, _ = measure(axes, d, skern, spoint)
+    us = us.reshape(len(d), size)
+    dd = descs_to_device(d, dev)
+    a_idx, _ = tune_eval(arch, axes, dd, k)
+    s_idx, _, fb = sur.infer(arch, axes, dd, gen.point_offsets(d), k, thresh)
+    a_idx, s_idx, fb = a_idx.cpu().numpy(), s_idx.cpu().numpy(), fb.cpu().numpy()
+    t = np.where(np.isfinite(us), us, np.inf)  # unlaunchable points never win and count as misses
+    ok = np.sum(np.isfinite(us), axis=1) >= k
+    best = np.argmin(t, axis=1)
+    meas_top = np.argsort(t, axis=1, kind="stable")[:, :k]
+
+    def stats(idx):
+        hit = np.array([best[i] in idx[i] for i in range(len(d))])[ok]
+        ov = np.array([len(set(idx[i]) & set(meas_top[i])) / k for i in range(len(d))])[ok]
+        first = np.array([t[i, idx[i, 0]] / t[i, best[i]] if idx[i, 0] >= 0 else np.inf
+                          for i in range(len(d))])[ok]
+        return float(hit.mean()), float(ov.mean()), float(np.median(first))
+
+    hs, os_, rs = stats(s_idx)
+    ha, oa, ra = stats(a_idx)
+    return {"kernels": int(ok.sum()), "k": k, "thresh": thresh, "hit_surrogate": hs, "hit_analytic": ha,
+            "overlap_surrogate": os_, "overlap_analytic": oa, "first_pick_slowdown_surrogate": rs,
+            "first_pick_slowdown_analytic": ra, "fallback_rate": float(fb[ok].mean())}
