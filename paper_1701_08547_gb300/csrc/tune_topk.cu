@@ -1,11 +1,11 @@
 // tune_topk: segmented top-k over an external FP32 score array (HBM-bound).
 //
-// One warp per segment, CTAs of 8 warps striding over segments. Lanes read
-// the segment with coalesced loads, four independent loads in flight per lane,
-// and keep a sorted register list of their k best (score, index); each lane
-// visits its elements in increasing index order, so a strict "<" keeps lower
-// indices first among equal scores. A k-round warp merge over an
-// order-preserving unsigned image of the scores emits the segment's top-k.
+// One warp per segment, CTAs of 8 warps striding over segments. Lanes read the
+// segment with coalesced loads, eight independent loads in flight per lane.
+// The warp keeps one exact top-k list (lane j = j-th best, as an
+// order-preserving unsigned image of the score plus its index) and its k-th
+// key; only when a block of 256 scores holds values at or below that key does
+// the warp merge them, in increasing (value, index) order, into the list.
 #include <stdint.h>
 
 #include "tune_internal.h"
@@ -28,111 +28,94 @@ __device__ __forceinline__ float key_value(unsigned k)
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-template <int KMAX>
-__device__ __forceinline__ void insert(float (&lc)[KMAX], int (&li)[KMAX], float c, int i)
+// Warp-wide top-k list: lane j < k holds the j-th best (order key, index), ascending.
+__device__ __forceinline__ bool key_less(unsigned a, int ia, unsigned b, int ib)
 {
-#pragma unroll
-    for (int j = KMAX - 1; j > 0; --j) {
-        bool shift = c < lc[j - 1];
-        bool here = !shift && c < lc[j];
-        float nc = shift ? lc[j - 1] : (here ? c : lc[j]);
-        int ni = shift ? li[j - 1] : (here ? i : li[j]);
-        lc[j] = nc;
-        li[j] = ni;
-    }
-    if (c < lc[0]) {
-        lc[0] = c;
-        li[0] = i;
-    }
+    return a < b || (a == b && ia < ib);
 }
 
-template <int KMAX>
-__device__ __forceinline__ float kth(const float (&lc)[KMAX], int k)
+__device__ __forceinline__ void list_insert(unsigned& lk, int& li, unsigned& tau_k, int& tau_i, unsigned k_new,
+                                            int i_new, int k, int lane)
 {
-    // Select chain (not lc[k - 1], which would force the list into local memory).
-    float t = lc[KMAX - 1];
-#pragma unroll
-    for (int j = KMAX - 2; j >= 0; --j) t = (j >= k - 1) ? lc[j] : t;
-    return t;
-}
-
-template <int KMAX>
-__device__ __forceinline__ void consider(float (&lc)[KMAX], int (&li)[KMAX], float& thr, int k, float v,
-                                         int j)
-{
-    v = v + 0.0f;  // -0 -> +0: equal scores compare equal in the merge keys too
-    if (v < thr) {  // false for NaN and for +inf
-        insert<KMAX>(lc, li, v, j);
-        thr = kth<KMAX>(lc, k);
+    const unsigned below = __ballot_sync(kFull, lane < k && key_less(lk, li, k_new, i_new));
+    const int pos = __popc(below);
+    const unsigned up_k = __shfl_up_sync(kFull, lk, 1);
+    const int up_i = __shfl_up_sync(kFull, li, 1);
+    if (lane < k) {
+        if (lane == pos) {
+            lk = k_new;
+            li = i_new;
+        } else if (lane > pos) {
+            lk = up_k;
+            li = up_i;
+        }
     }
+    tau_k = __shfl_sync(kFull, lk, k - 1);
+    tau_i = __shfl_sync(kFull, li, k - 1);
 }
 
-template <int KMAX>
+constexpr int kLoads = 8;  // independent loads in flight per lane
+
 __global__ void __launch_bounds__(kThreads)
-    topk_segmented_kernel(const float* __restrict__ scores, const int64_t* __restrict__ off,
-                          int64_t n_seg, int k, int32_t* __restrict__ out_i, float* __restrict__ out_s)
+    topk_segmented_kernel(const float* __restrict__ scores, const int64_t* __restrict__ off, int64_t n_seg, int k,
+                          int32_t* __restrict__ out_i, float* __restrict__ out_s)
 {
     const int lane = threadIdx.x & 31;
     const float kInf = __int_as_float(0x7f800000);
+    const unsigned kInfKey = order_key(kInf);
     for (int64_t s = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); s < n_seg;
          s += (int64_t)gridDim.x * kWarps) {
         const int64_t b = off[s];
         const int len = (int)(off[s + 1] - b);
         const float* seg = scores + b;
-        float lc[KMAX];
-        int li[KMAX];
+        unsigned lk = kInfKey;  // list entry of this lane (lanes < k)
+        int li = -1;
+        unsigned tau_k = kInfKey;  // the list's k-th key: candidates must not exceed it
+        int tau_i = -1;
+        for (int base = 0; base < len; base += 32 * kLoads) {
+            float v[kLoads];
 #pragma unroll
-        for (int j = 0; j < KMAX; ++j) {
-            lc[j] = kInf;
-            li[j] = -1;
-        }
-        float thr = kInf;
-        int j = lane;
-        for (; j + 96 < len; j += 128) {
-            const float v0 = __ldcs(seg + j), v1 = __ldcs(seg + j + 32), v2 = __ldcs(seg + j + 64),
-                        v3 = __ldcs(seg + j + 96);
-            consider<KMAX>(lc, li, thr, k, v0, j);
-            consider<KMAX>(lc, li, thr, k, v1, j + 32);
-            consider<KMAX>(lc, li, thr, k, v2, j + 64);
-            consider<KMAX>(lc, li, thr, k, v3, j + 96);
-        }
-        for (; j < len; j += 32) consider<KMAX>(lc, li, thr, k, __ldcs(seg + j), j);
-
-        float oc = kInf;
-        int oi = -1;
-        for (int r = 0; r < k; ++r) {
-            const unsigned hk = order_key(lc[0]);
-            const unsigned mk = __reduce_min_sync(kFull, hk);
-            if (mk >= order_key(kInf)) break;
-            const unsigned cand = hk == mk ? (unsigned)li[0] : 0xffffffffu;
-            const unsigned mi = __reduce_min_sync(kFull, cand);
-            if (lane == r) {
-                oc = key_value(mk);
-                oi = (int)mi;
+            for (int q = 0; q < kLoads; ++q) {
+                const int j = base + lane + 32 * q;
+                v[q] = j < len ? __ldcs(seg + j) + 0.0f : __int_as_float(0x7fc00000);  // -0 -> +0; NaN pads
             }
-            const bool win = hk == mk && (unsigned)li[0] == mi;
+            const float tau_v = key_value(tau_k);
+            unsigned cm = 0;
 #pragma unroll
-            for (int q = 0; q < KMAX - 1; ++q) {
-                lc[q] = win ? lc[q + 1] : lc[q];
-                li[q] = win ? li[q + 1] : li[q];
-            }
-            if (win) {
-                lc[KMAX - 1] = kInf;
-                li[KMAX - 1] = -1;
+            for (int q = 0; q < kLoads; ++q)
+                if (v[q] <= tau_v && v[q] < kInf) cm |= 1u << q;  // false for NaN and +inf
+            if (__ballot_sync(kFull, cm != 0u) == 0u) continue;
+            // Merge this block's candidates in increasing (value, index) order.
+            for (;;) {
+                unsigned hk = 0xffffffffu;
+                int hq = 0;
+#pragma unroll
+                for (int q = kLoads - 1; q >= 0; --q) {  // equal keys: the lower q (lower index) wins
+                    const unsigned kq = order_key(v[q]);
+                    if (((cm >> q) & 1u) && kq <= hk) {
+                        hk = kq;
+                        hq = q;
+                    }
+                }
+                const unsigned mk = __reduce_min_sync(kFull, hk);
+                if (mk == 0xffffffffu) break;
+                const int my_i = base + lane + 32 * hq;
+                const unsigned mi = __reduce_min_sync(kFull, hk == mk ? (unsigned)my_i : 0xffffffffu);
+                if (!key_less(mk, (int)mi, tau_k, tau_i)) break;
+                list_insert(lk, li, tau_k, tau_i, mk, (int)mi, k, lane);
+                if (hk == mk && my_i == (int)mi) cm &= ~(1u << hq);
             }
         }
         if (lane < k) {
-            out_i[s * k + lane] = oi;
-            out_s[s * k + lane] = oc;
+            out_i[s * k + lane] = li;
+            out_s[s * k + lane] = lk == kInfKey ? kInf : key_value(lk);
         }
     }
 }
 
-template <int KMAX>
-int launch(const float* scores, const int64_t* off, int64_t n_seg, int k, int32_t* oi, float* os,
-           cudaStream_t st)
+int launch(const float* scores, const int64_t* off, int64_t n_seg, int k, int32_t* oi, float* os, cudaStream_t st)
 {
-    auto kern = topk_segmented_kernel<KMAX>;
+    auto kern = topk_segmented_kernel;
     static int per_sm = 0;
     if (per_sm == 0) {
         TUNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0),
@@ -165,6 +148,5 @@ extern "C" int tune_topk(const float* scores, const int64_t* seg_offsets, int64_
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     TUNE_CUDA_TRY(cudaMemsetAsync(workspace, 0, tune::kWorkspaceHeader, s), "tune_topk: status reset");
     if (n_seg == 0) return TUNE_OK;
-    return k <= 8 ? launch<8>(scores, seg_offsets, n_seg, k, topk_idx, topk_score, s)
-                  : launch<16>(scores, seg_offsets, n_seg, k, topk_idx, topk_score, s);
+    return launch(scores, seg_offsets, n_seg, k, topk_idx, topk_score, s);
 }
