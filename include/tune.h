@@ -258,6 +258,11 @@ int surrogate_train(tune_surrogate* h, const uint16_t* feats, const float* label
 
 /* Ensemble size of a handle (0 for NULL). */
 int surrogate_members(const tune_surrogate* h);
+/* Options: 0 = forward layers on tcgen05 tensor cores (value 1, the default) or on
+ * mma.sync (value 0). */
+int surrogate_set_option(tune_surrogate* h, int option, int value);
+/* Synchronous: TUNE_ETIMEOUT if a bounded wait inside a surrogate kernel gave up. */
+int surrogate_status(tune_surrogate* h);
 
 /*
  * tune_features — the surrogate's 48 input features (zero-padded to 128 BF16

@@ -10,7 +10,10 @@
 
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "mlp_gemm.cuh"
+#include "tc_gemm.cuh"
 #include "tune_internal.h"
 
 using mlp::GemmArgs;
@@ -49,6 +52,8 @@ struct tune_surrogate {
     float *y = nullptr, *dy = nullptr, *lbl = nullptr, *loss = nullptr;  // [members][batch] / [members]
     float* part = nullptr;              // [members][KSPLIT][WID x WID]
     void* block = nullptr;              // the one device allocation
+    int* status = nullptr;              // device status word (timeouts of bounded waits)
+    int use_tc = 1;                     // forward layers on tcgen05 (1) or mma.sync (0)
 };
 
 namespace {
@@ -117,30 +122,47 @@ __global__ void head_bwd_act(const float* __restrict__ dy, const float* __restri
                                 mlp::gelu_grad(Z4[o]));
 }
 
-// grad w5[j] = sum_i dy[i] H4[i][j]; grad b5 = sum_i dy[i]   (one block of 256 threads per member)
-__global__ void head_bwd_params(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ H4, float* grad,
-                                int rows, int batch)
+// Column sums over rows in two stages (deterministic): stage 1 sums slices of
+// kRowSlice rows into part[mem][slice][WID + 1]; stage 2 adds the slices.
+constexpr int kRowSlice = 256;
+
+// part[.][.][j] = sum over the slice of dy[i] H4[i][j] (j < 256) and of dy[i] (j = 256)
+__global__ void head_bwd_partial(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ H4, float* part,
+                                 int rows, int batch, int slices)
 {
-    const int mem = blockIdx.x, j = threadIdx.x;
+    const int mem = blockIdx.y, sl = blockIdx.x, j = threadIdx.x;
     const float* d = dy + (long long)mem * batch;
     const __nv_bfloat16* h = H4 + (long long)mem * batch * WID;
     float s = 0.0f, sb = 0.0f;
-    for (int i = 0; i < rows; ++i) {
+    const int i1 = min(rows, (sl + 1) * kRowSlice);
+    for (int i = sl * kRowSlice; i < i1; ++i) {
         s = fmaf(d[i], __bfloat162float(h[(long long)i * WID + j]), s);
         sb += d[i];
     }
-    grad[mem * P + OFF_W5 + j] = s;
-    if (j == 0) grad[mem * P + OFF_B5] = sb;
+    float* o = part + ((long long)mem * slices + sl) * (WID + 1);
+    o[j] = s;
+    if (j == 0) o[WID] = sb;
 }
 
-// grad b[j] = sum_i dZ[i][j]   (one block of 256 threads per member)
-__global__ void bias_grad(const __nv_bfloat16* __restrict__ dZ, float* grad, long long off_b, int rows, int batch)
+// part[.][.][j] = sum over the slice of dZ[i][j]
+__global__ void bias_partial(const __nv_bfloat16* __restrict__ dZ, float* part, int rows, int batch, int slices)
 {
-    const int mem = blockIdx.x, j = threadIdx.x;
+    const int mem = blockIdx.y, sl = blockIdx.x, j = threadIdx.x;
     const __nv_bfloat16* d = dZ + (long long)mem * batch * WID;
     float s = 0.0f;
-    for (int i = 0; i < rows; ++i) s += __bfloat162float(d[(long long)i * WID + j]);
-    grad[mem * P + off_b + j] = s;
+    const int i1 = min(rows, (sl + 1) * kRowSlice);
+    for (int i = sl * kRowSlice; i < i1; ++i) s += __bfloat162float(d[(long long)i * WID + j]);
+    part[((long long)mem * slices + sl) * (WID + 1) + j] = s;
+}
+
+// grad[mem * P + off + j] = sum over slices of part[mem][slice][j], j < cols
+__global__ void slices_reduce(const float* __restrict__ part, float* grad, long long off, int cols, int slices)
+{
+    const int mem = blockIdx.x, j = threadIdx.x;
+    if (j >= cols) return;
+    float s = 0.0f;
+    for (int q = 0; q < slices; ++q) s += part[((long long)mem * slices + q) * (WID + 1) + j];
+    grad[mem * P + off + j] = s;
 }
 
 // grad W[o][i] = sum over splits of part[split][o][i]
@@ -222,10 +244,92 @@ GemmArgs gargs()
     return g;
 }
 
-// Forward through all members for rows [0, n_pad) of h->xin (n_pad a multiple of 128).
-int forward(tune_surrogate* h, int n_pad, cudaStream_t s)
+// ---- tcgen05 forward layers -----------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3-D BF16 map [batch][rows][K] (K contiguous), box 64 x box_rows x 1, 128-byte swizzle.
+int make_map(CUtensorMap* map, const void* base, uint64_t K, uint64_t rows, uint64_t batch, uint64_t row_bytes,
+             uint64_t batch_bytes, uint32_t box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return tune::fail(TUNE_ECUDA, "surrogate: cuTensorMapEncodeTiled unavailable");
+    const cuuint64_t dims[3] = {K, rows, batch};
+    const cuuint64_t strides[2] = {row_bytes, batch_bytes};
+    const cuuint32_t box[3] = {64, box_rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return tune::fail(TUNE_ECUDA, "surrogate: cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return TUNE_OK;
+}
+
+// One forward layer for every member: H = gelu(A W^T + b) (and Z = A W^T + b) with tcgen05.
+int tc_layer(tune_surrogate* h, int l, int n_pad, cudaStream_t s, const __nv_bfloat16* x_in, int n_valid,
+             bool store_z)
+{
+    const int kin = (int)fan_in(l);
+    CUtensorMap ta, tb;
+    int rc;
+    if (l == 0)  // rows past n_valid read as zeros (TMA out-of-bounds fill)
+        rc = make_map(&ta, x_in, IN, n_valid, 1, IN * 2, (uint64_t)n_pad * IN * 2, tc::BM);
+    else
+        rc = make_map(&ta, h->H[l - 1], WID, n_pad, h->members, WID * 2, (uint64_t)h->batch * WID * 2, tc::BM);
+    if (rc) return rc;
+    rc = make_map(&tb, h->wbf + BOFF_W(l), kin, WID, h->members, (uint64_t)kin * 2, (uint64_t)PB * 2, WID);
+    if (rc) return rc;
+    tc::Args g;
+    g.M = n_pad;
+    g.N = WID;
+    g.K = kin;
+    g.batched_a = l != 0;
+    g.bias = h->master + OFF_B(l);
+    g.sBias = P;
+    g.Z = store_z ? h->Z[l] : nullptr;
+    g.sZ = (long long)h->batch * WID;
+    g.H = h->H[l];
+    g.sH = (long long)h->batch * WID;
+    g.status = h->status;
+    const int smem = 1024 + (kin / tc::BK) * (tc::BM * tc::BK * 2 + WID * tc::BK * 2);
+    static bool attr = false;
+    if (!attr) {
+        TUNE_CUDA_TRY(cudaFuncSetAttribute(tc::gemm_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           1024 + tc::kMaxChunks * (tc::BM * tc::BK * 2 + WID * tc::BK * 2)),
+                      "surrogate: tc smem attribute");
+        attr = true;
+    }
+    tc::gemm_fwd_kernel<<<dim3(n_pad / tc::BM, h->members), tc::kThreads, smem, s>>>(ta, tb, g);
+    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: tc gemm launch");
+    return TUNE_OK;
+}
+
+// Forward through all members for rows [0, n_pad) of h->xin (n_pad a multiple of 128).
+// x_in: layer-1 input rows (h->xin, or the caller's features on the tcgen05 path);
+// n_valid rows of it exist; store_z keeps the pre-activations for a backward pass.
+int forward(tune_surrogate* h, int n_pad, cudaStream_t s, const __nv_bfloat16* x_in = nullptr, int n_valid = -1,
+            bool store_z = true)
+{
+    if (!x_in) x_in = h->xin;
+    if (n_valid < 0) n_valid = n_pad;
     for (int l = 0; l < NL; ++l) {
+        if (h->use_tc) {
+            int rc = tc_layer(h, l, n_pad, s, x_in, n_valid, store_z);
+            if (rc) return rc;
+            continue;
+        }
         GemmArgs g = gargs();
         g.A = l == 0 ? h->xin : h->H[l - 1];
         g.sA = l == 0 ? 0 : (long long)h->batch * WID;
@@ -256,7 +360,9 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
 {
     const int B = h->batch;
     loss_grad<<<h->members, 256, 0, s>>>(h->y, h->lbl, h->dy, h->loss, n, B);
-    head_bwd_params<<<h->members, WID, 0, s>>>(h->dy, h->H[NL - 1], h->grad, n_pad, B);
+    const int slices = (n_pad + kRowSlice - 1) / kRowSlice;
+    head_bwd_partial<<<dim3(slices, h->members), WID, 0, s>>>(h->dy, h->H[NL - 1], h->part, n_pad, B, slices);
+    slices_reduce<<<h->members, WID + 32, 0, s>>>(h->part, h->grad, OFF_W5, WID + 1, slices);
     head_bwd_act<<<dim3((unsigned)(((long long)B * WID + 255) / 256), h->members), 256, 0, s>>>(
         h->dy, h->master, h->Z[NL - 1], h->dZ[0], B);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: head backward launch");
@@ -287,7 +393,8 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
         if (rc) return rc;
         split_reduce<<<dim3((WID * kin + 255) / 256, h->members), 256, 0, s>>>(h->part, h->grad, OFF_W(l), kin,
                                                                                splits);
-        bias_grad<<<h->members, WID, 0, s>>>(dz, h->grad, OFF_B(l), n_pad, B);
+        bias_partial<<<dim3(slices, h->members), WID, 0, s>>>(dz, h->part, n_pad, B, slices);
+        slices_reduce<<<h->members, WID, 0, s>>>(h->part, h->grad, OFF_B(l), WID, slices);
         TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: reduce launch");
         if (l == 0) break;
         // input gradient of layer l, times gelu' of layer l-1: dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1})
@@ -340,6 +447,27 @@ int surrogate_param_count(void) { return (int)P; }
 
 int surrogate_members(const tune_surrogate* h) { return h ? h->members : 0; }
 
+int surrogate_set_option(tune_surrogate* h, int option, int value)
+{
+    tune::clear_error();
+    if (!h) return tune::fail(TUNE_EINVAL, "surrogate_set_option: NULL handle");
+    if (option == 0) {
+        h->use_tc = value != 0;
+        return TUNE_OK;
+    }
+    return tune::fail(TUNE_EINVAL, "surrogate_set_option: unknown option %d", option);
+}
+
+int surrogate_status(tune_surrogate* h)
+{
+    tune::clear_error();
+    if (!h) return tune::fail(TUNE_EINVAL, "surrogate_status: NULL handle");
+    int st = 0;
+    TUNE_CUDA_TRY(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost), "surrogate_status: copy");
+    if (st & 2) return tune::fail(TUNE_ETIMEOUT, "a bounded wait in a surrogate kernel gave up");
+    return TUNE_OK;
+}
+
 int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
 {
     tune::clear_error();
@@ -369,6 +497,7 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     add(B * 4);
     add(M * 4);
     add(M * KSPLIT * WID * WID * 4);
+    add(256);
     cudaError_t e = cudaMalloc(&h->block, bytes);
     if (e != cudaSuccess) {
         delete h;
@@ -391,6 +520,7 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     h->lbl = carve<float>(p, B);
     h->loss = carve<float>(p, M);
     h->part = carve<float>(p, M * KSPLIT * WID * WID);
+    h->status = carve<int>(p, 64);
     *out = h;
     return TUNE_OK;
 }
@@ -446,9 +576,13 @@ int surrogate_forward(tune_surrogate* h, const uint16_t* feats, int64_t n, float
     for (int64_t r0 = 0; r0 < n; r0 += h->batch) {
         const int nb = (int)((n - r0) < h->batch ? (n - r0) : h->batch);
         const int n_pad = (nb + 127) / 128 * 128;
-        int rc = load_batch(h, f + r0 * IN, h->lbl /*unused labels*/, nullptr, nb, s);
-        if (rc) return rc;
-        rc = forward(h, n_pad, s);
+        int rc;
+        if (h->use_tc) {  // layer 1 reads the caller's rows directly; no pre-activations kept
+            rc = forward(h, n_pad, s, f + r0 * IN, nb, false);
+        } else {
+            rc = load_batch(h, f + r0 * IN, h->lbl /*unused labels*/, nullptr, nb, s);
+            if (!rc) rc = forward(h, n_pad, s);
+        }
         if (rc) return rc;
         for (int mem = 0; mem < h->members; ++mem)
             TUNE_CUDA_TRY(cudaMemcpyAsync(pred + mem * n + r0, h->y + (long long)mem * h->batch, nb * sizeof(float),

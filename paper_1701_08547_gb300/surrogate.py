@@ -35,6 +35,10 @@ def _lib():
         L.surrogate_infer.restype = C.c_int
         L.surrogate_infer_workspace_bytes.argtypes = [C.c_int, i64, i32]
         L.surrogate_infer_workspace_bytes.restype = C.c_size_t
+        L.surrogate_set_option.argtypes = [vp, C.c_int, C.c_int]
+        L.surrogate_set_option.restype = C.c_int
+        L.surrogate_status.argtypes = [vp]
+        L.surrogate_status.restype = C.c_int
         L._surrogate_declared = True
     return L
 
@@ -70,6 +74,16 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+    def set_option(self, option, value):
+        native.check(self.L.surrogate_set_option(self.h, int(option), int(value)))
+
+    def use_tcgen05(self, on=True):
+        """Forward layers on tcgen05 tensor cores (default) or on mma.sync."""
+        self.set_option(0, 1 if on else 0)
+
+    def check(self):
+        native.check(self.L.surrogate_status(self.h))
 
     def set_params(self, flat):
         import numpy as np

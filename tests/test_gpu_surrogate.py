@@ -60,11 +60,28 @@ def test_forward_matches_oracle(dev):
     s, flat = make(2, 512)
     X = feats(700, 1)
     pred = s.forward(to_dev(X, dev)).cpu().numpy()
+    s.check()
     for m, p in enumerate(L.unpack(flat, 2)):
         y, _ = S.forward(p, X, bf=True)
         err = np.abs(pred[m] - y)
         assert np.all(err <= 2e-2 * (1 + np.abs(y))), err.max()
         assert np.median(err) < 2e-3
+
+
+def test_tcgen05_and_mma_sync_forward_agree(dev):
+    """The two tensor-core paths of the forward layers (tcgen05 with TMEM
+    accumulators, mma.sync with register accumulators) see the same BF16
+    operands and accumulate in FP32: outputs agree to FP32 summation order and
+    the occasional one-step BF16 rounding difference of a hidden activation."""
+    s, flat = make(3, 1024)
+    X = to_dev(feats(2500, 9), dev)
+    s.use_tcgen05(True)
+    a = s.forward(X).cpu().numpy()
+    s.check()
+    s.use_tcgen05(False)
+    b = s.forward(X).cpu().numpy()
+    assert np.all(np.abs(a - b) <= 1e-2 * (1 + np.abs(b))), np.abs(a - b).max()
+    assert np.median(np.abs(a - b)) < 1e-3
 
 
 def test_gradients_match_oracle(dev):
