@@ -37,6 +37,7 @@ WORKLOADS = {
     "dense128": (64, "dense128", 5, 1),
     "uneven": (1_000_000, "uneven", 5, 3),
     "topk": (100_000, None, 10, 11),
+    "surfwd": (1 << 20, None, 0, 12),
 }
 ISSUE_LANES_PER_SM_CLK = 4 * 32  # 4 schedulers x 32 lanes per SM and clock
 # Algorithmic work per point for the issue roofline: the per-point figure of the
@@ -390,6 +391,53 @@ def surrogate_section(args, dev, a, ax, peaks):
     }
 
 
+def run_surfwd(args):
+    """Surrogate forward throughput: 2^20 rows x 5 members through the tcgen05 and the
+    mma.sync layer paths (CUDA events), against the measured BF16 tensor peak."""
+    import torch
+
+    from paper_1701_08547_gb300 import build as B
+    from paper_1701_08547_gb300.surrogate import Surrogate
+    from workloads import mlp as L
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    sur = Surrogate(members=5, batch=65536)
+    sur.set_params(L.init_params(5))
+    n = args.kernels or (1 << 20)
+    g = torch.Generator(device=dev)
+    g.manual_seed(12)
+    X = torch.randn(n, 128, generator=g, device=dev).to(torch.bfloat16)
+    pred = torch.empty((5, n), device=dev)
+    peaks, kind = measured_peaks()
+    out = {}
+    for name, tc in (("tcgen05", True), ("mma_sync", False)):
+        sur.use_tcgen05(tc)
+        for _ in range(args.warmup):
+            sur.forward(X, pred)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+        for i in range(args.steps):
+            ev[2 * i].record()
+            sur.forward(X, pred)
+            ev[2 * i + 1].record()
+        torch.cuda.synchronize()
+        ms = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)) / args.steps
+        tf = n * 5 * MLP_FWD_FLOP / (ms * 1e-3) / 1e12
+        out[name] = {"ms": ms, "rows_per_s": n / (ms * 1e-3), "tflops": tf,
+                     "frac_bf16_peak": tf / peaks.get("bf16_tflops", 1900.0)}
+    sur.check()
+    return {"metric": "surrogate forward rows/sec (5 members)", "value": out["tcgen05"]["rows_per_s"],
+            "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["tcgen05"]["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"surfwd: {n} rows x 5 members, 128 -> 256 x 4 -> 1"},
+            "roofline": {"bound": "tensor", "achieved": out["tcgen05"]["tflops"],
+                         "peak": peaks.get("bf16_tflops", 1900.0), "unit": "TFLOP/s",
+                         "frac": out["tcgen05"]["frac_bf16_peak"], "traffic": None, "peak_source": kind},
+            "paths": out}
+
+
 def run_topk(args):
     """Segmented top-k over external scores: 100,000 segments x 16,384 float32
     scores (the dense workload's point count), top-10; HBM-bound."""
@@ -530,6 +578,8 @@ def main():
         line = run_reference(args)
     elif args.workload == "topk":
         line = run_topk(args)
+    elif args.workload == "surfwd":
+        line = run_surfwd(args)
     else:
         line = run_ours(args)
     if line is not None:

@@ -303,11 +303,10 @@ int tc_layer(tune_surrogate* h, int l, int n_pad, cudaStream_t s, const __nv_bfl
     g.H = h->H[l];
     g.sH = (long long)h->batch * WID;
     g.status = h->status;
-    const int smem = 1024 + (kin / tc::BK) * (tc::BM * tc::BK * 2 + WID * tc::BK * 2);
+    const int smem = tc::smem_bytes(WID);
     static bool attr = false;
     if (!attr) {
-        TUNE_CUDA_TRY(cudaFuncSetAttribute(tc::gemm_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           1024 + tc::kMaxChunks * (tc::BM * tc::BK * 2 + WID * tc::BK * 2)),
+        TUNE_CUDA_TRY(cudaFuncSetAttribute(tc::gemm_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                       "surrogate: tc smem attribute");
         attr = true;
     }

@@ -22,7 +22,6 @@ namespace tc {
 constexpr int kThreads = 256;  // eight warps: two per TMEM lane quarter (column halves)
 constexpr int BM = 128;        // rows per CTA (UMMA M)
 constexpr int BK = 64;         // K elements per chunk (one 128-byte swizzle span)
-constexpr int kMaxChunks = 4;  // K <= 256
 constexpr long long kSpin = 1LL << 22;  // try_wait iterations before giving up
 
 struct Args {
@@ -120,14 +119,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 
-// grid: (M / 128, members). Dynamic shared memory: 1024 alignment slack + chunks x (16 KB + N x 128 B).
-// N: a multiple of 64 in [64, 256] (two column halves of whole 32-column loads).
+// grid: (M / 128, members). Dynamic shared memory: 1024 alignment slack + kStages x (16 KB + N x 128 B).
+// N: a multiple of 64 in [64, 256] (two column halves of whole 32-column loads). K chunks pass through a
+// ring of kStages stages so that two CTAs fit on an SM and one's epilogue overlaps the other's MMAs.
+constexpr int kStages = 2;
+
+__host__ __device__ constexpr int smem_bytes(int N) { return 1024 + kStages * (BM * BK * 2 + N * BK * 2); }
+
 __global__ void __launch_bounds__(kThreads) gemm_fwd_kernel(const __grid_constant__ CUtensorMap ta,
                                                             const __grid_constant__ CUtensorMap tb,
                                                             const __grid_constant__ Args g)
 {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t bar_full[kMaxChunks];
+    __shared__ uint64_t bar_full[kStages];
+    __shared__ uint64_t bar_done[kStages];
     __shared__ uint64_t bar_mma;
     __shared__ uint32_t tmem_base;
     __shared__ int ok_flag;
@@ -135,8 +140,8 @@ __global__ void __launch_bounds__(kThreads) gemm_fwd_kernel(const __grid_constan
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int n_chunks = g.K / BK;
     const uint32_t a_bytes = BM * BK * 2, b_bytes = (uint32_t)g.N * BK * 2;
-    uint8_t* sA = smem;                       // chunks x 16 KB
-    uint8_t* sB = smem + n_chunks * a_bytes;  // chunks x (N x 128 B)
+    uint8_t* sA = smem;                      // kStages x 16 KB
+    uint8_t* sB = smem + kStages * a_bytes;  // kStages x (N x 128 B)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM, member = blockIdx.y;
     const uint32_t n_cols = g.N <= 32 ? 32 : g.N <= 64 ? 64 : g.N <= 128 ? 128 : 256;
@@ -147,7 +152,10 @@ __global__ void __launch_bounds__(kThreads) gemm_fwd_kernel(const __grid_constan
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (threadIdx.x == 32) {
-        for (int c = 0; c < n_chunks; ++c) mbar_init(&bar_full[c], 1);
+        for (int c = 0; c < kStages; ++c) {
+            mbar_init(&bar_full[c], 1);
+            mbar_init(&bar_done[c], 1);
+        }
         mbar_init(&bar_mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         ok_flag = 1;
@@ -158,28 +166,39 @@ __global__ void __launch_bounds__(kThreads) gemm_fwd_kernel(const __grid_constan
     const uint32_t tmem = tmem_base;
 
     if (threadIdx.x == 0) {
-        // loads: all K chunks of this tile (K <= 256 fits in shared memory)
-        for (int c = 0; c < n_chunks; ++c) {
-            mbar_expect_tx(&bar_full[c], a_bytes + b_bytes);
-            tma_load_3d(sA + c * a_bytes, &ta, c * BK, m0, g.batched_a ? member : 0, &bar_full[c]);
-            tma_load_3d(sB + c * b_bytes, &tb, c * BK, 0, member, &bar_full[c]);
-        }
-        // MMAs as each chunk lands: four K = 16 steps per 64-wide chunk
+        auto load = [&](int c) {  // chunk c -> stage c % kStages
+            const int st = c % kStages;
+            mbar_expect_tx(&bar_full[st], a_bytes + b_bytes);
+            tma_load_3d(sA + st * a_bytes, &ta, c * BK, m0, g.batched_a ? member : 0, &bar_full[st]);
+            tma_load_3d(sB + st * b_bytes, &tb, c * BK, 0, member, &bar_full[st]);
+        };
+        for (int c = 0; c < n_chunks && c < kStages; ++c) load(c);
         const uint32_t idesc = idesc_bf16(BM, g.N);
+        int loaded = n_chunks < kStages ? n_chunks : kStages;
         bool ok = true;
-        for (int c = 0; c < n_chunks && ok; ++c) {
-            ok = mbar_wait(&bar_full[c], 0, g.status);
+        for (int c = 0; c < n_chunks; ++c) {
+            const int st = c % kStages;
+            ok = mbar_wait(&bar_full[st], (c / kStages) & 1, g.status);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)
-                mma_bf16(tmem, sdesc(sA + c * a_bytes + kk * 32), sdesc(sB + c * b_bytes + kk * 32), idesc,
+                mma_bf16(tmem, sdesc(sA + st * a_bytes + kk * 32), sdesc(sB + st * b_bytes + kk * 32), idesc,
                          (c | kk) != 0);
+            mma_commit(&bar_done[st]);
+            // refill the stage of the previous chunk once its MMAs are done
+            if (c >= 1 && c - 1 + kStages < n_chunks) {
+                const int pc = c - 1, pst = pc % kStages;
+                ok = mbar_wait(&bar_done[pst], (pc / kStages) & 1, g.status);
+                if (!ok) break;
+                load(pc + kStages);
+                ++loaded;
+            }
         }
         if (!ok) {
             ok_flag = 0;
             // let the copies already issued finish before the CTA exits
-            for (int c = 0; c < n_chunks; ++c) mbar_wait(&bar_full[c], 0, g.status);
+            for (int c = 0; c < loaded; ++c) mbar_wait(&bar_full[c % kStages], (c / kStages) & 1, g.status);
         }
         mma_commit(&bar_mma);  // arrives when the issued MMAs (if any) complete
     }
@@ -200,7 +219,13 @@ __global__ void __launch_bounds__(kThreads) gemm_fwd_kernel(const __grid_constan
             float v[32];
             tmem_ld32(lane_addr + c0, v);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] += bias[c0 + i];
+            for (int i = 0; i < 32; i += 4) {
+                const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + c0 + i));
+                v[i] += b4.x;
+                v[i + 1] += b4.y;
+                v[i + 2] += b4.z;
+                v[i + 3] += b4.w;
+            }
             if (Z) {
 #pragma unroll
                 for (int i = 0; i < 32; i += 4)
