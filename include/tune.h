@@ -316,6 +316,28 @@ int tune_emit_measure(const tune_axes* axes, const tune_kernel_desc* descs, int6
                       int32_t items, float count_scale, int32_t reps, float* us, int32_t* regs,
                       tune_stream_t stream);
 
+/*
+ * tune_suggest — static search-space pruning (Section III-C "Static Search
+ * Analysis", Section IV-C Table "Suggested parameters to achieve theoretical
+ * occupancy"). Per kernel, at its registers r0 and shared memory s0 and the
+ * largest shared-memory capacity:
+ *   t_star[i]     mask over the thread-count axis: the thread counts of the
+ *                 kernel's space reaching the best theoretical occupancy
+ *   occ_star[i]   that occupancy, W* / W_mp
+ *   r_headroom[i] registers that can be added while some thread count of
+ *                 T* still reaches occ* (R*)
+ *   s_star[i]     the largest shared memory per block keeping the block count
+ *                 at the smallest thread count of T* (S*)
+ *   t_rule[i]     the rule-based reduction: intensity (FP32 + FP64 counts over
+ *                 GLDST + SLDST counts) > 4.0 keeps the upper half of T*
+ *                 (floor(|T*| / 2) values, at least one), else the lower half.
+ * All outputs device arrays [n_kernels]; -1 headrooms for kernels with no valid point.
+ */
+int tune_suggest(const tune_arch* arch, const tune_axes* axes, const tune_kernel_desc* descs,
+                 int64_t n_kernels, uint32_t* t_star, float* occ_star, int32_t* r_headroom,
+                 int32_t* s_star, uint32_t* t_rule, void* workspace, size_t ws_bytes,
+                 tune_stream_t stream);
+
 /* Bytes of device workspace the call needs (at least 256). */
 size_t tune_workspace_bytes(int call, int64_t n, int32_t k);
 

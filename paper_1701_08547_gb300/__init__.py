@@ -12,7 +12,7 @@ from . import native
 from .native import (TUNE_EMIT_POINTS, TUNE_SCHED_CHUNK, TUNE_SCHED_CTAS,  # noqa: F401
                      TUNE_SCHED_THREAD, TUNE_SCHED_WARP, TuneError)
 
-__all__ = ["tune_eval", "tune_topk", "tune_autotune", "tune_features", "tune_workspace_bytes", "tune_check",
+__all__ = ["tune_eval", "tune_topk", "tune_autotune", "tune_features", "tune_suggest", "tune_workspace_bytes", "tune_check",
            "descs_to_device", "TUNE_EMIT_POINTS", "TUNE_SCHED_WARP", "TUNE_SCHED_THREAD",
            "TUNE_SCHED_CHUNK", "TUNE_SCHED_CTAS", "TuneError"]
 
@@ -139,6 +139,28 @@ def tune_features(arch, axes, descs, sample_kernel, sample_point, feats=None, wo
                          _ptr(feats), _ptr(workspace_buf), workspace_buf.numel(), _stream(stream))
     native.check(rc)
     return feats
+
+
+def tune_suggest(arch, axes, descs, workspace_buf=None, stream=None):
+    """Static pruning per kernel: dict of device tensors t_star, occ_star, r_headroom, s_star, t_rule."""
+    torch = _torch()
+    L = native.load()
+    n = descs.numel() * descs.element_size() // 64
+    dev = descs.device
+    out = {"t_star": torch.empty(n, dtype=torch.int32, device=dev),
+           "occ_star": torch.empty(n, dtype=torch.float32, device=dev),
+           "r_headroom": torch.empty(n, dtype=torch.int32, device=dev),
+           "s_star": torch.empty(n, dtype=torch.int32, device=dev),
+           "t_rule": torch.empty(n, dtype=torch.int32, device=dev)}
+    if workspace_buf is None:
+        workspace_buf = workspace(native.TUNE_CALL_EVAL, 0, 1, dev)
+    a = native.make_arch(arch)
+    x = native.make_axes(axes)
+    rc = L.tune_suggest(C.byref(a), C.byref(x), _ptr(descs), n, _ptr(out["t_star"]), _ptr(out["occ_star"]),
+                        _ptr(out["r_headroom"]), _ptr(out["s_star"]), _ptr(out["t_rule"]), _ptr(workspace_buf),
+                        workspace_buf.numel(), _stream(stream))
+    native.check(rc)
+    return out
 
 
 def tune_check(workspace_buf, stream=None):

@@ -83,6 +83,8 @@ def load():
     L.tune_autotune.restype = C.c_int
     L.tune_features.argtypes = [C.POINTER(TuneArch), C.POINTER(TuneAxes), vp, vp, vp, i64, vp, vp, sz, vp]
     L.tune_features.restype = C.c_int
+    L.tune_suggest.argtypes = [C.POINTER(TuneArch), C.POINTER(TuneAxes), vp, i64, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.tune_suggest.restype = C.c_int
     _lib = L
     return L
 
