@@ -214,7 +214,7 @@ int tune_topk(const float* scores, const int64_t* seg_offsets, int64_t n_seg, in
  *
  * An ensemble of MLPs predicting ln(runtime in microseconds) of a tuning
  * point from 48 static features (zero-padded to 128 inputs): 128 -> 256 ->
- * 256 -> 256 -> 256 -> 1 with exact GELU, BF16 weights and activations, FP32
+ * 256 -> 256 -> 256 -> 1 with GELU (tanh form), BF16 weights and activations, FP32
  * accumulation, FP32 master weights, Adam, MSE loss. All members are trained
  * together on the same batches by the library's BF16 tensor-core kernels.
  * Unlike the tune_* calls, a surrogate handle owns device memory (weights,
@@ -242,9 +242,12 @@ int surrogate_param_count(void);
 int surrogate_set_params(tune_surrogate* h, const float* host, int64_t n);
 /* Copy to host: what = 0 master weights, 1 gradients of the last step, 2 Adam m, 3 Adam v
  * (members x param_count floats), 4 last loss per member (members floats), 5 last
- * predictions (members x batch). Synchronous. */
+ * predictions (members x batch), 6 the E4M3 codes of W2..W4 as their values (members x 3
+ * x 256 x 256), 7 the per-row scales of those codes (members x 3 x 256). Synchronous. */
 int surrogate_get(tune_surrogate* h, int what, float* host, int64_t n);
-/* pred (device, [members, n]) = each member's output for feats (device bf16 [n, 128]). */
+/* pred (device, [members, n]) = each member's output for feats (device bf16 [n, 128]).
+ * By default one persistent launch runs every member over 128-row tiles with the
+ * activations kept on chip (option 1). feats must be 16-byte aligned. */
 int surrogate_forward(tune_surrogate* h, const uint16_t* feats, int64_t n, float* pred, tune_stream_t stream);
 /* One step on rows feats[0..n), labels[0..n) (device), 1 <= n <= batch: forward, MSE
  * loss, backward into the gradient buffer, and (apply_update != 0) one Adam step. */
@@ -258,8 +261,11 @@ int surrogate_train(tune_surrogate* h, const uint16_t* feats, const float* label
 
 /* Ensemble size of a handle (0 for NULL). */
 int surrogate_members(const tune_surrogate* h);
-/* Options: 0 = forward layers on tcgen05 tensor cores (value 1, the default) or on
- * mma.sync (value 0). */
+/* Options: 0 = layer-by-layer forward on tcgen05 tensor cores (value 1, the default) or
+ * on mma.sync (value 0); 1 = how surrogate_forward / surrogate_infer run the ensemble:
+ * 0 layer by layer (option 0 picks the GEMM), 1 fused BF16 (default), 2 fused with
+ * layers 2-4 on E4M3 codes: W2..W4 quantised per output row (scale = max |w| / 448,
+ * nearest-even, saturating), activations with unit scale, FP32 accumulation. */
 int surrogate_set_option(tune_surrogate* h, int option, int value);
 /* Synchronous: TUNE_ETIMEOUT if a bounded wait inside a surrogate kernel gave up. */
 int surrogate_status(tune_surrogate* h);

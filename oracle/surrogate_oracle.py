@@ -2,15 +2,24 @@
 
 TEST INFRASTRUCTURE ONLY (tests, smoke, bench CPU baseline); shares no code
 with the CUDA kernels. Textbook formulas:
-  z_l = W_l h_{l-1} + b_l, h_l = GELU(z_l) = z Phi(z) (Phi the standard normal CDF, exact
-  via erf), y = w5 . h_4 + b5, L = mean (y - t)^2;
+  z_l = W_l h_{l-1} + b_l, h_l = GELU(z_l), GELU in its tanh form (Hendrycks & Gimpel):
+  GELU(z) = z/2 (1 + tanh(u)), u = sqrt(2/pi) (z + 0.044715 z^3); y = w5 . h_4 + b5,
+  L = mean (y - t)^2;
   dL/dy = 2 (y - t) / n; dz_4 = dy w5 * GELU'(z_4); dz_{l-1} = (W_l^T dz_l) * GELU'(z_{l-1});
-  dW_l = sum_rows dz_l h_{l-1}^T, db_l = sum_rows dz_l; GELU'(z) = Phi(z) + z phi(z);
+  dW_l = sum_rows dz_l h_{l-1}^T, db_l = sum_rows dz_l;
+  GELU'(z) = (1 + tanh u)/2 + z/2 (1 - tanh^2 u) sqrt(2/pi) (1 + 3 * 0.044715 z^2);
   Adam (Kingma & Ba 2015): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
   w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
 With bf16=True, the values the method stores in BF16 (inputs, weights, activations h_l
 and the back-propagated dz_l) are rounded to BF16 (via FP32, round-to-nearest-even) at
 the same points; all arithmetic stays FP64.
+
+FP8 inference (forward_fp8): layers 2-4 take E4M3 operands (OCP FP8: 4 exponent bits,
+bias 7, 3 mantissa bits, largest finite 448, subnormal spacing 2^-9). Weights are scaled
+per output row: s_n = max_k |W[n][k]| / 448 (1 if the row is zero), code = E4M3(W / s_n),
+both steps in FP32 as the kernel takes them (the codes are integers: both sides decide
+them in the same precision); activations are quantised with unit scale. Rounding to
+E4M3 is to nearest, ties to even, saturating at +-448.
 """
 
 import math
@@ -19,7 +28,6 @@ import numpy as np
 
 from workloads import mlp as L
 
-_erf = np.vectorize(math.erf, otypes=[np.float64])
 
 
 def bf16(x):
@@ -30,12 +38,41 @@ def bf16(x):
     return rounded.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+GELU_K = math.sqrt(2.0 / math.pi)
+GELU_C = 0.044715
+
+
 def gelu(z):
-    return 0.5 * z * (1.0 + _erf(z / math.sqrt(2.0)))
+    z = np.asarray(z, dtype=np.float64)
+    return 0.5 * z * (1.0 + np.tanh(GELU_K * (z + GELU_C * z ** 3)))
 
 
 def gelu_grad(z):
-    return 0.5 * (1.0 + _erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+    z = np.asarray(z, dtype=np.float64)
+    t = np.tanh(GELU_K * (z + GELU_C * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * GELU_K * (1.0 + 3.0 * GELU_C * z * z)
+
+
+E4M3_MAX = 448.0
+
+
+def e4m3(x):
+    """Round to the E4M3 grid (nearest, ties to even, saturating at +-448); float64 values."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    _, e = np.frexp(a)                           # a = m 2^e, m in [0.5, 1)
+    E = np.maximum(e - 1, -6)                    # binade exponent; below 2^-6 the subnormal spacing
+    step = np.ldexp(1.0, E - 3)                  # 3 mantissa bits
+    q = np.minimum(np.rint(a / step) * step, E4M3_MAX)
+    return np.copysign(q, x)
+
+
+def quantize_rows(W):
+    """Per-row E4M3 quantisation of a weight matrix, in FP32 like the kernel: (codes, scales)."""
+    W32 = np.asarray(W, dtype=np.float32)
+    amax = np.max(np.abs(W32), axis=1)
+    s = np.where(amax > 0, amax / np.float32(E4M3_MAX), np.float32(1.0)).astype(np.float32)
+    return e4m3(W32 / s[:, None]), s
 
 
 def _r(x, on):
@@ -53,6 +90,19 @@ def forward(p, X, bf=True):
         cache[f"z{l}"], cache[f"h{l}"] = z, h
     y = h @ np.asarray(p["w5"], np.float64) + float(p["b5"][0])
     return y, cache
+
+
+def forward_fp8(p, X):
+    """Forward with layer 1 in BF16 and layers 2-4 on E4M3 codes (see the module header):
+    z_l = s_l * (E4M3(h_{l-1}) . codes_l) + b_l; the head reads BF16(h_4)."""
+    h = bf16(X)
+    z = h @ bf16(p["W1"]).T + np.asarray(p["b1"], np.float64)
+    h = gelu(z)
+    for l in range(2, 5):
+        q, s = quantize_rows(p[f"W{l}"])
+        z = (e4m3(h) @ q.T) * s.astype(np.float64) + np.asarray(p[f"b{l}"], np.float64)
+        h = gelu(z)
+    return bf16(h) @ np.asarray(p["w5"], np.float64) + float(p["b5"][0])
 
 
 def loss_and_grads(p, X, t, bf=True):

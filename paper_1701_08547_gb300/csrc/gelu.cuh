@@ -1,0 +1,36 @@
+// GELU of the surrogate's hidden layers, tanh form (Hendrycks & Gimpel):
+//   gelu(z)  = z/2 (1 + tanh(u)),  u = sqrt(2/pi) (z + 0.044715 z^3)
+//   gelu'(z) = (1 + tanh(u))/2 + z/2 (1 - tanh(u)^2) sqrt(2/pi) (1 + 3 * 0.044715 z^2)
+// tanh is the hardware approximation (tanh.approx.f32, about 2^-11 relative
+// error), one multi-function-unit operation per element.
+#pragma once
+
+namespace mlp {
+
+constexpr float kGeluK = 0.7978845608028654f;  // sqrt(2 / pi)
+constexpr float kGeluC = 0.044715f;
+
+__device__ __forceinline__ float tanh_hw(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float gelu(float z)
+{
+    const float p = fmaf(kGeluC, z * z, 1.0f);
+    const float t = tanh_hw((kGeluK * z) * p);
+    const float hz = 0.5f * z;
+    return fmaf(hz, t, hz);
+}
+
+__device__ __forceinline__ float gelu_grad(float z)
+{
+    const float z2 = z * z;
+    const float t = tanh_hw((kGeluK * z) * fmaf(kGeluC, z2, 1.0f));
+    const float du = kGeluK * fmaf(3.0f * kGeluC, z2, 1.0f);
+    return fmaf(0.5f * z * du, fmaf(-t, t, 1.0f), 0.5f * (1.0f + t));
+}
+
+}  // namespace mlp

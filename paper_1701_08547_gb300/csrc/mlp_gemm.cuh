@@ -10,6 +10,8 @@
 // K a multiple of 32, leading dimensions multiples of 8 elements.
 #pragma once
 
+#include "gelu.cuh"
+
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -43,14 +45,6 @@ struct GemmArgs {
     long long sSplit;  // stride between split slices of F
 };
 
-__device__ __forceinline__ float gelu_exact(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-
-__device__ __forceinline__ float gelu_grad(float z)
-{
-    const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
-    const float pdf = 0.39894228040143268f * expf(-0.5f * z * z);
-    return cdf + z * pdf;
-}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -221,7 +215,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(const __grid_co
                     const float z1 = v1 + g.bias[batch * g.sBias + n + 1];
                     if (g.Z) *reinterpret_cast<float2*>(g.Z + batch * g.sZ + off) = make_float2(z0, z1);
                     *reinterpret_cast<__nv_bfloat162*>(g.H + batch * g.sH + off) =
-                        __floats2bfloat162_rn(gelu_exact(z0), gelu_exact(z1));
+                        __floats2bfloat162_rn(gelu(z0), gelu(z1));
                 } else if (EPI == EPI_GELU_GRAD) {
                     const float2 z = *reinterpret_cast<const float2*>(g.Z + batch * g.sZ + off);
                     *reinterpret_cast<__nv_bfloat162*>(g.H + batch * g.sH + off) =

@@ -1,5 +1,5 @@
 // Learned surrogate of the static cost: an ensemble of MLPs
-// (128 inputs = 48 features + zero padding -> 256 -> 256 -> 256 -> 256 -> 1, exact GELU),
+// (128 inputs = 48 features + zero padding -> 256 -> 256 -> 256 -> 256 -> 1, GELU in tanh form),
 // BF16 weights and activations, FP32 accumulation, FP32 master weights, Adam,
 // trained by this file's kernels (forward, backward, optimiser) on the GPU.
 // Members are batched through the grouped GEMM (blockIdx.z = member).
@@ -10,10 +10,12 @@
 
 #include <vector>
 
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include "mlp_gemm.cuh"
 #include "tc_gemm.cuh"
+#include "tc_mlp.cuh"
 #include "tune_internal.h"
 
 using mlp::GemmArgs;
@@ -54,6 +56,10 @@ struct tune_surrogate {
     void* block = nullptr;              // the one device allocation
     int* status = nullptr;              // device status word (timeouts of bounded waits)
     int use_tc = 1;                     // forward layers on tcgen05 (1) or mma.sync (0)
+    int fwd_mode = 1;                   // surrogate_forward: 0 layer by layer, 1 fused BF16, 2 fused FP8
+    uint8_t* w8 = nullptr;              // E4M3 codes of W2..W4 [members][3][256][256]
+    float* wscale = nullptr;            // their per-row scales [members][3][256]
+    bool fp8_stale = true;              // master weights changed since the last quantisation
 };
 
 namespace {
@@ -209,6 +215,27 @@ __global__ void cast_weights(const float* master, __nv_bfloat16* wbf, int member
     wbf[e] = __float2bfloat16_rn(master[mem * P + OFF_W(l) + (q - BOFF_W(l))]);
 }
 
+// Per-row E4M3 quantisation of W2..W4 (FP32, as the oracle mirrors it): s = max |w| / 448
+// (1 for a zero row), code = E4M3(w / s), nearest-even, saturating. grid (256, 3, members) x 256.
+__global__ void quantize_fp8(const float* __restrict__ master, uint8_t* w8, float* wscale)
+{
+    const int row = blockIdx.x, l = blockIdx.y + 1, mem = blockIdx.z;
+    const float w = master[mem * P + OFF_W(l) + (long long)row * WID + threadIdx.x];
+    __shared__ float red[WID / 32];
+    float a = fabsf(w);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    float amax = 0.0f;
+#pragma unroll
+    for (int i = 0; i < WID / 32; ++i) amax = fmaxf(amax, red[i]);
+    const float sc = amax > 0.0f ? __fdiv_rn(amax, 448.0f) : 1.0f;
+    const long long r = ((long long)mem * 3 + (l - 1)) * WID + row;
+    w8[r * WID + threadIdx.x] = __nv_cvt_float_to_fp8(__fdiv_rn(w, sc), __NV_SATFINITE, __NV_E4M3);
+    if (threadIdx.x == 0) wscale[r] = sc;
+}
+
 // Batch gather: xin[r] = feats[order[r]], lbl[r] = labels[order[r]] (rows past n are zero).
 __global__ void gather_batch(const __nv_bfloat16* __restrict__ feats, const float* __restrict__ labels,
                              const int32_t* __restrict__ order, int n, int batch, __nv_bfloat16* xin, float* lbl)
@@ -313,6 +340,93 @@ int tc_layer(tune_surrogate* h, int l, int n_pad, cudaStream_t s, const __nv_bfl
     tc::gemm_fwd_kernel<<<dim3(n_pad / tc::BM, h->members), tc::kThreads, smem, s>>>(ta, tb, g);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: tc gemm launch");
     return TUNE_OK;
+}
+
+// N-D map (N <= 4) with 128-byte swizzle; strides in bytes for dimensions 1..N-1.
+int make_map_nd(CUtensorMap* map, CUtensorMapDataType dt, int rank, const void* base, const cuuint64_t* dims,
+                const cuuint64_t* strides, const cuuint32_t* box)
+{
+    auto fn = encode_fn();
+    if (!fn) return tune::fail(TUNE_ECUDA, "surrogate: cuTensorMapEncodeTiled unavailable");
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = fn(map, dt, rank, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return tune::fail(TUNE_ECUDA, "surrogate: cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return TUNE_OK;
+}
+
+int refresh_fp8(tune_surrogate* h, cudaStream_t s)
+{
+    if (!h->fp8_stale) return TUNE_OK;
+    quantize_fp8<<<dim3(WID, NL - 1, h->members), WID, 0, s>>>(h->master, h->w8, h->wscale);
+    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: quantize launch");
+    h->fp8_stale = false;
+    return TUNE_OK;
+}
+
+template <bool FP8>
+int launch_fused(const CUtensorMap& tx, const CUtensorMap& tw1, const CUtensorMap& tw, const tcm::Args& g,
+                 unsigned grid, cudaStream_t s)
+{
+    constexpr int smem = tcm::Cfg<FP8>::smem;
+    static bool attr = false;
+    if (!attr) {
+        TUNE_CUDA_TRY(cudaFuncSetAttribute(tcm::mlp_infer_kernel<FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           smem),
+                      "surrogate: fused smem attribute");
+        attr = true;
+    }
+    tcm::mlp_infer_kernel<FP8><<<grid, tcm::kThreads, smem, s>>>(tx, tw1, tw, g);
+    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: fused launch");
+    return TUNE_OK;
+}
+
+// Whole-ensemble forward of n feature rows in one persistent launch (tc_mlp.cuh):
+// pred[m][i] for every member; BF16 throughout, or layers 2-4 on E4M3 codes.
+int fused_forward(tune_surrogate* h, const __nv_bfloat16* feats, int64_t n, float* pred, bool fp8, cudaStream_t s)
+{
+    if (n <= 0) return TUNE_OK;
+    if (n > (1LL << 30)) return tune::fail(TUNE_EINVAL, "surrogate_forward: more than 2^30 rows");
+    if (fp8) {
+        int rc = refresh_fp8(h, s);
+        if (rc) return rc;
+    }
+    CUtensorMap tx, tw1, tw;
+    const cuuint64_t xd[2] = {IN, (cuuint64_t)n}, xs[1] = {IN * 2};
+    const cuuint32_t xb[2] = {64, tcm::kRows};
+    int rc = make_map_nd(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, feats, xd, xs, xb);
+    if (rc) return rc;
+    const cuuint64_t d1[3] = {IN, WID, (cuuint64_t)h->members}, s1[2] = {IN * 2, PB * 2};
+    const cuuint32_t b1[3] = {64, WID, 1};
+    rc = make_map_nd(&tw1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, h->wbf, d1, s1, b1);
+    if (rc) return rc;
+    const cuuint64_t dw[4] = {WID, WID, NL - 1, (cuuint64_t)h->members};
+    if (fp8) {
+        const cuuint64_t sw[3] = {WID, WID * WID, (NL - 1) * WID * WID};
+        const cuuint32_t bw[4] = {128, WID, 1, 1};
+        rc = make_map_nd(&tw, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, h->w8, dw, sw, bw);
+    } else {
+        const cuuint64_t sw[3] = {WID * 2, WID * WID * 2, PB * 2};
+        const cuuint32_t bw[4] = {64, WID, 1, 1};
+        rc = make_map_nd(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, h->wbf + BOFF_W(1), dw, sw, bw);
+    }
+    if (rc) return rc;
+    tcm::Args g;
+    g.n = (int)n;
+    g.members = h->members;
+    g.units = (n + tcm::kRows - 1) / tcm::kRows * h->members;
+    g.master = h->master;
+    g.P = P;
+    for (int l = 0; l < NL; ++l) g.off_b[l] = OFF_B(l);
+    g.off_w5 = OFF_W5;
+    g.off_b5 = OFF_B5;
+    g.wscale = h->wscale;
+    g.pred = pred;
+    g.status = h->status;
+    const long long sms = tune::device_sm_count();
+    const unsigned grid = (unsigned)(g.units < sms ? g.units : sms);
+    return fp8 ? launch_fused<true>(tx, tw1, tw, g, grid, s) : launch_fused<false>(tx, tw1, tw, g, grid, s);
 }
 
 // Forward through all members for rows [0, n_pad) of h->xin (n_pad a multiple of 128).
@@ -426,6 +540,7 @@ int adam(tune_surrogate* h, cudaStream_t s)
     const long long total = (long long)h->members * P;
     adam_update<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h->master, h->grad, h->m, h->v, h->wbf, h->members,
                                                                  h->lr, h->b1, h->b2, h->eps, c1, c2);
+    h->fp8_stale = true;
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: adam launch");
     return TUNE_OK;
 }
@@ -452,6 +567,11 @@ int surrogate_set_option(tune_surrogate* h, int option, int value)
     if (!h) return tune::fail(TUNE_EINVAL, "surrogate_set_option: NULL handle");
     if (option == 0) {
         h->use_tc = value != 0;
+        return TUNE_OK;
+    }
+    if (option == 1) {
+        if (value < 0 || value > 2) return tune::fail(TUNE_EINVAL, "surrogate_set_option: forward mode outside 0..2");
+        h->fwd_mode = value;
         return TUNE_OK;
     }
     return tune::fail(TUNE_EINVAL, "surrogate_set_option: unknown option %d", option);
@@ -497,6 +617,8 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     add(M * 4);
     add(M * KSPLIT * WID * WID * 4);
     add(256);
+    add(M * (NL - 1) * WID * WID);
+    add(M * (NL - 1) * WID * 4);
     cudaError_t e = cudaMalloc(&h->block, bytes);
     if (e != cudaSuccess) {
         delete h;
@@ -520,6 +642,8 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     h->loss = carve<float>(p, M);
     h->part = carve<float>(p, M * KSPLIT * WID * WID);
     h->status = carve<int>(p, 64);
+    h->w8 = carve<uint8_t>(p, M * (NL - 1) * WID * WID);
+    h->wscale = carve<float>(p, M * (NL - 1) * WID);
     *out = h;
     return TUNE_OK;
 }
@@ -539,6 +663,7 @@ int surrogate_set_params(tune_surrogate* h, const float* host, int64_t n)
     TUNE_CUDA_TRY(cudaMemset(h->m, 0, n * sizeof(float)), "set_params: reset m");
     TUNE_CUDA_TRY(cudaMemset(h->v, 0, n * sizeof(float)), "set_params: reset v");
     h->step = 0;
+    h->fp8_stale = true;
     const long long tot = (long long)h->members * PB;
     cast_weights<<<(unsigned)((tot + 255) / 256), 256>>>(h->master, h->wbf, h->members);
     TUNE_CUDA_TRY(cudaGetLastError(), "set_params: cast");
@@ -560,6 +685,27 @@ int surrogate_get(tune_surrogate* h, int what, float* host, int64_t n)
         src = h->y;
         cnt = (int64_t)h->members * h->batch;
     }
+    if (what == 6 || what == 7) {  // E4M3 codes of W2..W4 (decoded), their row scales
+        const int64_t rows = (int64_t)h->members * (NL - 1) * WID;
+        if (n != (what == 6 ? rows * WID : rows)) return tune::fail(TUNE_EINVAL, "surrogate_get: bad size");
+        int rc = refresh_fp8(h, 0);
+        if (rc) return rc;
+        TUNE_CUDA_TRY(cudaDeviceSynchronize(), "surrogate_get: sync");
+        if (what == 7) {
+            TUNE_CUDA_TRY(cudaMemcpy(host, h->wscale, n * sizeof(float), cudaMemcpyDeviceToHost), "surrogate_get: copy");
+            return TUNE_OK;
+        }
+        std::vector<uint8_t> codes(n);
+        TUNE_CUDA_TRY(cudaMemcpy(codes.data(), h->w8, n, cudaMemcpyDeviceToHost), "surrogate_get: copy");
+        for (int64_t i = 0; i < n; ++i) {  // E4M3: sign, 4 exponent bits (bias 7), 3 mantissa bits
+            const uint8_t b = codes[i];
+            const int e = (b >> 3) & 15, m = b & 7;
+            float v = e ? ldexpf(1.0f + m / 8.0f, e - 7) : ldexpf(m / 8.0f, -6);
+            if (e == 15 && m == 7) v = NAN;
+            host[i] = (b & 0x80) ? -v : v;
+        }
+        return TUNE_OK;
+    }
     if (!src || n != cnt) return tune::fail(TUNE_EINVAL, "surrogate_get: bad selector or size");
     TUNE_CUDA_TRY(cudaDeviceSynchronize(), "surrogate_get: sync");
     TUNE_CUDA_TRY(cudaMemcpy(host, src, n * sizeof(float), cudaMemcpyDeviceToHost), "surrogate_get: copy");
@@ -572,6 +718,7 @@ int surrogate_forward(tune_surrogate* h, const uint16_t* feats, int64_t n, float
     if (!h || (n > 0 && (!feats || !pred))) return tune::fail(TUNE_EINVAL, "surrogate_forward: NULL argument");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const auto* f = reinterpret_cast<const __nv_bfloat16*>(feats);
+    if (h->fwd_mode != 0) return fused_forward(h, f, n, pred, h->fwd_mode == 2, s);
     for (int64_t r0 = 0; r0 < n; r0 += h->batch) {
         const int nb = (int)((n - r0) < h->batch ? (n - r0) : h->batch);
         const int n_pad = (nb + 127) / 128 * 128;

@@ -17,6 +17,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "gelu.cuh"
+
 namespace tc {
 
 constexpr int kThreads = 256;  // eight warps: two per TMEM lane quarter (column halves)
@@ -117,7 +119,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+using mlp::gelu;
 
 // grid: (M / 128, members). Dynamic shared memory: 1024 alignment slack + kStages x (16 KB + N x 128 B).
 // N: a multiple of 64 in [64, 256] (two column halves of whole 32-column loads). K chunks pass through a

@@ -53,7 +53,8 @@ def _stream(stream):
 class Surrogate:
     """A handle to an MLP ensemble living on the GPU."""
 
-    GET_PARAMS, GET_GRADS, GET_M, GET_V, GET_LOSS, GET_PRED = range(6)
+    GET_PARAMS, GET_GRADS, GET_M, GET_V, GET_LOSS, GET_PRED, GET_FP8_CODES, GET_FP8_SCALES = range(8)
+    FWD_LAYERED, FWD_FUSED_BF16, FWD_FUSED_FP8 = range(3)
 
     def __init__(self, members=5, batch=8192, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         self.L = _lib()
@@ -82,6 +83,11 @@ class Surrogate:
         """Forward layers on tcgen05 tensor cores (default) or on mma.sync."""
         self.set_option(0, 1 if on else 0)
 
+    def set_forward_mode(self, mode):
+        """forward()/infer(): layer by layer (0), one fused launch in BF16 (1, the default),
+        or fused with layers 2-4 on E4M3 codes (2)."""
+        self.set_option(1, mode)
+
     def check(self):
         native.check(self.L.surrogate_status(self.h))
 
@@ -94,7 +100,8 @@ class Surrogate:
     def get(self, what):
         import numpy as np
 
-        n = {4: self.members, 5: self.members * self.batch}.get(what, self.members * self.P)
+        n = {4: self.members, 5: self.members * self.batch, 6: self.members * 3 * 256 * 256,
+             7: self.members * 3 * 256}.get(what, self.members * self.P)
         out = np.empty(n, dtype=np.float32)
         native.check(self.L.surrogate_get(self.h, what, out.ctypes.data, n))
         return out

@@ -1,5 +1,6 @@
 """Pins of the MLP oracle: GELU values, gradients by central differences,
-Adam's first step in closed form, BF16 rounding against torch's conversion."""
+Adam's first step in closed form, BF16 and E4M3 rounding against torch's
+conversions, the FP8 forward against the FP64 forward."""
 
 import math
 
@@ -11,15 +12,54 @@ from workloads import mlp as L
 
 
 def test_gelu_values():
-    # GELU(z) = z Phi(z): Phi(1) = 0.8413447460685429, Phi(-1) = 0.15865525393145707
-    assert S.gelu(np.array([1.0]))[0] == pytest.approx(0.8413447460685429, rel=1e-15)
-    assert S.gelu(np.array([-1.0]))[0] == pytest.approx(-0.15865525393145707, rel=1e-15)
+    torch = pytest.importorskip("torch")
+    z = np.concatenate([np.linspace(-8, 8, 161), [1.0, -1.0, 0.5, 30.0, -30.0]])
+    want = torch.nn.functional.gelu(torch.tensor(z, dtype=torch.float64), approximate="tanh").numpy()
+    assert np.allclose(S.gelu(z), want, rtol=1e-14, atol=1e-15)
+    # tanh form against the erf definition z Phi(z): Phi(1) = 0.8413447460685429; the two
+    # forms differ by less than 1e-3 everywhere (Hendrycks & Gimpel)
+    assert abs(S.gelu(np.array([1.0]))[0] - 0.8413447460685429) < 1e-3
+    exact = np.array([0.5 * x * (1 + math.erf(x / math.sqrt(2))) for x in z])
+    assert np.max(np.abs(S.gelu(z) - exact)) < 1e-3
     assert S.gelu(np.array([0.0]))[0] == 0.0
     assert S.gelu_grad(np.array([0.0]))[0] == 0.5
-    z = np.linspace(-4, 4, 33)
+    zz = np.linspace(-4, 4, 33)
     h = 1e-6
-    fd = (S.gelu(z + h) - S.gelu(z - h)) / (2 * h)
-    assert np.allclose(S.gelu_grad(z), fd, atol=1e-8)
+    fd = (S.gelu(zz + h) - S.gelu(zz - h)) / (2 * h)
+    assert np.allclose(S.gelu_grad(zz), fd, atol=1e-8)
+
+
+def test_e4m3_rounding():
+    """E4M3 (OCP FP8): against torch's float8_e4m3fn conversion inside the finite range, ties to
+    even, subnormals, saturation."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(50000) * 50, rng.standard_normal(50000) * 0.01,
+                        rng.uniform(-448, 448, 20000)]).astype(np.float32)
+    want = torch.tensor(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(S.e4m3(x), want)
+    # 1 + 1/16 lies halfway between 1 and 1.125 (even: 1); 1 + 3/16 between 1.125 and 1.25 (even: 1.25)
+    cases = {1 + 1 / 16: 1.0, 1 + 3 / 16: 1.25, 2.0 ** -9: 2.0 ** -9, 2.0 ** -10: 0.0, 3 * 2.0 ** -10: 2.0 ** -8,
+             448.0: 448.0, 460.0: 448.0, 1e6: 448.0, -1e6: -448.0, 0.0: 0.0, 240.0: 240.0, 250.0: 256.0}
+    for a, b in cases.items():
+        assert S.e4m3(np.array([a]))[0] == b, a
+
+
+def test_fp8_quantization_and_forward():
+    flat = L.init_params(1, [5])
+    p = L.unpack(flat, 1)[0]
+    q, s = S.quantize_rows(p["W2"])
+    assert q.shape == (256, 256) and s.dtype == np.float32
+    assert np.all(np.max(np.abs(q), axis=1) == 448.0)        # each row's largest weight maps to 448
+    assert np.array_equal(q, S.e4m3(q))                     # codes lie on the grid
+    rel = np.abs(q * s[:, None] - p["W2"]) / np.max(np.abs(p["W2"]), axis=1, keepdims=True)
+    assert rel.max() <= 2.0 ** -4 * 1.0001                  # half a step of 3 mantissa bits
+    X = np.zeros((300, L.IN))
+    X[:, :L.FEATURES] = np.random.default_rng(1).standard_normal((300, L.FEATURES))
+    y8 = S.forward_fp8(p, X)
+    y, _ = S.forward(p, X, bf=False)
+    err = np.abs(y8 - y)
+    assert np.max(err) < 0.1 * (1 + np.max(np.abs(y))) and np.median(err) < 0.02, (err.max(), np.median(err))
 
 
 def test_bf16_rounding_matches_torch():
