@@ -18,8 +18,8 @@ FP8 inference (forward_fp8): layers 2-4 take E4M3 operands (OCP FP8: 4 exponent 
 bias 7, 3 mantissa bits, largest finite 448, subnormal spacing 2^-9). Weights are scaled
 per output row: s_n = max_k |W[n][k]| / 448 (1 if the row is zero), code = E4M3(W / s_n),
 both steps in FP32 as the kernel takes them (the codes are integers: both sides decide
-them in the same precision); activations are quantised with unit scale. Rounding to
-E4M3 is to nearest, ties to even, saturating at +-448.
+them in the same precision); activations are quantised with scale 1/2 (codes of 2 h).
+Rounding to E4M3 is to nearest, ties to even, saturating at +-448.
 """
 
 import math
@@ -94,15 +94,15 @@ def forward(p, X, bf=True):
 
 def forward_fp8(p, X):
     """Forward with layer 1 in BF16 and layers 2-4 on E4M3 codes (see the module header):
-    z_l = s_l * (E4M3(h_{l-1}) . codes_l) + b_l; the head reads BF16(h_4)."""
+    z_l = (s_l / 2) (E4M3(2 h_{l-1}) . codes_l) + b_l; the head reads h_4 unrounded."""
     h = bf16(X)
     z = h @ bf16(p["W1"]).T + np.asarray(p["b1"], np.float64)
     h = gelu(z)
     for l in range(2, 5):
         q, s = quantize_rows(p[f"W{l}"])
-        z = (e4m3(h) @ q.T) * s.astype(np.float64) + np.asarray(p[f"b{l}"], np.float64)
+        z = (e4m3(2.0 * h) @ q.T) * (0.5 * s.astype(np.float64)) + np.asarray(p[f"b{l}"], np.float64)
         h = gelu(z)
-    return bf16(h) @ np.asarray(p["w5"], np.float64) + float(p["b5"][0])
+    return h @ np.asarray(p["w5"], np.float64) + float(p["b5"][0])
 
 
 def loss_and_grads(p, X, t, bf=True):

@@ -59,6 +59,7 @@ struct tune_surrogate {
     int fwd_mode = 1;                   // surrogate_forward: 0 layer by layer, 1 fused BF16, 2 fused FP8
     uint8_t* w8 = nullptr;              // E4M3 codes of W2..W4 [members][3][256][256]
     float* wscale = nullptr;            // their per-row scales [members][3][256]
+    float* wscale_half = nullptr;       // the scales halved (the fused epilogue's multipliers)
     bool fp8_stale = true;              // master weights changed since the last quantisation
 };
 
@@ -217,7 +218,7 @@ __global__ void cast_weights(const float* master, __nv_bfloat16* wbf, int member
 
 // Per-row E4M3 quantisation of W2..W4 (FP32, as the oracle mirrors it): s = max |w| / 448
 // (1 for a zero row), code = E4M3(w / s), nearest-even, saturating. grid (256, 3, members) x 256.
-__global__ void quantize_fp8(const float* __restrict__ master, uint8_t* w8, float* wscale)
+__global__ void quantize_fp8(const float* __restrict__ master, uint8_t* w8, float* wscale, float* wscale_half)
 {
     const int row = blockIdx.x, l = blockIdx.y + 1, mem = blockIdx.z;
     const float w = master[mem * P + OFF_W(l) + (long long)row * WID + threadIdx.x];
@@ -233,7 +234,10 @@ __global__ void quantize_fp8(const float* __restrict__ master, uint8_t* w8, floa
     const float sc = amax > 0.0f ? __fdiv_rn(amax, 448.0f) : 1.0f;
     const long long r = ((long long)mem * 3 + (l - 1)) * WID + row;
     w8[r * WID + threadIdx.x] = __nv_cvt_float_to_fp8(__fdiv_rn(w, sc), __NV_SATFINITE, __NV_E4M3);
-    if (threadIdx.x == 0) wscale[r] = sc;
+    if (threadIdx.x == 0) {
+        wscale[r] = sc;
+        wscale_half[r] = 0.5f * sc;
+    }
 }
 
 // Batch gather: xin[r] = feats[order[r]], lbl[r] = labels[order[r]] (rows past n are zero).
@@ -359,7 +363,7 @@ int make_map_nd(CUtensorMap* map, CUtensorMapDataType dt, int rank, const void* 
 int refresh_fp8(tune_surrogate* h, cudaStream_t s)
 {
     if (!h->fp8_stale) return TUNE_OK;
-    quantize_fp8<<<dim3(WID, NL - 1, h->members), WID, 0, s>>>(h->master, h->w8, h->wscale);
+    quantize_fp8<<<dim3(WID, NL - 1, h->members), WID, 0, s>>>(h->master, h->w8, h->wscale, h->wscale_half);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: quantize launch");
     h->fp8_stale = false;
     return TUNE_OK;
@@ -392,24 +396,28 @@ int fused_forward(tune_surrogate* h, const __nv_bfloat16* feats, int64_t n, floa
         int rc = refresh_fp8(h, s);
         if (rc) return rc;
     }
+    // The tensor maps address 8-byte elements: TMA moves the same bytes with the same
+    // 128-byte swizzle whatever the element type, in a quarter (BF16) or an eighth (E4M3)
+    // of the element count. Dimension 0 and the boxes are in 8-byte units.
     CUtensorMap tx, tw1, tw;
-    const cuuint64_t xd[2] = {IN, (cuuint64_t)n}, xs[1] = {IN * 2};
-    const cuuint32_t xb[2] = {64, tcm::kRows};
-    int rc = make_map_nd(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, feats, xd, xs, xb);
+    const auto u64 = CU_TENSOR_MAP_DATA_TYPE_UINT64;
+    const cuuint64_t xd[2] = {IN * 2 / 8, (cuuint64_t)n}, xs[1] = {IN * 2};
+    const cuuint32_t xb[2] = {16, tcm::kRows};
+    int rc = make_map_nd(&tx, u64, 2, feats, xd, xs, xb);
     if (rc) return rc;
-    const cuuint64_t d1[3] = {IN, WID, (cuuint64_t)h->members}, s1[2] = {IN * 2, PB * 2};
-    const cuuint32_t b1[3] = {64, WID, 1};
-    rc = make_map_nd(&tw1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, h->wbf, d1, s1, b1);
+    const cuuint64_t d1[3] = {IN * 2 / 8, WID, (cuuint64_t)h->members}, s1[2] = {IN * 2, PB * 2};
+    const cuuint32_t b1[3] = {16, WID, 1};
+    rc = make_map_nd(&tw1, u64, 3, h->wbf, d1, s1, b1);
     if (rc) return rc;
-    const cuuint64_t dw[4] = {WID, WID, NL - 1, (cuuint64_t)h->members};
+    const cuuint32_t bw[4] = {16, WID, 1, 1};
     if (fp8) {
+        const cuuint64_t dw[4] = {WID / 8, WID, NL - 1, (cuuint64_t)h->members};
         const cuuint64_t sw[3] = {WID, WID * WID, (NL - 1) * WID * WID};
-        const cuuint32_t bw[4] = {128, WID, 1, 1};
-        rc = make_map_nd(&tw, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, h->w8, dw, sw, bw);
+        rc = make_map_nd(&tw, u64, 4, h->w8, dw, sw, bw);
     } else {
+        const cuuint64_t dw[4] = {WID * 2 / 8, WID, NL - 1, (cuuint64_t)h->members};
         const cuuint64_t sw[3] = {WID * 2, WID * WID * 2, PB * 2};
-        const cuuint32_t bw[4] = {64, WID, 1, 1};
-        rc = make_map_nd(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, h->wbf + BOFF_W(1), dw, sw, bw);
+        rc = make_map_nd(&tw, u64, 4, h->wbf + BOFF_W(1), dw, sw, bw);
     }
     if (rc) return rc;
     tcm::Args g;
@@ -421,7 +429,7 @@ int fused_forward(tune_surrogate* h, const __nv_bfloat16* feats, int64_t n, floa
     for (int l = 0; l < NL; ++l) g.off_b[l] = OFF_B(l);
     g.off_w5 = OFF_W5;
     g.off_b5 = OFF_B5;
-    g.wscale = h->wscale;
+    g.wscale_half = h->wscale_half;
     g.pred = pred;
     g.status = h->status;
     const long long sms = tune::device_sm_count();
@@ -619,6 +627,7 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     add(256);
     add(M * (NL - 1) * WID * WID);
     add(M * (NL - 1) * WID * 4);
+    add(M * (NL - 1) * WID * 4);
     cudaError_t e = cudaMalloc(&h->block, bytes);
     if (e != cudaSuccess) {
         delete h;
@@ -644,6 +653,7 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     h->status = carve<int>(p, 64);
     h->w8 = carve<uint8_t>(p, M * (NL - 1) * WID * WID);
     h->wscale = carve<float>(p, M * (NL - 1) * WID);
+    h->wscale_half = carve<float>(p, M * (NL - 1) * WID);
     *out = h;
     return TUNE_OK;
 }

@@ -5,20 +5,29 @@
 // Work unit = (tile of 128 rows, member). A CTA runs two units at a time, one
 // per "chain": each chain owns an activation buffer in shared memory and a
 // 256-column FP32 accumulator in tensor memory. Layer l of a unit is
-//   MMA:      acc = act . W_l^T            (tcgen05.mma, operands in smem)
-//   epilogue: act = q(gelu(acc * s + b))   (tcgen05.ld, CUDA cores, st.shared)
+//   MMA:      acc = act . W_l^T              (tcgen05.mma, operands in smem)
+//   epilogue: act = q(2 gelu(acc * s + b))   (tcgen05.ld, CUDA cores, st.shared)
 // and the MMA issuer alternates the chains layer by layer, so one chain's
 // epilogue runs while the other chain's MMAs occupy the tensor cores.
 //
-// Roles (320 threads): warp 0 streams weights (and each unit's input rows)
-// with TMA through a ring of 32 KB stages; warp 1 issues the MMAs; warps 2-5
-// are chain 0's epilogue and warps 6-9 chain 1's (thread = accumulator row).
+// Roles (576 threads): warp 0 streams weights (and each unit's input rows)
+// with TMA through a ring of 32 KB stages (all 256 output rows of a 128-byte
+// K chunk; the tensor maps address 8-byte elements, the bytes and their
+// 128-byte swizzle being the same for BF16 and E4M3 data); warp 1 issues the MMAs; warps 2-17
+// run the epilogues of both chains in the MMA issue order (each layer's
+// epilogue gets all sixteen warps): thread = accumulator row, four warps per
+// TMEM lane quarter, one per 64-column quarter.
+//
+// The epilogue stores 2 gelu(z) = z (1 + tanh u), one operation fewer than
+// gelu itself, and the next layer (or the head) takes half its accumulator.
+// In BF16 this is exact: doubling commutes with rounding, so the results are
+// those of storing gelu(z).
 //
 // Precision: layer 1 (K = 128) is BF16 x BF16 in both variants. The BF16
-// variant keeps layers 2-4 in BF16; the FP8 variant stores the hidden
-// activations and W2..W4 as E4M3 codes (per-row weight scales applied in the
-// epilogue, unit activation scale) and runs layers 2-4 with kind::f8f6f4.
-// The head reads BF16(h4) and sums in FP32.
+// variant keeps layers 2-4 in BF16 (GELU in FP32); the FP8 variant stores
+// E4M3 codes of 2 h (activation scale 1/2, GELU on packed f16 pairs) and W2..W4
+// as E4M3 codes with per-row scales, and runs layers 2-4 with kind::f8f6f4.
+// The head takes the FP32 values 2 h4 and sums in FP32.
 //
 // Every wait is bounded; on timeout the kernel sets status bit 2, stops
 // issuing work, waits (bounded) for the copies and MMAs it issued, frees its
@@ -36,7 +45,8 @@
 namespace tcm {
 
 constexpr int kRows = 128, kIn = 128, kWid = 256, kLayers = 4;
-constexpr int kThreads = 320;
+constexpr int kEpiWarps = 16;  // shared by the two chains
+constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kChunkA = kRows * 128;  // one 128-byte-wide K chunk of an activation tile
 constexpr int kChunkW = kWid * 128;   // one 128-byte-wide K chunk of a weight matrix
 
@@ -58,7 +68,7 @@ struct Args {
     long long P;
     long long off_b[kLayers];
     long long off_w5, off_b5;
-    const float* wscale;    // FP8: [members][3][256] per-row scales of W2..W4
+    const float* wscale_half;  // FP8: [members][3][256] halves of the per-row scales of W2..W4
     float* pred;            // [members][n]
     int* status;
 };
@@ -136,10 +146,36 @@ __device__ __forceinline__ void st_shared_v4(uint8_t* p, uint32_t a, uint32_t b,
                  : "memory");
 }
 
+__device__ __forceinline__ void ld16(const float* p, float (&x)[16])
+{
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(p + i));
+        x[i] = q.x;
+        x[i + 1] = q.y;
+        x[i + 2] = q.z;
+        x[i + 3] = q.w;
+    }
+}
+
+// 16 consecutive accumulator columns of this thread's TMEM lane (row), then the wait.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // grid: min(SMs, units) persistent CTAs; CTA b runs units b, b + gridDim.x, ...;
 // its j-th unit goes to chain j % 2. Unit u = (tile u / members, member u % members).
 template <bool FP8>
-__global__ void __launch_bounds__(kThreads, 1) mlp_infer_kernel(const __grid_constant__ CUtensorMap tx,
+__global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtensorMap tx,
                                                                 const __grid_constant__ CUtensorMap tw1,
                                                                 const __grid_constant__ CUtensorMap tw,
                                                                 const __grid_constant__ Args g)
@@ -147,9 +183,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer_kernel(const __grid_con
     using C = Cfg<FP8>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t w_full[C::stages], w_empty[C::stages];
-    __shared__ uint64_t x_full[2], act_free[2], acc_full[2], act_ready[2], drain;
+    __shared__ uint64_t x_full[2], act_free[2], acc_full[2], act_ready[2], head_bar[2], drain;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
+    __shared__ float head_part[2][3][kRows];  // head sums of column quarters 1-3, per chain
 
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* ring = smem + 2 * C::act_bytes;
@@ -171,7 +208,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer_kernel(const __grid_con
             tc::mbar_init(&x_full[s], 1);
             tc::mbar_init(&act_free[s], 1);
             tc::mbar_init(&acc_full[s], 1);
-            tc::mbar_init(&act_ready[s], 128);
+            tc::mbar_init(&act_ready[s], 32 * kEpiWarps);
+            tc::mbar_init(&head_bar[s], 3 * kRows);
         }
         tc::mbar_init(&drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -203,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer_kernel(const __grid_con
                             uint8_t* act = smem + s * C::act_bytes;
                             tc::mbar_expect_tx(&x_full[s], 2 * kChunkA);
                             tma_load_2d(act, &tx, 0, tile * kRows, &x_full[s]);
-                            tma_load_2d(act + kChunkA, &tx, 64, tile * kRows, &x_full[s]);
+                            tma_load_2d(act + kChunkA, &tx, 16, tile * kRows, &x_full[s]);
                             x_last[s] = jj;
                         }
                         for (int c = 0; c < C::chunks(l); ++c, ++seq) {
@@ -213,11 +251,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer_kernel(const __grid_con
                                                            abort_v)))
                                 break;
                             tc::mbar_expect_tx(&w_full[st], kChunkW);
+                            // maps address 8-byte elements: 16 per 128-byte K chunk
                             if (l == 0)
-                                tc::tma_load_3d(ring + st * kChunkW, &tw1, c * 64, 0, mem, &w_full[st]);
+                                tc::tma_load_3d(ring + st * kChunkW, &tw1, c * 16, 0, mem, &w_full[st]);
                             else
-                                tma_load_4d(ring + st * kChunkW, &tw, c * (FP8 ? 128 : 64), 0, l - 1, mem,
-                                            &w_full[st]);
+                                tma_load_4d(ring + st * kChunkW, &tw, c * 16, 0, l - 1, mem, &w_full[st]);
                         }
                     }
                 }
@@ -278,84 +316,98 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer_kernel(const __grid_con
             tc::mbar_wait(&drain, 0, g.status);
         }
     } else {
-        // ---- epilogue: chain s, TMEM lane quarter q, one accumulator row per thread ----
-        const int s = (warp - 2) >> 2, q = warp & 3;
+        // ---- epilogue: all sixteen warps serve the chains in the MMA issue order; warp =
+        // (TMEM lane quarter q, column quarter cq), thread = accumulator row ----
+        const int e = warp - 2, q = warp & 3, cq = e >> 2;
         const int r = q * 32 + lane;  // row in the tile
-        uint8_t* act = smem + s * C::act_bytes;
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * kWid);
+        const int c_beg = cq * (kWid / 4), c_end = c_beg + kWid / 4;
         bool ok = true;
-        for (long long jj = s; jj < my_units && ok; jj += 2) {
-            const long long k = jj >> 1;
-            const long long u = blockIdx.x + jj * gridDim.x;
-            const int tile = (int)(u / g.members), mem = (int)(u % g.members);
-            const float* prm = g.master + mem * g.P;
-            float yh = 0.0f;
-            for (int l = 0; l < kLayers; ++l) {
-                if (!(ok = wait_bar(&acc_full[s], (uint32_t)((4 * k + l) & 1), g.status, abort_v))) break;
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const float* bias = prm + g.off_b[l];
-                const float* scl = (FP8 && l > 0) ? g.wscale + ((long long)mem * 3 + (l - 1)) * kWid : nullptr;
-                const float* w5 = prm + g.off_w5;
-                for (int n0 = 0; n0 < kWid; n0 += 32) {
-                    float v[32];
-                    tc::tmem_ld32(taddr + (uint32_t)n0, v);
+        for (long long j = 0; j < my_units && ok; j += 2) {
+            for (int l = 0; l < kLayers && ok; ++l) {
 #pragma unroll
-                    for (int i = 0; i < 32; i += 4) {
-                        const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + n0 + i));
-                        if (FP8 && l > 0) {
-                            const float4 s4 = __ldg(reinterpret_cast<const float4*>(scl + n0 + i));
-                            v[i] = fmaf(v[i], s4.x, b4.x);
-                            v[i + 1] = fmaf(v[i + 1], s4.y, b4.y);
-                            v[i + 2] = fmaf(v[i + 2], s4.z, b4.z);
-                            v[i + 3] = fmaf(v[i + 3], s4.w, b4.w);
+                for (int s = 0; s < 2; ++s) {
+                    const long long jj = j + s;
+                    if (jj >= my_units || !ok) break;
+                    const long long k = jj >> 1;
+                    const long long u = blockIdx.x + jj * gridDim.x;
+                    const int tile = (int)(u / g.members), mem = (int)(u % g.members);
+                    const float* prm = g.master + mem * g.P;
+                    uint8_t* act = smem + s * C::act_bytes;
+                    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * kWid);
+                    if (!(ok = wait_bar(&acc_full[s], (uint32_t)((4 * k + l) & 1), g.status, abort_v))) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const float* bias = prm + g.off_b[l];
+                    const float* scl = (FP8 && l > 0) ? g.wscale_half + ((long long)mem * 3 + (l - 1)) * kWid : nullptr;
+                    const float* w5 = prm + g.off_w5;
+                    // Layers 2-4 read 2 h (see the header), so their accumulator is halved here.
+                    const float acc_mul = l > 0 ? 0.5f : 1.0f;
+                    const bool f8 = FP8 && l > 0, head = l == kLayers - 1;
+                    float yh = 0.0f;
+                    for (int n0 = c_beg; n0 < c_end; n0 += 16) {
+                        // the block's parameters are requested before the accumulator wait so that
+                        // their latency overlaps it
+                        float bb[16], ss[16], ww[16];
+                        ld16(bias + n0, bb);
+                        if (f8) ld16(scl + n0, ss);
+                        if (head) ld16(w5 + n0, ww);
+                        float v[16];
+                        tmem_ld16(taddr + (uint32_t)n0, v);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] = fmaf(v[i], f8 ? ss[i] : acc_mul, bb[i]);
+                        if (FP8 && !head) {
+                            // E4M3 codes of 2 gelu(z) on packed halves: 16 columns = one 16-byte unit
+                            uint32_t w[4];
+#pragma unroll
+                            for (int qd = 0; qd < 4; ++qd) {
+                                const float* x = v + 4 * qd;
+                                const uint32_t c0 = mlp::e4m3x2_f16x2(mlp::gelu2_f16x2(mlp::f16x2_sat(x[0], x[1])));
+                                const uint32_t c1 = mlp::e4m3x2_f16x2(mlp::gelu2_f16x2(mlp::f16x2_sat(x[2], x[3])));
+                                w[qd] = c0 | (c1 << 16);
+                            }
+                            st_shared_v4(act + (n0 >> 7) * kChunkA + swz(r, (n0 & 127) >> 4), w[0], w[1], w[2], w[3]);
+                            continue;
+                        }
+                        // 2 gelu(z) = z (1 + tanh u) in FP32
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const float t = mlp::tanh_hw(mlp::gelu_u(v[i], v[i] * v[i]));
+                            v[i] = fmaf(v[i], t, v[i]);
+                        }
+                        if (head) {
+                            // head on 2 h4; the sum is halved with b5 added below
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) yh = fmaf(ww[i], v[i], yh);
                         } else {
-                            v[i] += b4.x;
-                            v[i + 1] += b4.y;
-                            v[i + 2] += b4.z;
-                            v[i + 3] += b4.w;
+                            // BF16(2 h): 16 columns = two 16-byte units of chunk n0/64
+                            uint8_t* base = act + (n0 >> 6) * kChunkA;
+                            const int j0 = (n0 & 63) >> 3;
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const float* x = v + 8 * h;
+                                st_shared_v4(base + swz(r, j0 + h), pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]),
+                                             pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
+                            }
                         }
                     }
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] = mlp::gelu(v[i]);
-                    if (l == kLayers - 1) {
-#pragma unroll
-                        for (int i = 0; i < 32; i += 4) {
-                            const float4 w4 = __ldg(reinterpret_cast<const float4*>(w5 + n0 + i));
-                            yh = fmaf(w4.x, __bfloat162float(__float2bfloat16_rn(v[i])), yh);
-                            yh = fmaf(w4.y, __bfloat162float(__float2bfloat16_rn(v[i + 1])), yh);
-                            yh = fmaf(w4.z, __bfloat162float(__float2bfloat16_rn(v[i + 2])), yh);
-                            yh = fmaf(w4.w, __bfloat162float(__float2bfloat16_rn(v[i + 3])), yh);
-                        }
-                    } else if (FP8) {
-                        // columns n0..n0+31 = bytes n0%128.. of chunk n0/128: two 16-byte units
-                        uint8_t* base = act + (n0 >> 7) * kChunkA;
-                        const int j0 = (n0 & 127) >> 4;
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const float* x = v + 16 * h;
-                            st_shared_v4(base + swz(r, j0 + h), pack_e4m3(x[0], x[1], x[2], x[3]),
-                                         pack_e4m3(x[4], x[5], x[6], x[7]), pack_e4m3(x[8], x[9], x[10], x[11]),
-                                         pack_e4m3(x[12], x[13], x[14], x[15]));
-                        }
-                    } else {
-                        // columns n0..n0+31 = bytes 2 (n0%64).. of chunk n0/64: four 16-byte units
-                        uint8_t* base = act + (n0 >> 6) * kChunkA;
-                        const int j0 = (n0 & 63) >> 3;
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            const float* x = v + 8 * h;
-                            st_shared_v4(base + swz(r, j0 + h), pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]),
-                                         pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
-                        }
+                    if (!head) {
+                        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    } else if (cq > 0) {
+                        // the other column quarters' head sums for quarter 0; a quarter can only
+                        // overwrite its slot at the chain's next unit, after quarter 0 has
+                        // arrived on that unit's act_ready
+                        head_part[s][cq - 1][r] = yh;
+                        mbar_arrive(&head_bar[s]);
+                    }
+                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                    mbar_arrive(&act_ready[s]);
+                    if (head && cq == 0) {
+                        if (!(ok = wait_bar(&head_bar[s], (uint32_t)(k & 1), g.status, abort_v))) break;
+                        const int row = tile * kRows + r;
+                        const float sum = ((yh + head_part[s][0][r]) + head_part[s][1][r]) + head_part[s][2][r];
+                        if (row < g.n) g.pred[(long long)mem * g.n + row] = fmaf(sum, 0.5f, prm[g.off_b5]);
                     }
                 }
-                if (l < kLayers - 1) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                mbar_arrive(&act_ready[s]);
             }
-            if (!ok) break;
-            const int row = tile * kRows + r;
-            if (row < g.n) g.pred[(long long)mem * g.n + row] = yh + prm[g.off_b5];
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
