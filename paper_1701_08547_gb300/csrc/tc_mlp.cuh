@@ -23,10 +23,10 @@
 // In BF16 this is exact: doubling commutes with rounding, so the results are
 // those of storing gelu(z).
 //
-// Precision: layer 1 (K = 128) is BF16 x BF16 in both variants. The BF16
-// variant keeps layers 2-4 in BF16 (GELU in FP32); the FP8 variant stores
-// E4M3 codes of 2 h (activation scale 1/2, GELU on packed f16 pairs) and W2..W4
-// as E4M3 codes with per-row scales, and runs layers 2-4 with kind::f8f6f4.
+// Precision: layer 1 (K = 128) is BF16 x BF16 in both variants; GELU is
+// evaluated in FP32. The BF16 variant keeps layers 2-4 in BF16; the FP8
+// variant stores E4M3 codes of 2 h (activation scale 1/2) and W2..W4 as E4M3
+// codes with per-row scales, and runs layers 2-4 with kind::f8f6f4.
 // The head takes the FP32 values 2 h4 and sums in FP32.
 //
 // Every wait is bounded; on timeout the kernel sets status bit 2, stops
@@ -354,24 +354,19 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                         tmem_ld16(taddr + (uint32_t)n0, v);
 #pragma unroll
                         for (int i = 0; i < 16; ++i) v[i] = fmaf(v[i], f8 ? ss[i] : acc_mul, bb[i]);
-                        if (FP8 && !head) {
-                            // E4M3 codes of 2 gelu(z) on packed halves: 16 columns = one 16-byte unit
-                            uint32_t w[4];
-#pragma unroll
-                            for (int qd = 0; qd < 4; ++qd) {
-                                const float* x = v + 4 * qd;
-                                const uint32_t c0 = mlp::e4m3x2_f16x2(mlp::gelu2_f16x2(mlp::f16x2_sat(x[0], x[1])));
-                                const uint32_t c1 = mlp::e4m3x2_f16x2(mlp::gelu2_f16x2(mlp::f16x2_sat(x[2], x[3])));
-                                w[qd] = c0 | (c1 << 16);
-                            }
-                            st_shared_v4(act + (n0 >> 7) * kChunkA + swz(r, (n0 & 127) >> 4), w[0], w[1], w[2], w[3]);
-                            continue;
-                        }
-                        // 2 gelu(z) = z (1 + tanh u) in FP32
+                        // 2 gelu(z) = z (1 + tanh u) in FP32: one multi-function-unit tanh per element
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             const float t = mlp::tanh_hw(mlp::gelu_u(v[i], v[i] * v[i]));
                             v[i] = fmaf(v[i], t, v[i]);
+                        }
+                        if (FP8 && !head) {
+                            // E4M3 codes of 2 h: 16 columns = one 16-byte unit
+                            uint32_t w[4];
+#pragma unroll
+                            for (int qd = 0; qd < 4; ++qd) w[qd] = pack_e4m3(v[4 * qd], v[4 * qd + 1], v[4 * qd + 2], v[4 * qd + 3]);
+                            st_shared_v4(act + (n0 >> 7) * kChunkA + swz(r, (n0 & 127) >> 4), w[0], w[1], w[2], w[3]);
+                            continue;
                         }
                         if (head) {
                             // head on 2 h4; the sum is halved with b5 added below

@@ -4,9 +4,8 @@ call, BF16 or with layers 2-4 on E4M3 codes) with the FP64 oracle.
 Tolerances. BF16: as for the layer-by-layer forward (one BF16 step, 2^-8, per
 stored activation, through four layers): |dy| <= 2e-2 (1 + |y|). FP8: the
 E4M3 codes of the weights are integers decided in FP32 on both sides and must
-match exactly; the activation codes follow values that the GPU computes on
-packed f16 pairs with the hardware tanh (errors of a few 2^-11) and the
-oracle in FP64, so a code can land one E4M3 step (2^-3 relative) away.
+match exactly; the activation codes follow values that the GPU computes in
+FP32 with the hardware tanh (about 2^-11 relative) and the oracle in FP64, so a code can land one E4M3 step (2^-3 relative) away.
 Perturbing the oracle's pre-quantisation activations by up to 2^-8 moves its
 outputs by at most 0.034 on these models (0.003 median); the test allows
 |dy| <= 5e-2 (1 + |y|) and a median of 1e-2.
