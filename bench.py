@@ -375,6 +375,7 @@ def surrogate_section(args, dev, a, ax, peaks):
     held_out = gen.descriptors(args.sur_eval, 40, "dense")
     ev = SD.evaluate(sur, a, ax, held_out, dev, k=5, thresh=0.1)
     ev_nofb = SD.evaluate(sur, a, ax, held_out, dev, k=5, thresh=1e30)
+    pruning = SD.evaluate_pruning(a, ax, held_out, dev)
     peak = peaks.get("bf16_tflops", 1900.0)
     return {
         "members": members,
@@ -388,6 +389,7 @@ def surrogate_section(args, dev, a, ax, peaks):
                   "fallback_rate": float(fb.float().mean().item())},
         "top5_vs_analytic": {"overlap": agree_overlap, "analytic_best_in_surrogate_top5": agree_hit},
         "top5_vs_measured_best": {"thresh_0.1": ev, "no_fallback": ev_nofb},
+        "static_pruning_vs_measured_best": pruning,
     }
 
 

@@ -323,6 +323,19 @@ int tune_emit_measure(const tune_axes* axes, const tune_kernel_desc* descs, int6
                       tune_stream_t stream);
 
 /*
+ * tune_eval_archs — tune_eval of the same descriptors against n_arch
+ * architecture rows (1..8) in one launch (a sweep over GPU generations:
+ * Eqs. 1-6 with each row's limits and throughputs). archs: host array
+ * [n_arch]. Outputs topk_idx / topk_cost [n_arch][n_kernels][k]; row i's
+ * results equal tune_eval(&archs[i], ...) bit for bit. flags: TUNE_SCHED_WARP
+ * with its chunk and CTA fields only. Workspace: the 256-byte header (status
+ * word and one queue counter per row).
+ */
+int tune_eval_archs(const tune_arch* archs, int32_t n_arch, const tune_axes* axes, const tune_kernel_desc* descs,
+                    int64_t n_kernels, int32_t k, uint32_t flags, int32_t* topk_idx, float* topk_cost,
+                    void* workspace, size_t ws_bytes, tune_stream_t stream);
+
+/*
  * tune_suggest — static search-space pruning (Section III-C "Static Search
  * Analysis", Section IV-C Table "Suggested parameters to achieve theoretical
  * occupancy"). Per kernel, at its registers r0 and shared memory s0 and the

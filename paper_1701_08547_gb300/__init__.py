@@ -12,7 +12,7 @@ from . import native
 from .native import (TUNE_EMIT_POINTS, TUNE_SCHED_CHUNK, TUNE_SCHED_CTAS,  # noqa: F401
                      TUNE_SCHED_THREAD, TUNE_SCHED_WARP, TuneError)
 
-__all__ = ["tune_eval", "tune_topk", "tune_autotune", "tune_features", "tune_suggest", "tune_workspace_bytes", "tune_check",
+__all__ = ["tune_eval", "tune_eval_archs", "tune_topk", "tune_autotune", "tune_features", "tune_suggest", "tune_workspace_bytes", "tune_check",
            "descs_to_device", "TUNE_EMIT_POINTS", "TUNE_SCHED_WARP", "TUNE_SCHED_THREAD",
            "TUNE_SCHED_CHUNK", "TUNE_SCHED_CTAS", "TuneError"]
 
@@ -75,6 +75,27 @@ def tune_eval(arch, axes, descs, k, flags=0, topk_idx=None, topk_cost=None, pt_b
     rc = L.tune_eval(C.byref(a), C.byref(x), _ptr(descs), n, int(k), int(flags), _ptr(topk_idx),
                      _ptr(topk_cost), _ptr(pt_blocks), _ptr(pt_warps), _ptr(pt_cost),
                      _ptr(pt_offsets), _ptr(workspace_buf), workspace_buf.numel(), _stream(stream))
+    native.check(rc)
+    return topk_idx, topk_cost
+
+
+def tune_eval_archs(archs, axes, descs, k, flags=0, workspace_buf=None, stream=None):
+    """tune_eval against several architecture rows in one launch.
+    Returns (topk_idx int32 [n_arch, n, k], topk_cost float32 [n_arch, n, k])."""
+    torch = _torch()
+    L = native.load()
+    assert descs.is_cuda and descs.is_contiguous() and descs.numel() * descs.element_size() % 64 == 0
+    n = descs.numel() * descs.element_size() // 64
+    dev = descs.device
+    na = len(archs)
+    topk_idx = torch.empty((na, n, k), dtype=torch.int32, device=dev)
+    topk_cost = torch.empty((na, n, k), dtype=torch.float32, device=dev)
+    if workspace_buf is None:
+        workspace_buf = workspace(native.TUNE_CALL_EVAL, 0, k, dev)
+    rows = (native.TuneArch * na)(*[native.make_arch(a) for a in archs])
+    x = native.make_axes(axes)
+    rc = L.tune_eval_archs(rows, na, C.byref(x), _ptr(descs), n, int(k), int(flags), _ptr(topk_idx),
+                           _ptr(topk_cost), _ptr(workspace_buf), workspace_buf.numel(), _stream(stream))
     native.check(rc)
     return topk_idx, topk_cost
 

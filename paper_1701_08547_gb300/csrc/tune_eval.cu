@@ -38,8 +38,11 @@ constexpr unsigned kFull = 0xffffffffu;
 
 
 
+constexpr int kMaxArch = 8;  // architecture rows of one launch (blockIdx.y)
+
 struct EvalParams {
-    tune_arch a;
+    tune_arch a[kMaxArch];
+    int n_arch;
     tune_axes x;
     int64_t n_kernels;
     int k;
@@ -73,9 +76,8 @@ struct WarpTables {
     int upos[8];
 };
 
-__device__ void build_cta_tables(const EvalParams& p, CtaTables& ct)
+__device__ void build_cta_tables(const EvalParams& p, const tune_arch& a, CtaTables& ct)
 {
-    const tune_arch& a = p.a;
     const tune_axes& x = p.x;
     for (int i = threadIdx.x; i < kMaxB * 16; i += blockDim.x) {
         int b = i >> 4, g = i & 15;
@@ -185,10 +187,15 @@ __global__ void __maxnreg__(64)
 {
     __shared__ CtaTables ct;
     __shared__ WarpTables wts[kWarps];
-    build_cta_tables(p, ct);
+    // blockIdx.y selects the architecture row; its results and work queue follow those of
+    // the rows before it
+    const tune_arch& a = p.a[blockIdx.y];
+    topk_idx += (int64_t)blockIdx.y * p.n_kernels * p.k;
+    topk_cost += (int64_t)blockIdx.y * p.n_kernels * p.k;
+    queue += blockIdx.y;
+    build_cta_tables(p, a, ct);
     __syncthreads();
 
-    const tune_arch& a = p.a;
     const tune_axes& x = p.x;
     const int lane = threadIdx.x & 31;
     WarpTables& w = wts[threadIdx.x >> 5];
@@ -506,10 +513,10 @@ __global__ void __maxnreg__(KMAX > 8 ? 128 : 96)
 {
     __shared__ CtaTables ct;
     __shared__ float4 utab[8][kThreadsT];  // per unroll position: C_nm, C_m, R, warps | wbmax << 8
-    build_cta_tables(p, ct);
+    const tune_arch& a = p.a[0];
+    build_cta_tables(p, a, ct);
     __syncthreads();
 
-    const tune_arch& a = p.a;
     const tune_axes& x = p.x;
     const float kInf = __int_as_float(0x7f800000);
     const int k = p.k;
@@ -712,12 +719,14 @@ int launch(const EvalParams& p, const tune_kernel_desc* descs, int32_t* ti, floa
     const int sms = tune::device_sm_count();
     if (sms <= 0) return tune::fail(TUNE_ECUDA, "tune_eval: cannot query the SM count");
     const int64_t need = (p.n_kernels + kWarps - 1) / kWarps;
-    const int64_t cap = (int64_t)sms * (ctas_per_sm > 0 ? min(ctas_per_sm, per_sm) : per_sm);
+    // a persistent grid shared by the architecture rows (blockIdx.y)
+    int64_t cap = (int64_t)sms * (ctas_per_sm > 0 ? min(ctas_per_sm, per_sm) : per_sm) / p.n_arch;
+    if (cap < 1) cap = 1;
     const int grid = (int)(need < cap ? need : cap);
-    // The queue counter is the second 8-byte word of the zeroed workspace header.
+    // The queue counters (one per row) follow the status word in the zeroed workspace header.
     unsigned long long* queue = reinterpret_cast<unsigned long long*>(status) + 1;
-    kern<<<grid, kThreads, 0, s>>>(p, reinterpret_cast<const int4*>(descs), ti, tc, pb, pw, pc, po,
-                                   status, queue);
+    kern<<<dim3(grid, p.n_arch), kThreads, 0, s>>>(p, reinterpret_cast<const int4*>(descs), ti, tc, pb, pw, pc, po,
+                                                  status, queue);
     TUNE_CUDA_TRY(cudaGetLastError(), "tune_eval: kernel launch");
     return TUNE_OK;
 }
@@ -805,7 +814,8 @@ extern "C" int tune_eval(const tune_arch* arch, const tune_axes* axes, const tun
     if (n_kernels == 0) return TUNE_OK;
 
     EvalParams p;
-    p.a = *arch;
+    p.a[0] = *arch;
+    p.n_arch = 1;
     p.x = *axes;
     p.n_kernels = n_kernels;
     p.k = k;
@@ -894,7 +904,8 @@ extern "C" int tune_eval_noalloc(const tune_arch* arch, const tune_axes* axes,
     TUNE_CUDA_TRY(cudaMemsetAsync(scratch, 0, tune::kWorkspaceHeader, s), "tune_eval_noalloc: scratch reset");
     if (n_kernels > 0) {
         EvalParams p;
-        p.a = *arch;
+        p.a[0] = *arch;
+        p.n_arch = 1;
         p.x = *axes;
         p.n_kernels = n_kernels;
         p.k = k;
@@ -914,4 +925,45 @@ extern "C" int tune_eval_noalloc(const tune_arch* arch, const tune_axes* axes,
         return tune::fail(TUNE_EINVAL, "a descriptor was malformed (mask outside the axes, negative "
                                        "count, register or shared-memory field)");
     return TUNE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tune_eval_archs: the same ranking for every kernel against several
+// architecture rows in one launch (blockIdx.y = row).
+// ---------------------------------------------------------------------------
+extern "C" int tune_eval_archs(const tune_arch* archs, int32_t n_arch, const tune_axes* axes,
+                               const tune_kernel_desc* descs, int64_t n_kernels, int32_t k, uint32_t flags,
+                               int32_t* topk_idx, float* topk_cost, void* workspace, size_t ws_bytes,
+                               tune_stream_t stream)
+{
+    tune::clear_error();
+    if (!archs || n_arch < 1 || n_arch > kMaxArch)
+        return tune::fail(TUNE_EINVAL, "n_arch = %d outside [1, %d] or archs NULL", n_arch, kMaxArch);
+    for (int i = 0; i < n_arch; ++i) {
+        int rc = validate(&archs[i], axes, k);
+        if (rc) return rc;
+    }
+    if (n_kernels < 0) return tune::fail(TUNE_EINVAL, "n_kernels < 0");
+    if (!workspace || ws_bytes < tune::kWorkspaceHeader)
+        return tune::fail(TUNE_ENOMEM, "workspace smaller than %d bytes", tune::kWorkspaceHeader);
+    if (n_kernels > 0 && (!descs || !topk_idx || !topk_cost))
+        return tune::fail(TUNE_EINVAL, "descs, topk_idx and topk_cost must be non-NULL");
+    if ((reinterpret_cast<uintptr_t>(descs) & 15) != 0)
+        return tune::fail(TUNE_EINVAL, "descs must be 16-byte aligned");
+    if (flags & ~(TUNE_SCHED_WARP | 0xff00u))
+        return tune::fail(TUNE_EINVAL, "flags 0x%x: only TUNE_SCHED_WARP and its chunk/CTA fields", flags);
+    const int chunk_code = (int)((flags >> 8) & 0xfu);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int* status = static_cast<int*>(workspace);
+    TUNE_CUDA_TRY(cudaMemsetAsync(workspace, 0, tune::kWorkspaceHeader, s), "tune_eval_archs: status reset");
+    if (n_kernels == 0) return TUNE_OK;
+    EvalParams p;
+    for (int i = 0; i < n_arch; ++i) p.a[i] = archs[i];
+    p.n_arch = n_arch;
+    p.x = *axes;
+    p.n_kernels = n_kernels;
+    p.k = k;
+    p.chunk = chunk_code == 0 ? 0 : (1 << (chunk_code - 1));
+    return launch<false>(p, descs, topk_idx, topk_cost, nullptr, nullptr, nullptr, nullptr, status, s,
+                         (int)((flags >> 12) & 0xfu));
 }

@@ -68,6 +68,9 @@ def load():
     L.tune_eval.argtypes = [C.POINTER(TuneArch), C.POINTER(TuneAxes), vp, i64, i32, u32, vp, vp,
                             vp, vp, vp, vp, vp, sz, vp]
     L.tune_eval.restype = C.c_int
+    L.tune_eval_archs.argtypes = [C.POINTER(TuneArch), i32, C.POINTER(TuneAxes), vp, i64, i32, u32, vp, vp, vp, sz,
+                                  vp]
+    L.tune_eval_archs.restype = C.c_int
     L.tune_topk.argtypes = [vp, vp, i64, i32, vp, vp, vp, sz, vp]
     L.tune_topk.restype = C.c_int
     L.tune_workspace_bytes.argtypes = [C.c_int, i64, i32]

@@ -17,7 +17,7 @@ import ctypes as C
 import numpy as np
 
 from . import native
-from . import descs_to_device, tune_eval, tune_features
+from . import descs_to_device, tune_eval, tune_features, tune_suggest
 from .surrogate import Surrogate
 
 ITEMS = 65536
@@ -27,6 +27,8 @@ COUNT_SCALE = 1.0 / 1024.0
 T_MIN_POS, G_MIN_POS = 1, 6
 # Held-out spaces, fully timed: 5 thread counts x 4 grids x unroll {1, 4} x carveout {0, 100}
 EVAL_T, EVAL_G, EVAL_U, EVAL_C = [1, 3, 7, 15, 31], [7, 9, 11, 13], [0, 3], [0, 3]
+# Pruning spaces, fully timed: all 32 thread counts x grids {512, 2048} x unroll 1 x carveout 100
+PRUNE_T, PRUNE_G, PRUNE_U, PRUNE_C = list(range(32)), [9, 11], [0], [3]
 
 
 def _emit_lib():
@@ -156,3 +158,34 @@ def evaluate(sur, arch, axes, descs, dev, k=5, thresh=0.1):
     return {"kernels": int(ok.sum()), "k": k, "thresh": thresh, "hit_surrogate": hs, "hit_analytic": ha,
             "overlap_surrogate": os_, "overlap_analytic": oa, "first_pick_slowdown_surrogate": rs,
             "first_pick_slowdown_analytic": ra, "fallback_rate": float(fb[ok].mean())}
+
+
+def evaluate_pruning(arch, axes, descs, dev):
+    """Static pruning (tune_suggest) against measured times: every point of spaces with all 32
+    thread counts is timed; per kernel, is the measured-best thread count in T* (and in the
+    rule's half of T*), and how much slower is the best point left in the pruned space."""
+    from workloads import gen
+
+    d = descs.copy()
+    d["space_mask"] = np.uint64(gen.mask_bits(PRUNE_T, PRUNE_G, PRUNE_U, PRUNE_C))
+    size = int(gen.space_sizes(d[:1])[0])
+    n_g = len(PRUNE_G)
+    us, _ = measure(axes, d, np.repeat(np.arange(len(d)), size), np.tile(np.arange(size), len(d)).astype(np.int32))
+    t = np.where(np.isfinite(us), us, np.inf).reshape(len(d), len(PRUNE_T), n_g)  # canonical order: T, then G
+    sug = tune_suggest(arch, axes, descs_to_device(d, dev))
+    star = sug["t_star"].cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+    rule = sug["t_rule"].cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+    ok = np.isfinite(t.min(axis=(1, 2))) & (star != 0)
+    best_t = t.min(axis=2)                       # per kernel, per thread count
+    overall = best_t.min(axis=1)
+
+    def stats(mask):
+        sel = np.array([[(m >> p) & 1 for p in PRUNE_T] for m in mask], dtype=bool)
+        pruned = np.where(sel, best_t, np.inf).min(axis=1)
+        hit = (pruned == overall)[ok]
+        slow = (pruned / overall)[ok]
+        return {"hit": float(hit.mean()), "median_slowdown": float(np.median(slow)),
+                "p90_slowdown": float(np.quantile(slow, 0.9)), "kept_thread_counts": float(sel[ok].sum(1).mean())}
+
+    return {"kernels": int(ok.sum()), "thread_counts": len(PRUNE_T), "grids": [int(axes["g"][p]) for p in PRUNE_G],
+            "static_t_star": stats(star), "rule": stats(rule)}

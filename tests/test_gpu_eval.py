@@ -217,3 +217,22 @@ def test_full_size_uneven_sampled(dev, oracle):
         idx, cost = idx.cpu().numpy(), cost.cpu().numpy()
         assert np.array_equal(idx[pick], o["idx"]), fl
         assert np.array_equal(cost[pick].view(np.uint32), o["cost"].view(np.uint32)), fl
+
+
+@pytest.mark.parametrize("flags", [0, 0x10 | (4 << 8)])
+def test_all_arch_rows_in_one_launch(dev, oracle, flags):
+    """tune_eval_archs: every architecture row in one launch (static stride and work queue)
+    equals the oracle row by row, bit for bit."""
+    import paper_1701_08547_gb300 as T
+
+    names = list(archs.ARCHS)
+    rows = [archs.arch(n) for n in names]
+    ax = gen.axes()
+    d = gen.descriptors(700, 8, "uneven")
+    d["r0"] = np.minimum(d["r0"], 60)
+    idx, cost = T.tune_eval_archs(rows, ax, T.descs_to_device(d, dev), 6, flags=flags)
+    idx, cost = idx.cpu().numpy(), cost.cpu().numpy()
+    for i, a in enumerate(rows):
+        o = oracle.evaluate(a, ax, d, 6)
+        assert np.array_equal(idx[i], o["idx"]), (names[i], np.argwhere(idx[i] != o["idx"])[:5])
+        assert np.array_equal(cost[i].view(np.uint32), o["cost"].view(np.uint32)), names[i]

@@ -81,3 +81,22 @@ def test_gpu_suggest_matches_oracle(oracle, name):
         assert g["occ_star"][i] == np.float32(o["occ_star"]), i
         assert g["r_headroom"][i] == o["r_headroom"] and g["s_star"][i] == o["s_star"], i
         assert int(g["t_rule"][i]) & 0xffffffff == o["t_rule"], i
+
+
+@pytest.mark.gpu
+def test_gpu_pruning_against_measured_times():
+    """Pruned spaces against timed variants on this GPU: the report is complete and
+    self-consistent (the rule keeps a subset of T*, so it cannot do better)."""
+    import torch
+
+    from paper_1701_08547_gb300 import build
+    from paper_1701_08547_gb300 import surrogate_data as SD
+
+    build.build()
+    a, ax = archs.arch("sm_103"), gen.axes()
+    r = SD.evaluate_pruning(a, ax, gen.descriptors(40, 41, "dense"), torch.device("cuda:0"))
+    assert r["kernels"] >= 30
+    st, ru = r["static_t_star"], r["rule"]
+    assert st["kept_thread_counts"] == 5.0 and ru["kept_thread_counts"] == 2.0
+    assert 1.0 <= st["median_slowdown"] <= ru["median_slowdown"]
+    assert ru["hit"] <= st["hit"] <= 1.0
