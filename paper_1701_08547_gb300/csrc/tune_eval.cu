@@ -10,15 +10,19 @@
 //  * per kernel, lane-parallel: the per-unroll cost sums C_nm(U), C_m(U)
 //    (compensated FP32 sums), register-limited warps, per-carveout G_S, and
 //    the (T, U) block limit min(G_W, G_R);
-//  * hot loop: a lane walks (T, U, C) triples; occupancy B*, W* come from
-//    two table lookups and a min (grid size does not enter Eqs. 1-5), then
-//    all grid sizes G of that triple cost one FP32 multiply each:
-//    cost(T,G,U,C) = X(T,U,C) * ipar(B*, G);
-//  * each lane keeps a sorted register list of its k best (cost, index);
-//    lanes visit points in increasing canonical index, so a strict "<"
-//    keeps lower indices first among equal costs;
-//  * a k-round warp merge (two redux.sync minima per round) emits the
-//    kernel's top-k.
+//  * pre-pass: a lane walks (T, U, C) triples; occupancy B*, W* come from
+//    two table lookups and a min (grid size does not enter Eqs. 1-5); every
+//    grid size G of a triple costs X(T,U,C) * ipar(B*, G), and since a product
+//    by X > 0 is monotone under round-to-nearest the triple's cheapest point
+//    is exactly X * min_G ipar(B*, G): one FP32 multiply per triple. The k-th
+//    smallest triple minimum bounds the kernel's k-th best cost (tau0); each
+//    triple's minimum is kept as a 16-bit truncated key in shared memory;
+//  * main pass: lanes scan the keys; only triples whose key can still beat
+//    the bound are re-evaluated, and the warp merges their grid sizes in
+//    increasing (cost, index) order into a warp-wide exact top-k list (lane j
+//    holds the j-th best); ties go to the lower canonical index.
+//  * with TUNE_EMIT_POINTS the main pass instead computes and writes every
+//    point's B*, W* and cost.
 #include <math.h>
 #include <stdint.h>
 
@@ -74,6 +78,7 @@ struct WarpTables {
     int tpos[32];            // t position by t rank
     int gpos[16];            // g position by g rank
     int upos[8];
+    unsigned short key[32 * 32];  // upper 16 bits of each triple's minimum cost, by triple rank
 };
 
 __device__ void build_cta_tables(const EvalParams& p, const tune_arch& a, CtaTables& ct)
@@ -306,20 +311,27 @@ __global__ void __maxnreg__(64)
             X = __fmul_rn(__fmaf_rn(ucv.y, ct.hide[W], ucv.x), ct.lane[tp]);
         };
 
-        // ---- pre-pass: each triple's cheapest grid size costs X * min_G ipar(B*, G).
-        // Each lane keeps its four smallest; the k-th smallest over the warp is a
-        // valid starting bound tau0 (k distinct triples each own a point <= tau0).
+        // ---- pre-pass: each triple's cheapest grid size costs X * min_G ipar(B*, G)
+        // (exactly: a product by X > 0 is monotone under round-to-nearest, so the
+        // minimum over G of fl(X * ipar) is fl(X * min_G ipar)). Each lane keeps its
+        // four smallest; the k-th smallest over the warp is a valid starting bound
+        // tau0 (k distinct triples each own a point <= tau0). Without EMIT the
+        // triple minima are also stored, truncated to their upper 16 bits, so that
+        // the main pass scans keys instead of re-evaluating every triple.
         float tau0 = kInf;
         if (!EMIT) {
             float m0 = kInf, m1 = kInf, m2 = kInf, m3 = kInf;
             int t_r = t0, uc_r = uc0;
             for (int it = 0; it < n_iter; ++it) {
+                unsigned key = 0xffffu;  // no point: never a candidate
                 if (t_r < nT) {
                     int B, W;
                     float X;
                     triple(t_r, uc_r, B, W, X);
                     if (B > 0) {
-                        float v = __fmul_rn(X, iparmin[B - 1]);
+                        // NaN (from infinite counts) is ranked as +inf
+                        float v = fminf(__fmul_rn(X, iparmin[B - 1]), kInf);
+                        key = __float_as_uint(v) >> 16;
                         float lo;
                         lo = fminf(m0, v); v = fmaxf(m0, v); m0 = lo;
                         lo = fminf(m1, v); v = fmaxf(m1, v); m1 = lo;
@@ -333,6 +345,7 @@ __global__ void __maxnreg__(64)
                         ++t_r;
                     }
                 }
+                w.key[(it << 5) + lane] = (unsigned short)key;
             }
             for (int r = 0; r < k; ++r) {
                 const unsigned mb = __reduce_min_sync(kFull, __float_as_uint(m0));
@@ -349,77 +362,17 @@ __global__ void __maxnreg__(64)
         }
 
         // ---- main pass. The warp keeps one exact top-k list (lane j = j-th best)
-        // and its k-th key tau. Every point's cost is computed and folded into its
-        // triple's minimum; only when some lane's minimum can still enter the list
-        // does the warp merge the lanes' candidates in increasing (cost, index).
+        // and its k-th key tau. Only when some lane's triple can still enter the
+        // list does the warp merge the lanes' candidates in increasing (cost, index).
         float lc = kInf;  // this lane's list entry (lanes < k)
         int li = -1;
         float tau_c = kInf;
         int tau_i = -1;
-        const int64_t off = EMIT ? pt_off[kid] : 0;
-        int t_r = t0, uc_r = uc0;
-        for (int it = 0; it < n_iter; ++it) {
-            bool any = false;
-            float X = 0.0f;
-            int B = 0, base = 0;
-            if (t_r < nT) {
-                int W;
-                triple(t_r, uc_r, B, W, X);
-                base = t_r * g_stride + uc_r;
-                if (B > 0) {
-                    const float4* row = reinterpret_cast<const float4*>(ipar_rows + (B - 1) * 16);
-                    float c[16];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (q * 4 < nG) {
-                            const float4 f = row[q];
-                            c[4 * q + 0] = __fmul_rn(X, f.x);
-                            c[4 * q + 1] = __fmul_rn(X, f.y);
-                            c[4 * q + 2] = __fmul_rn(X, f.z);
-                            c[4 * q + 3] = __fmul_rn(X, f.w);
-                        } else {
-                            c[4 * q + 0] = c[4 * q + 1] = c[4 * q + 2] = c[4 * q + 3] = kInf;
-                        }
-                    }
-                    // min over the triple's costs (padding entries are +inf or NaN; fminf
-                    // drops NaN)
-                    float m01 = fminf(fminf(c[0], c[1]), fminf(c[2], c[3]));
-                    float m23 = fminf(fminf(c[4], c[5]), fminf(c[6], c[7]));
-                    float m45 = fminf(fminf(c[8], c[9]), fminf(c[10], c[11]));
-                    float m67 = fminf(fminf(c[12], c[13]), fminf(c[14], c[15]));
-                    const float cmin = fminf(fminf(m01, m23), fminf(m45, m67));
-                    any = cmin <= fminf(tau_c, tau0);
-                    if (EMIT) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            if (j < nG) {
-                                const int64_t at = off + base + j * nUC;
-                                if (pt_b) pt_b[at] = B;
-                                if (pt_w) pt_w[at] = W;
-                                if (pt_c) pt_c[at] = c[j];
-                            }
-                        }
-                    }
-                } else if (EMIT) {
-                    for (int j = 0; j < nG; ++j) {
-                        const int64_t at = off + base + j * nUC;
-                        if (pt_b) pt_b[at] = 0;
-                        if (pt_w) pt_w[at] = 0;
-                        if (pt_c) pt_c[at] = kInf;
-                    }
-                }
-                t_r += dq;
-                uc_r += dr;
-                if (uc_r >= nUC) {
-                    uc_r -= nUC;
-                    ++t_r;
-                }
-            }
-            if (__ballot_sync(kFull, any) == 0u) continue;
 
-            // Merge: each candidate lane walks its triple's grid sizes in increasing
-            // cost (the order of X * ipar(B*, G) over G depends on B* only); the warp
-            // repeatedly inserts the smallest head until no head can enter the list.
+        // Merge: each candidate lane walks its triple's grid sizes in increasing
+        // cost (the order of X * ipar(B*, G) over G depends on B* only); the warp
+        // repeatedly inserts the smallest head until no head can enter the list.
+        auto merge = [&](bool any, int B, float X, int base) {
             int r = 0;
             float hc = kInf;
             int hi = 0x7fffffff;
@@ -443,6 +396,72 @@ __global__ void __maxnreg__(64)
                 if (mc >= 0x7f800000u || mcf > tau0 || !key_less(mcf, (int)mi, tau_c, tau_i)) break;
                 warp_list_insert(lc, li, tau_c, tau_i, mcf, (int)mi, k, lane);
                 if (hc == mcf && hi == (int)mi) advance();
+            }
+        };
+
+        if (!EMIT) {
+            // Candidates: triples whose truncated minimum key does not exceed the
+            // truncated bound min(tau, tau0) (a superset of the exact test; the
+            // merge applies the exact one).
+            unsigned bkey = __float_as_uint(tau0) >> 16;
+            for (int it = 0; it < n_iter; ++it) {
+                const bool any = w.key[(it << 5) + lane] <= bkey;
+                if (__ballot_sync(kFull, any) == 0u) continue;
+                int B = 0, base = 0;
+                float X = 0.0f;
+                if (any) {
+                    const int tr = (it << 5) + lane;
+                    const int t_r = tr / nUC;
+                    const int uc_r = tr - t_r * nUC;
+                    int W;
+                    triple(t_r, uc_r, B, W, X);
+                    base = t_r * g_stride + uc_r;
+                }
+                merge(any, B, X, base);
+                bkey = __float_as_uint(fminf(tau_c, tau0)) >> 16;
+            }
+        } else {
+            // Every point's cost is computed and written; each triple's minimum
+            // decides whether the warp merges.
+            const int64_t off = pt_off[kid];
+            int t_r = t0, uc_r = uc0;
+            for (int it = 0; it < n_iter; ++it) {
+                bool any = false;
+                float X = 0.0f;
+                int B = 0, base = 0;
+                if (t_r < nT) {
+                    int W;
+                    triple(t_r, uc_r, B, W, X);
+                    base = t_r * g_stride + uc_r;
+                    if (B > 0) {
+                        const float* row = ipar_rows + (B - 1) * 16;
+                        any = __fmul_rn(X, iparmin[B - 1]) <= tau_c;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (j < nG) {
+                                const int64_t at = off + base + j * nUC;
+                                if (pt_b) pt_b[at] = B;
+                                if (pt_w) pt_w[at] = W;
+                                if (pt_c) pt_c[at] = __fmul_rn(X, row[j]);
+                            }
+                        }
+                    } else {
+                        for (int j = 0; j < nG; ++j) {
+                            const int64_t at = off + base + j * nUC;
+                            if (pt_b) pt_b[at] = 0;
+                            if (pt_w) pt_w[at] = 0;
+                            if (pt_c) pt_c[at] = kInf;
+                        }
+                    }
+                    t_r += dq;
+                    uc_r += dr;
+                    if (uc_r >= nUC) {
+                        uc_r -= nUC;
+                        ++t_r;
+                    }
+                }
+                if (__ballot_sync(kFull, any) == 0u) continue;
+                merge(any, B, X, base);
             }
         }
 
@@ -629,21 +648,8 @@ __global__ void __maxnreg__(KMAX > 8 ? 128 : 96)
         int thr_i = -1;
         for_triples([&](int B, float X, int base) {
             if (g_dense) {
-                const float4* row = reinterpret_cast<const float4*>(ct.ipar[B - 1]);
-                float c[16];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 f = row[q];
-                    c[4 * q + 0] = __fmul_rn(X, f.x);
-                    c[4 * q + 1] = __fmul_rn(X, f.y);
-                    c[4 * q + 2] = __fmul_rn(X, f.z);
-                    c[4 * q + 3] = __fmul_rn(X, f.w);
-                }
-                const float m01 = fminf(fminf(c[0], c[1]), fminf(c[2], c[3]));
-                const float m23 = fminf(fminf(c[4], c[5]), fminf(c[6], c[7]));
-                const float m45 = fminf(fminf(c[8], c[9]), fminf(c[10], c[11]));
-                const float m67 = fminf(fminf(c[12], c[13]), fminf(c[14], c[15]));
-                const float cmin = fminf(fminf(m01, m23), fminf(m45, m67));
+                // the triple's cheapest point (a product by X > 0 keeps the order of ipar)
+                const float cmin = __fmul_rn(X, ct.iparmin[B - 1]);
                 if (cmin <= fminf(thr_c, tau0)) {
                     // grid sizes in increasing cost: the order of ipar(B*, G) over G
 #pragma unroll 1
