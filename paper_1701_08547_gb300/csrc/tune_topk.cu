@@ -1,10 +1,11 @@
 // tune_topk: segmented top-k over an external FP32 score array (HBM-bound).
 //
 // One warp per segment, CTAs of 8 warps striding over segments. Lanes read the
-// segment with coalesced loads, eight independent loads in flight per lane.
+// segment's 16-byte-aligned body with coalesced float4 loads, the next batch in
+// flight while the current one is filtered.
 // The warp keeps one exact top-k list (lane j = j-th best, as an
 // order-preserving unsigned image of the score plus its index) and its k-th
-// key; only when a block of 256 scores holds values at or below that key does
+// key; only when a batch of 512 scores holds values at or below that key does
 // the warp merge them, in increasing (value, index) order, into the list.
 #include <stdint.h>
 
@@ -54,57 +55,124 @@ __device__ __forceinline__ void list_insert(unsigned& lk, int& li, unsigned& tau
     tau_i = __shfl_sync(kFull, li, k - 1);
 }
 
-constexpr int kLoads = 8;  // independent loads in flight per lane
+constexpr int kVec = 4;                 // 16-byte loads per lane per batch
+constexpr int kBatchF4 = 32 * kVec;     // float4 words per warp batch (2 KB)
+constexpr unsigned kNaNBits = 0x7fc00000u;
 
+// Filter bound: a score can enter the list only if it is <= tau (ties are decided
+// by index in the merge). While the list is not full, tau is +inf and every finite
+// score qualifies; the bound is then the largest finite float, which also keeps
+// +inf and NaN out (the comparison is false for NaN).
+__device__ __forceinline__ float filter_bound(unsigned tau_k)
+{
+    const float t = key_value(tau_k);
+    return t < __int_as_float(0x7f800000) ? t : __int_as_float(0x7f7fffff);
+}
+
+// Merges the candidates of one batch (bit j of cm marks v[j]; index of v[j] is
+// idx0 + stride_of(j)) into the warp list in increasing (key, index) order, until
+// the smallest remaining candidate can no longer enter.
+template <int N, typename IndexOf>
+__device__ __forceinline__ void merge_batch(const float (&v)[N], unsigned cm, IndexOf index_of, unsigned& lk,
+                                            int& li, unsigned& tau_k, int& tau_i, int k, int lane)
+{
+    for (;;) {
+        unsigned hk = 0xffffffffu;
+        int hq = 0;
+#pragma unroll
+        for (int q = N - 1; q >= 0; --q) {  // equal keys: the lower q (lower index) wins
+            const unsigned kq = order_key(v[q]);
+            if (((cm >> q) & 1u) && kq <= hk) {
+                hk = kq;
+                hq = q;
+            }
+        }
+        const unsigned mk = __reduce_min_sync(kFull, hk);
+        if (mk == 0xffffffffu) break;
+        const int my_i = index_of(hq);
+        const unsigned mi = __reduce_min_sync(kFull, hk == mk ? (unsigned)my_i : 0xffffffffu);
+        if (!key_less(mk, (int)mi, tau_k, tau_i)) break;
+        list_insert(lk, li, tau_k, tau_i, mk, (int)mi, k, lane);
+        if (hk == mk && my_i == (int)mi) cm &= ~(1u << hq);
+    }
+}
+
+// One warp per segment. The segment's 16-byte-aligned body is read as float4
+// words, kVec per lane per batch, and the next batch's loads are issued before
+// the current batch is filtered, so each warp keeps up to 4 KB in flight; the
+// (at most 3 + 3) unaligned head and tail scores are read with scalar loads.
 __global__ void __launch_bounds__(kThreads)
     topk_segmented_kernel(const float* __restrict__ scores, const int64_t* __restrict__ off, int64_t n_seg, int k,
                           int32_t* __restrict__ out_i, float* __restrict__ out_s)
 {
     const int lane = threadIdx.x & 31;
     const float kInf = __int_as_float(0x7f800000);
+    const float kNaN = __int_as_float(kNaNBits);
     const unsigned kInfKey = order_key(kInf);
-    for (int64_t s = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); s < n_seg;
-         s += (int64_t)gridDim.x * kWarps) {
-        const int64_t b = off[s];
-        const int len = (int)(off[s + 1] - b);
+    const int64_t stride = (int64_t)gridDim.x * kWarps;
+    int64_t s = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    int64_t nb = s < n_seg ? off[s] : 0, ne = s < n_seg ? off[s + 1] : 0;
+    for (; s < n_seg; s += stride) {
+        const int64_t b = nb;
+        const int len = (int)(ne - b);
+        if (s + stride < n_seg) {  // the next segment's bounds, ahead of this segment's work
+            nb = off[s + stride];
+            ne = off[s + stride + 1];
+        }
         const float* seg = scores + b;
+        // head: scores before the first 16-byte boundary; body: n4 float4 words; tail: the rest
+        const int head = min((int)(((16u - ((unsigned)reinterpret_cast<uintptr_t>(seg) & 15u)) & 15u) >> 2), len);
+        const int n4 = (len - head) >> 2;
+        const int tail0 = head + 4 * n4;
+        const float4* body = reinterpret_cast<const float4*>(seg + head);
+
         unsigned lk = kInfKey;  // list entry of this lane (lanes < k)
         int li = -1;
-        unsigned tau_k = kInfKey;  // the list's k-th key: candidates must not exceed it
+        unsigned tau_k = kInfKey;  // the list's k-th key
         int tau_i = -1;
-        for (int base = 0; base < len; base += 32 * kLoads) {
-            float v[kLoads];
+
+        // head and tail together, one score per lane (lanes >= head take the tail)
+        {
+            const int j = lane < head ? lane : tail0 + (lane - head);
+            float v[1];
+            v[0] = (lane < head || j < len) ? __ldcs(seg + j) + 0.0f : kNaN;  // -0 -> +0; NaN pads
+            const unsigned cm = v[0] <= filter_bound(tau_k) ? 1u : 0u;
+            if (__ballot_sync(kFull, cm != 0u))
+                merge_batch<1>(v, cm, [&](int) { return j; }, lk, li, tau_k, tau_i, k, lane);
+        }
+
+        auto load = [&](float4 (&w)[kVec], int f0) {
 #pragma unroll
-            for (int q = 0; q < kLoads; ++q) {
-                const int j = base + lane + 32 * q;
-                v[q] = j < len ? __ldcs(seg + j) + 0.0f : __int_as_float(0x7fc00000);  // -0 -> +0; NaN pads
+            for (int q = 0; q < kVec; ++q) {
+                const int f = f0 + lane + 32 * q;
+                w[q] = f < n4 ? __ldcs(body + f) : make_float4(kNaN, kNaN, kNaN, kNaN);
             }
-            const float tau_v = key_value(tau_k);
+        };
+        float4 cur[kVec];
+        load(cur, 0);
+        for (int f0 = 0; f0 < n4; f0 += kBatchF4) {
+            float4 nxt[kVec];
+            load(nxt, f0 + kBatchF4);  // all-NaN (no loads) past the end
+            float v[4 * kVec];
+#pragma unroll
+            for (int q = 0; q < kVec; ++q) {
+                v[4 * q + 0] = cur[q].x + 0.0f;
+                v[4 * q + 1] = cur[q].y + 0.0f;
+                v[4 * q + 2] = cur[q].z + 0.0f;
+                v[4 * q + 3] = cur[q].w + 0.0f;
+            }
+            const float tb = filter_bound(tau_k);
             unsigned cm = 0;
 #pragma unroll
-            for (int q = 0; q < kLoads; ++q)
-                if (v[q] <= tau_v && v[q] < kInf) cm |= 1u << q;  // false for NaN and +inf
-            if (__ballot_sync(kFull, cm != 0u) == 0u) continue;
-            // Merge this block's candidates in increasing (value, index) order.
-            for (;;) {
-                unsigned hk = 0xffffffffu;
-                int hq = 0;
-#pragma unroll
-                for (int q = kLoads - 1; q >= 0; --q) {  // equal keys: the lower q (lower index) wins
-                    const unsigned kq = order_key(v[q]);
-                    if (((cm >> q) & 1u) && kq <= hk) {
-                        hk = kq;
-                        hq = q;
-                    }
-                }
-                const unsigned mk = __reduce_min_sync(kFull, hk);
-                if (mk == 0xffffffffu) break;
-                const int my_i = base + lane + 32 * hq;
-                const unsigned mi = __reduce_min_sync(kFull, hk == mk ? (unsigned)my_i : 0xffffffffu);
-                if (!key_less(mk, (int)mi, tau_k, tau_i)) break;
-                list_insert(lk, li, tau_k, tau_i, mk, (int)mi, k, lane);
-                if (hk == mk && my_i == (int)mi) cm &= ~(1u << hq);
+            for (int j = 0; j < 4 * kVec; ++j)
+                if (v[j] <= tb) cm |= 1u << j;
+            if (__ballot_sync(kFull, cm != 0u)) {
+                const int i0 = head + 4 * (f0 + lane);
+                merge_batch<4 * kVec>(v, cm, [&](int j) { return i0 + 128 * (j >> 2) + (j & 3); }, lk, li, tau_k,
+                                      tau_i, k, lane);
             }
+#pragma unroll
+            for (int q = 0; q < kVec; ++q) cur[q] = nxt[q];
         }
         if (lane < k) {
             out_i[s * k + lane] = li;
@@ -145,6 +213,8 @@ extern "C" int tune_topk(const float* scores, const int64_t* seg_offsets, int64_
         return tune::fail(TUNE_ENOMEM, "workspace too small");
     if (n_seg > 0 && (!scores || !seg_offsets || !topk_idx || !topk_score))
         return tune::fail(TUNE_EINVAL, "scores, seg_offsets and outputs must be non-NULL");
+    if ((reinterpret_cast<uintptr_t>(scores) & 3) != 0)
+        return tune::fail(TUNE_EINVAL, "scores must be 4-byte aligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     TUNE_CUDA_TRY(cudaMemsetAsync(workspace, 0, tune::kWorkspaceHeader, s), "tune_topk: status reset");
     if (n_seg == 0) return TUNE_OK;

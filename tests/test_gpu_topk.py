@@ -74,3 +74,27 @@ def test_large_segments(dev, oracle):
     off = np.zeros(len(lens) + 1, np.int64)
     off[1:] = np.cumsum(lens)
     check(dev, oracle, gen.scores(int(off[-1]), 9), off, 10)
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_unaligned_base(dev, oracle, shift):
+    """Scores that start 4, 8 or 12 bytes past a 16-byte boundary: every segment's
+    aligned body, head and tail move."""
+    import torch
+
+    import paper_1701_08547_gb300 as T
+
+    rng = np.random.default_rng(40 + shift)
+    lens = np.concatenate([[0, 1, 3, 4, 5, 7, 515, 4099], rng.integers(0, 9000, 60)])
+    off = np.zeros(len(lens) + 1, np.int64)
+    off[1:] = np.cumsum(lens)
+    n = int(off[-1])
+    s = gen.scores(n, 23 + shift)
+    buf = torch.empty(n + shift, dtype=torch.float32, device=dev)
+    buf[shift:] = torch.from_numpy(s).to(dev)
+    view = buf[shift:]
+    assert view.data_ptr() % 16 == 4 * shift
+    gi, gv = T.tune_topk(view, torch.from_numpy(off).to(dev), 7)
+    o = oracle.topk(s, off, 7)
+    assert np.array_equal(gi.cpu().numpy(), o["idx"])
+    assert np.array_equal(gv.cpu().numpy(), o["cost"])
