@@ -16,9 +16,9 @@
 //    by X > 0 is monotone under round-to-nearest the triple's cheapest point
 //    is exactly X * min_G ipar(B*, G): one FP32 multiply per triple. The k-th
 //    smallest triple minimum bounds the kernel's k-th best cost (tau0); each
-//    triple's minimum is kept as a 16-bit truncated key in shared memory;
-//  * main pass: lanes scan the keys; only triples whose key can still beat
-//    the bound are re-evaluated, and the warp merges their grid sizes in
+//    triple's minimum is kept in shared memory;
+//  * main pass: lanes scan the minima; only triples that can still beat the
+//    bound are re-evaluated, and the warp merges their grid sizes in
 //    increasing (cost, index) order into a warp-wide exact top-k list (lane j
 //    holds the j-th best); ties go to the lower canonical index.
 //  * with TUNE_EMIT_POINTS the main pass instead computes and writes every
@@ -63,22 +63,28 @@ struct CtaTables {
     unsigned char divt[kMaxW + 1][32];  // floor(w / W_B) by (w, t position)
     unsigned char perm[kMaxB][16];   // g positions of ipar row b in increasing (value, g) order
     float iparmin[kMaxB];            // min of ipar row b over all axis grid sizes
+    unsigned short rwarps[256];      // register-limited warps by R (Eq. 4, per-warp allocation)
+    unsigned short rwbmax[256];      // largest W_B whose block fits the per-block register limit, by R
+    int cap_lo[4];                   // first capacity index allowed by carveout position c
 };
 
 struct WarpTables {
-    float iparc[kMaxB][16];  // ipar rows compacted to the kernel's grid sizes
     float iparmin[kMaxB];    // min over the kernel's grid sizes of ipar(b, G)
-    float4 uc[32];           // by (u rank * n_C + c rank): C_nm, C_m, u rank, G_S
     unsigned char gwr[32][8];  // min(G_W, G_R) by (t rank, u rank)
     float cnm[8], cm[8];     // by u rank
     int warps_r[8];          // register-limited warps (clamped to kMaxW) by u rank
     int wb_max[8];           // largest W_B whose block fits the per-block register limit
     int regs[8];             // R by u rank
     int gs[4];               // G_S by c rank
-    int tpos[32];            // t position by t rank
+    float2 tinfo[32];        // (W_B as int bits, lane efficiency) by t rank
     int gpos[16];            // g position by g rank
-    int upos[8];
-    unsigned short key[32 * 32];  // upper 16 bits of each triple's minimum cost, by triple rank
+    union {
+        float key[32 * 32];  // ranking pass: each triple's minimum cost, by (row, lane)
+        struct {             // emitting pass:
+            float iparc[kMaxB][16];  // ipar rows compacted to the kernel's grid sizes
+            float4 uc[32];   // by (u rank * n_C + c rank): C_nm, C_m, u rank, G_S
+        };
+    };
 };
 
 __device__ void build_cta_tables(const EvalParams& p, const tune_arch& a, CtaTables& ct)
@@ -136,7 +142,34 @@ __device__ void build_cta_tables(const EvalParams& p, const tune_arch& a, CtaTab
     } else if (tid < 32 + kMaxW + 1 + 8) {
         int c = tid - 32 - kMaxW - 1;
         ct.rcp[c] = c < TUNE_NCLASS ? __fdiv_rn(1.0f, a.ipc[c]) : 0.0f;
+    } else if (tid < 32 + kMaxW + 1 + 8 + 4) {
+        // capacities are ascending: those at or above index cap_lo satisfy the carveout
+        const int c = tid - 32 - kMaxW - 1 - 8;
+        const long long need = c < x.n_c ? (long long)x.c[c] * a.smem_caps[a.n_smem_caps - 1] : 0;
+        int i = 0;
+        while (i < a.n_smem_caps && 100LL * a.smem_caps[i] < need) ++i;
+        ct.cap_lo[c] = i;
     }
+    for (int R = tid; R < 256; R += blockDim.x) {
+        int warps, wbmax;
+        reg_params(a, R, warps, wbmax);
+        ct.rwarps[R] = (unsigned short)warps;
+        ct.rwbmax[R] = (unsigned short)min(wbmax, 65535);
+    }
+}
+
+// G_S (Eq. 5) as smem_blocks(), starting the capacity search at the carveout's
+// first admissible capacity (carveout position cp).
+__device__ __forceinline__ int smem_blocks_from(const tune_arch& a, const CtaTables& ct, int s0, int cp)
+{
+    if (s0 > a.smem_block_max) return 0;
+    const int s_alloc = ceil_div(s0 + a.smem_reserved_block, a.smem_alloc_unit) * a.smem_alloc_unit;
+    if (s_alloc == 0) return a.max_blocks_sm;
+    for (int i = ct.cap_lo[cp]; i < a.n_smem_caps; ++i) {
+        const int ci = a.smem_caps[i];
+        if (ci >= s_alloc) return ci / s_alloc;
+    }
+    return 0;
 }
 
 // G_R (Eq. 4) for R registers and blocks of W_B warps (t position tp).
@@ -157,6 +190,14 @@ __device__ __forceinline__ int reg_blocks(const tune_arch& a, const CtaTables& c
 __device__ __forceinline__ bool key_less(float c, int i, float c2, int i2)
 {
     return c < c2 || (c == c2 && i < i2);
+}
+
+// floor(n / d) for 0 <= n < 8192 and 1 <= d <= 32, given rcp = 1/d rounded to
+// nearest: (n + 1/2) / d lies at least 1/64 away from an integer, far more than
+// the rounding error of the product, so truncation is exact.
+__device__ __forceinline__ int small_div(int n, float rcp)
+{
+    return __float2int_rz(__fmul_rn((float)n + 0.5f, rcp));
 }
 
 // Warp-wide top-k list: lane j < k holds the j-th best (cost, index), ascending.
@@ -206,270 +247,298 @@ __global__ void __maxnreg__(64)
     WarpTables& w = wts[threadIdx.x >> 5];
     const float kInf = __int_as_float(0x7f800000);
     const int k = p.k;
+    const int64_t n_k = p.n_kernels;
     const uint32_t g_ok = (1u << x.n_g) - 1u;
 
     // Work distribution: a static stride over descriptors, or (chunk > 0) a queue
-    // from which each warp takes `chunk` consecutive descriptors at a time.
+    // from which each warp takes `chunk` consecutive descriptors at a time. The next
+    // descriptor's words, and in queue mode the start of the chunk after the current
+    // one, are fetched while the current descriptor is evaluated.
     const int64_t stride = (int64_t)gridDim.x * kWarps;
-    int64_t kid = p.chunk == 0 ? (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5) - stride : 0;
-    int64_t q_end = 0;  // queue mode: the first ++kid (= 1) is not below q_end, so a grab follows
-    auto next_kernel = [&]() -> bool {
-        if (p.chunk == 0) {
-            kid += stride;
-            return kid < p.n_kernels;
-        }
-        if (++kid < q_end) return true;
-        unsigned long long b = 0;
-        if (lane == 0) b = atomicAdd(queue, (unsigned long long)p.chunk);
-        b = __shfl_sync(kFull, b, 0);
-        kid = (int64_t)b;
-        q_end = min(kid + p.chunk, p.n_kernels);
-        return kid < p.n_kernels;
+    unsigned long long grabbed = 0;  // lane 0: start of the next chunk, once grabbed
+    auto grab = [&]() {
+        if (lane == 0) grabbed = atomicAdd(queue, (unsigned long long)p.chunk);
     };
-    while (next_kernel()) {
-        // ---- descriptor: lanes 0..3 load the four 16-byte words, then broadcast.
-        const int4 v = __ldg(descs + kid * 4 + (lane & 3));
-        int4 vw[4];
+    int64_t kid, q_end = 0;
+    if (p.chunk == 0) {
+        kid = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    } else {
+        grab();
+        kid = (int64_t)__shfl_sync(kFull, grabbed, 0);
+        q_end = min(kid + p.chunk, n_k);
+        if (kid < n_k) grab();
+    }
+    // lanes 0..3 hold the four 16-byte words of the descriptor (lane & 3)
+    int4 v = kid < n_k ? __ldg(descs + kid * 4 + (lane & 3)) : make_int4(0, 0, 0, 0);
+    while (kid < n_k) {
+        int64_t nk;
+        if (p.chunk == 0) {
+            nk = kid + stride;
+        } else if (kid + 1 < q_end) {
+            nk = kid + 1;
+        } else {
+            nk = (int64_t)__shfl_sync(kFull, grabbed, 0);
+            q_end = min(nk + p.chunk, n_k);
+            if (nk < n_k) grab();
+        }
+        const int4 v_next = nk < n_k ? __ldg(descs + nk * 4 + (lane & 3)) : make_int4(0, 0, 0, 0);
+
+        do {  // evaluate descriptor kid (break = done)
+            int4 vw[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            vw[q] = make_int4(__shfl_sync(kFull, v.x, q), __shfl_sync(kFull, v.y, q),
-                              __shfl_sync(kFull, v.z, q), __shfl_sync(kFull, v.w, q));
-        Desc kd;
-        unpack(vw, kd);
-        const int r0 = kd.r0, s0 = kd.s0;
-        const uint32_t tm = kd.tm, gm = kd.gm, um = kd.um, cm = kd.cm;
-        const bool bad = desc_bad(kd, x);
-        const int nT = __popc(tm), nG = __popc(gm), nU = __popc(um), nC = __popc(cm);
-        if (bad || nT * nG * nU * nC == 0) {
-            if (bad && lane == 0) atomicOr(status, tune::kStatusInvalid);
-            if (lane < k) {
-                topk_idx[kid * k + lane] = -1;
-                topk_cost[kid * k + lane] = kInf;
-            }
-            continue;
-        }
-        const int nUC = nU * nC;
-
-        // ---- per-axis compaction: lane = axis position.
-        const uint32_t below = (1u << lane) - 1u;
-        if ((tm >> lane) & 1u) w.tpos[__popc(tm & below)] = lane;
-        if (lane < 16 && ((gm >> lane) & 1u)) w.gpos[__popc(gm & below)] = lane;
-        if (lane < 8 && ((um >> lane) & 1u)) {
-            const int ur = __popc(um & below);
-            const int U = x.u[lane];
-            const int R = r0 + 4 * (U - 1);
-            unit_costs(kd.n, kd.d, U, ct.rcp, a.work_scale, w.cnm[ur], w.cm[ur]);
-            w.regs[ur] = R;
-            w.upos[ur] = lane;
-            reg_params(a, R, w.warps_r[ur], w.wb_max[ur]);
-        }
-        if (lane < 4 && ((cm >> lane) & 1u)) w.gs[__popc(cm & below)] = smem_blocks(a, s0, x.c[lane]);
-        __syncwarp();
-        // ---- (T, U) block limit min(G_W, G_R); lane = t rank.
-        if (lane < nT) {
-            const int tp = w.tpos[lane];
-            const int wb = ct.wb[tp];
-            const int gw = ct.gw[tp];
-            for (int ur = 0; ur < nU; ++ur) {
-                const int gr = reg_blocks(a, ct, w.regs[ur], wb, tp, w.warps_r[ur], w.wb_max[ur]);
-                w.gwr[lane][ur] = (unsigned char)min(gw, gr);
-            }
-        }
-        // ---- (U, C) pair table; lane = pair rank.
-        if (lane < nUC) {
-            const int ur = lane / nC, cr = lane - (lane / nC) * nC;
-            w.uc[lane] = make_float4(w.cnm[ur], w.cm[ur], __int_as_float(ur), __int_as_float(w.gs[cr]));
-        }
-        // ---- waves/slots factor rows, compacted to this kernel's grid sizes.
-        const bool g_dense = gm == g_ok;
-        if (!g_dense && lane < kMaxB) {
-            float mn = kInf;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float v = j < nG ? ct.ipar[lane][w.gpos[j]] : kInf;
-                w.iparc[lane][j] = v;
-                mn = fminf(mn, v);
-            }
-            w.iparmin[lane] = mn;
-        }
-        __syncwarp();
-        const float* ipar_rows = g_dense ? &ct.ipar[0][0] : &w.iparc[0][0];
-        const float* iparmin = g_dense ? ct.iparmin : w.iparmin;
-
-        // ---- (T, U, C) triples of this lane: t rank advances by 32 / nUC per step.
-        const int t0 = lane / nUC, uc0 = lane - (lane / nUC) * nUC;
-        const int dq = 32 / nUC, dr = 32 - (32 / nUC) * nUC;
-        const int g_stride = nG * nUC;
-        const int n_iter = (nT * nUC + 31) >> 5;
-        // B* and the grid-independent cost factor X of one triple.
-        auto triple = [&](int t_r, int uc_r, int& B, int& W, float& X) {
-            const float4 ucv = w.uc[uc_r];
-            const int ur = __float_as_int(ucv.z);
-            const int tp = w.tpos[t_r];
-            B = min((int)w.gwr[t_r][ur], __float_as_int(ucv.w));
-            W = B * ct.wb[tp];
-            X = __fmul_rn(__fmaf_rn(ucv.y, ct.hide[W], ucv.x), ct.lane[tp]);
-        };
-
-        // ---- pre-pass: each triple's cheapest grid size costs X * min_G ipar(B*, G)
-        // (exactly: a product by X > 0 is monotone under round-to-nearest, so the
-        // minimum over G of fl(X * ipar) is fl(X * min_G ipar)). Each lane keeps its
-        // four smallest; the k-th smallest over the warp is a valid starting bound
-        // tau0 (k distinct triples each own a point <= tau0). Without EMIT the
-        // triple minima are also stored, truncated to their upper 16 bits, so that
-        // the main pass scans keys instead of re-evaluating every triple.
-        float tau0 = kInf;
-        if (!EMIT) {
-            float m0 = kInf, m1 = kInf, m2 = kInf, m3 = kInf;
-            int t_r = t0, uc_r = uc0;
-            for (int it = 0; it < n_iter; ++it) {
-                unsigned key = 0xffffu;  // no point: never a candidate
-                if (t_r < nT) {
-                    int B, W;
-                    float X;
-                    triple(t_r, uc_r, B, W, X);
-                    if (B > 0) {
-                        // NaN (from infinite counts) is ranked as +inf
-                        float v = fminf(__fmul_rn(X, iparmin[B - 1]), kInf);
-                        key = __float_as_uint(v) >> 16;
-                        float lo;
-                        lo = fminf(m0, v); v = fmaxf(m0, v); m0 = lo;
-                        lo = fminf(m1, v); v = fmaxf(m1, v); m1 = lo;
-                        lo = fminf(m2, v); v = fmaxf(m2, v); m2 = lo;
-                        m3 = fminf(m3, v);
-                    }
-                    t_r += dq;
-                    uc_r += dr;
-                    if (uc_r >= nUC) {
-                        uc_r -= nUC;
-                        ++t_r;
-                    }
+            for (int q = 0; q < 4; ++q)
+                vw[q] = make_int4(__shfl_sync(kFull, v.x, q), __shfl_sync(kFull, v.y, q),
+                                  __shfl_sync(kFull, v.z, q), __shfl_sync(kFull, v.w, q));
+            Desc kd;
+            unpack(vw, kd);
+            const int r0 = kd.r0, s0 = kd.s0;
+            const uint32_t tm = kd.tm, gm = kd.gm, um = kd.um, cm = kd.cm;
+            const bool bad = desc_bad(kd, x);
+            const int nT = __popc(tm), nG = __popc(gm), nU = __popc(um), nC = __popc(cm);
+            if (bad || nT * nG * nU * nC == 0) {
+                if (bad && lane == 0) atomicOr(status, tune::kStatusInvalid);
+                if (lane < k) {
+                    topk_idx[kid * k + lane] = -1;
+                    topk_cost[kid * k + lane] = kInf;
                 }
-                w.key[(it << 5) + lane] = (unsigned short)key;
+                break;
             }
-            for (int r = 0; r < k; ++r) {
-                const unsigned mb = __reduce_min_sync(kFull, __float_as_uint(m0));
-                tau0 = __uint_as_float(mb);
-                if (mb >= 0x7f800000u) break;
-                const unsigned who = __ballot_sync(kFull, __float_as_uint(m0) == mb);
-                if (lane == __ffs(who) - 1) {
-                    m0 = m1;
-                    m1 = m2;
-                    m2 = m3;
-                    m3 = kInf;
+            const int nUC = nU * nC;
+            const int g_stride = nG * nUC;
+
+            // ---- per-axis tables, lane = axis position: per unroll the cost sums and
+            // register limits, per carveout G_S.
+            const uint32_t below = (1u << lane) - 1u;
+            if (lane < 16 && ((gm >> lane) & 1u)) w.gpos[__popc(gm & below)] = lane;
+            if (lane < 8 && ((um >> lane) & 1u)) {
+                const int ur = __popc(um & below);
+                const int U = x.u[lane];
+                const int R = r0 + 4 * (U - 1);
+                unit_costs(kd.n, kd.d, U, ct.rcp, a.work_scale, w.cnm[ur], w.cm[ur]);
+                w.regs[ur] = R;
+                if (R >= 0 && R < 256) {
+                    w.warps_r[ur] = ct.rwarps[R];
+                    w.wb_max[ur] = ct.rwbmax[R];
+                } else {
+                    reg_params(a, R, w.warps_r[ur], w.wb_max[ur]);
                 }
             }
-        }
-
-        // ---- main pass. The warp keeps one exact top-k list (lane j = j-th best)
-        // and its k-th key tau. Only when some lane's triple can still enter the
-        // list does the warp merge the lanes' candidates in increasing (cost, index).
-        float lc = kInf;  // this lane's list entry (lanes < k)
-        int li = -1;
-        float tau_c = kInf;
-        int tau_i = -1;
-
-        // Merge: each candidate lane walks its triple's grid sizes in increasing
-        // cost (the order of X * ipar(B*, G) over G depends on B* only); the warp
-        // repeatedly inserts the smallest head until no head can enter the list.
-        auto merge = [&](bool any, int B, float X, int base) {
-            int r = 0;
-            float hc = kInf;
-            int hi = 0x7fffffff;
-            auto advance = [&]() {
-                hc = kInf;
-                hi = 0x7fffffff;
-                while (r < x.n_g) {
-                    const int g = ct.perm[B - 1][r++];
-                    if ((gm >> g) & 1u) {
-                        hc = __fmul_rn(X, ct.ipar[B - 1][g]);
-                        hi = base + __popc(gm & ((1u << g) - 1u)) * nUC;
-                        break;
+            if (lane < 4 && ((cm >> lane) & 1u)) w.gs[__popc(cm & below)] = smem_blocks_from(a, ct, s0, lane);
+            __syncwarp();
+            // ---- per thread count (lane = t position): W_B and lane efficiency by t rank,
+            // and the (T, U) block limit min(G_W, G_R).
+            if ((tm >> lane) & 1u) {
+                const int tr = __popc(tm & below);
+                const int wb = ct.wb[lane];
+                const int gw = ct.gw[lane];
+                w.tinfo[tr] = make_float2(__int_as_float(wb), ct.lane[lane]);
+                for (int ur = 0; ur < nU; ++ur) {
+                    const int gr = reg_blocks(a, ct, w.regs[ur], wb, lane, w.warps_r[ur], w.wb_max[ur]);
+                    w.gwr[tr][ur] = (unsigned char)min(gw, gr);
+                }
+            }
+            // ---- (U, C) pair table for the emitting pass; lane = pair rank.
+            if (EMIT && lane < nUC) {
+                const int ur = lane / nC, cr = lane - (lane / nC) * nC;
+                w.uc[lane] = make_float4(w.cnm[ur], w.cm[ur], __int_as_float(ur), __int_as_float(w.gs[cr]));
+            }
+            // ---- waves/slots factor rows, compacted to this kernel's grid sizes, and
+            // their minima.
+            const bool g_dense = gm == g_ok;
+            if (lane < kMaxB) {
+                if (g_dense) {
+                    w.iparmin[lane] = ct.iparmin[lane];
+                } else {
+                    float mn = kInf;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float f = j < nG ? ct.ipar[lane][w.gpos[j]] : kInf;
+                        if (EMIT) w.iparc[lane][j] = f;
+                        mn = fminf(mn, f);
                     }
+                    w.iparmin[lane] = mn;
+                }
+            }
+            __syncwarp();
+
+            float lc = kInf;  // this lane's entry of the warp's top-k list (lanes < k)
+            int li = -1;
+            float tau_c = kInf;  // the list's k-th key
+            int tau_i = -1;
+            float tau0 = kInf;   // bound from the pre-pass
+
+            // Merge: each candidate lane walks its triple's grid sizes in increasing
+            // cost (the order of X * ipar(B*, G) over G depends on B* only); the warp
+            // repeatedly inserts the smallest head until no head can enter the list.
+            auto merge = [&](bool any, int B, float X, int base) {
+                int r = 0;
+                float hc = kInf;
+                int hi = 0x7fffffff;
+                auto advance = [&]() {
+                    hc = kInf;
+                    hi = 0x7fffffff;
+                    while (r < x.n_g) {
+                        const int g = ct.perm[B - 1][r++];
+                        if ((gm >> g) & 1u) {
+                            hc = __fmul_rn(X, ct.ipar[B - 1][g]);
+                            hi = base + __popc(gm & ((1u << g) - 1u)) * nUC;
+                            break;
+                        }
+                    }
+                };
+                if (any) advance();
+                for (;;) {
+                    const unsigned mc = __reduce_min_sync(kFull, __float_as_uint(hc));
+                    const float mcf = __uint_as_float(mc);
+                    const unsigned mi = __reduce_min_sync(kFull, hc == mcf ? (unsigned)hi : 0xffffffffu);
+                    if (mc >= 0x7f800000u || mcf > tau0 || !key_less(mcf, (int)mi, tau_c, tau_i)) break;
+                    warp_list_insert(lc, li, tau_c, tau_i, mcf, (int)mi, k, lane);
+                    if (hc == mcf && hi == (int)mi) advance();
                 }
             };
-            if (any) advance();
-            for (;;) {
-                const unsigned mc = __reduce_min_sync(kFull, __float_as_uint(hc));
-                const float mcf = __uint_as_float(mc);
-                const unsigned mi = __reduce_min_sync(kFull, hc == mcf ? (unsigned)hi : 0xffffffffu);
-                if (mc >= 0x7f800000u || mcf > tau0 || !key_less(mcf, (int)mi, tau_c, tau_i)) break;
-                warp_list_insert(lc, li, tau_c, tau_i, mcf, (int)mi, k, lane);
-                if (hc == mcf && hi == (int)mi) advance();
-            }
-        };
 
-        if (!EMIT) {
-            // Candidates: triples whose truncated minimum key does not exceed the
-            // truncated bound min(tau, tau0) (a superset of the exact test; the
-            // merge applies the exact one).
-            unsigned bkey = __float_as_uint(tau0) >> 16;
-            for (int it = 0; it < n_iter; ++it) {
-                const bool any = w.key[(it << 5) + lane] <= bkey;
-                if (__ballot_sync(kFull, any) == 0u) continue;
-                int B = 0, base = 0;
-                float X = 0.0f;
-                if (any) {
-                    const int tr = (it << 5) + lane;
-                    const int t_r = tr / nUC;
-                    const int uc_r = tr - t_r * nUC;
-                    int W;
-                    triple(t_r, uc_r, B, W, X);
-                    base = t_r * g_stride + uc_r;
+            if (!EMIT) {
+                // ---- pre-pass over (T, U) pairs, lane = pair rank mod 32, carveouts inner.
+                // Every grid size G of a triple costs X(T,U,C) * ipar(B*, G); a product by
+                // X > 0 is monotone under round-to-nearest, so the triple's cheapest point
+                // is exactly X * min_G ipar(B*, G). Each lane keeps its four smallest triple
+                // minima; the k-th smallest over the warp bounds the kernel's k-th best
+                // cost (k distinct triples each own a point <= tau0). Each minimum is also
+                // stored at its triple rank (t rank * nUC + u rank * nC + c rank), so that
+                // the carveouts of one (T, U) pair sit in neighbouring lanes of the scan.
+                const int nP = nT * nU;
+                const int n_prow = (nP + 31) >> 5;
+                const int n_rows = (nP * nC + 31) >> 5;
+                const float rcp_u = __frcp_rn((float)nU), rcp_c = __frcp_rn((float)nC);
+                const float rcp_uc = __frcp_rn((float)nUC);
+                w.key[((n_rows - 1) << 5) + lane] = __int_as_float(0x7fc00000);  // tail: no triple (NaN)
+                __syncwarp();
+                float m0 = kInf, m1 = kInf, m2 = kInf, m3 = kInf;
+                for (int j = 0; j < n_prow; ++j) {
+                    const int pr = lane + (j << 5);
+                    if (pr >= nP) break;
+                    const int t_r = small_div(pr, rcp_u);
+                    const int u_r = pr - t_r * nU;
+                    const float2 ti = w.tinfo[t_r];
+                    const int wb = __float_as_int(ti.x);
+                    const float ln = ti.y;
+                    const int gwr = w.gwr[t_r][u_r];
+                    const float cnm = w.cnm[u_r], cmv = w.cm[u_r];
+                    float* krow = &w.key[pr * nC];
+                    for (int c = 0; c < nC; ++c) {
+                        float key = __int_as_float(0x7fc00000);  // no point (NaN): never a candidate
+                        const int B = min(gwr, w.gs[c]);
+                        if (B > 0) {
+                            const float X = __fmul_rn(__fmaf_rn(cmv, ct.hide[B * wb], cnm), ln);
+                            // NaN (from infinite counts) is ranked as +inf
+                            float m = fminf(__fmul_rn(X, w.iparmin[B - 1]), kInf);
+                            key = m;
+                            float lo;
+                            lo = fminf(m0, m); m = fmaxf(m0, m); m0 = lo;
+                            lo = fminf(m1, m); m = fmaxf(m1, m); m1 = lo;
+                            lo = fminf(m2, m); m = fmaxf(m2, m); m2 = lo;
+                            m3 = fminf(m3, m);
+                        }
+                        krow[c] = key;
+                    }
                 }
-                merge(any, B, X, base);
-                bkey = __float_as_uint(fminf(tau_c, tau0)) >> 16;
-            }
-        } else {
-            // Every point's cost is computed and written; each triple's minimum
-            // decides whether the warp merges.
-            const int64_t off = pt_off[kid];
-            int t_r = t0, uc_r = uc0;
-            for (int it = 0; it < n_iter; ++it) {
-                bool any = false;
-                float X = 0.0f;
-                int B = 0, base = 0;
-                if (t_r < nT) {
-                    int W;
-                    triple(t_r, uc_r, B, W, X);
-                    base = t_r * g_stride + uc_r;
-                    if (B > 0) {
-                        const float* row = ipar_rows + (B - 1) * 16;
-                        any = __fmul_rn(X, iparmin[B - 1]) <= tau_c;
+                __syncwarp();
+                for (int r = 0; r < k; ++r) {
+                    const unsigned mb = __reduce_min_sync(kFull, __float_as_uint(m0));
+                    tau0 = __uint_as_float(mb);
+                    if (mb >= 0x7f800000u) break;
+                    const unsigned who = __ballot_sync(kFull, __float_as_uint(m0) == mb);
+                    if (lane == __ffs(who) - 1) {
+                        m0 = m1;
+                        m1 = m2;
+                        m2 = m3;
+                        m3 = kInf;
+                    }
+                }
+
+                // ---- main pass: lanes scan the stored minima; candidates are triples whose
+                // minimum does not exceed the bound min(tau, tau0).
+                float bound = tau0;
+                for (int r = 0; r < n_rows; ++r) {
+                    const bool any = w.key[(r << 5) + lane] <= bound;
+                    if (__ballot_sync(kFull, any) == 0u) continue;
+                    int B = 0, base = 0;
+                    float X = 0.0f;
+                    if (any) {
+                        const int tri = (r << 5) + lane;
+                        const int t_r = small_div(tri, rcp_uc);
+                        const int uc_r = tri - t_r * nUC;
+                        const int u_r = small_div(uc_r, rcp_c);
+                        const int c = uc_r - u_r * nC;
+                        const float2 ti = w.tinfo[t_r];
+                        B = min((int)w.gwr[t_r][u_r], w.gs[c]);
+                        X = __fmul_rn(__fmaf_rn(w.cm[u_r], ct.hide[B * __float_as_int(ti.x)], w.cnm[u_r]), ti.y);
+                        base = t_r * g_stride + uc_r;
+                    }
+                    merge(any, B, X, base);
+                    bound = fminf(tau_c, tau0);
+                }
+            } else {
+                // ---- emitting pass: every point's B*, W* and cost is written; lanes walk
+                // (T, U, C) triples, the t rank advancing by 32 / nUC per step.
+                const float* ipar_rows = g_dense ? &ct.ipar[0][0] : &w.iparc[0][0];
+                const int t0 = lane / nUC, uc0 = lane - (lane / nUC) * nUC;
+                const int dq = 32 / nUC, dr = 32 - (32 / nUC) * nUC;
+                const int n_iter = (nT * nUC + 31) >> 5;
+                const int64_t off = pt_off[kid];
+                int t_r = t0, uc_r = uc0;
+                for (int it = 0; it < n_iter; ++it) {
+                    bool any = false;
+                    float X = 0.0f;
+                    int B = 0, base = 0;
+                    if (t_r < nT) {
+                        const float4 ucv = w.uc[uc_r];
+                        const int ur = __float_as_int(ucv.z);
+                        const float2 ti = w.tinfo[t_r];
+                        B = min((int)w.gwr[t_r][ur], __float_as_int(ucv.w));
+                        const int W = B * __float_as_int(ti.x);
+                        X = __fmul_rn(__fmaf_rn(ucv.y, ct.hide[W], ucv.x), ti.y);
+                        base = t_r * g_stride + uc_r;
+                        if (B > 0) {
+                            const float* row = ipar_rows + (B - 1) * 16;
+                            any = __fmul_rn(X, w.iparmin[B - 1]) <= tau_c;
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            if (j < nG) {
+                            for (int j = 0; j < 16; ++j) {
+                                if (j < nG) {
+                                    const int64_t at = off + base + j * nUC;
+                                    if (pt_b) pt_b[at] = B;
+                                    if (pt_w) pt_w[at] = W;
+                                    if (pt_c) pt_c[at] = __fmul_rn(X, row[j]);
+                                }
+                            }
+                        } else {
+                            for (int j = 0; j < nG; ++j) {
                                 const int64_t at = off + base + j * nUC;
-                                if (pt_b) pt_b[at] = B;
-                                if (pt_w) pt_w[at] = W;
-                                if (pt_c) pt_c[at] = __fmul_rn(X, row[j]);
+                                if (pt_b) pt_b[at] = 0;
+                                if (pt_w) pt_w[at] = 0;
+                                if (pt_c) pt_c[at] = kInf;
                             }
                         }
-                    } else {
-                        for (int j = 0; j < nG; ++j) {
-                            const int64_t at = off + base + j * nUC;
-                            if (pt_b) pt_b[at] = 0;
-                            if (pt_w) pt_w[at] = 0;
-                            if (pt_c) pt_c[at] = kInf;
+                        t_r += dq;
+                        uc_r += dr;
+                        if (uc_r >= nUC) {
+                            uc_r -= nUC;
+                            ++t_r;
                         }
                     }
-                    t_r += dq;
-                    uc_r += dr;
-                    if (uc_r >= nUC) {
-                        uc_r -= nUC;
-                        ++t_r;
-                    }
+                    if (__ballot_sync(kFull, any) == 0u) continue;
+                    merge(any, B, X, base);
                 }
-                if (__ballot_sync(kFull, any) == 0u) continue;
-                merge(any, B, X, base);
             }
-        }
 
-        if (lane < k) {
-            topk_idx[kid * k + lane] = li;
-            topk_cost[kid * k + lane] = lc;
-        }
-        __syncwarp();  // the warp's tables are rewritten for the next kernel
+            if (lane < k) {
+                topk_idx[kid * k + lane] = li;
+                topk_cost[kid * k + lane] = lc;
+            }
+        } while (false);
+        __syncwarp();  // the warp's tables are rewritten for the next descriptor
+        kid = nk;
+        v = v_next;
     }
 }
 
