@@ -48,9 +48,12 @@ L2_FLUSH_BYTES = 256 << 20       # larger than the 126.5 MB L2
 
 
 def algorithmic_instructions(descs, axes):
-    """Thread-instructions of the factored evaluation (this kernel's minimum):
-    per point 1 FMUL (cost = X * ipar(B*, G)) + 1 FSETP (compare with the k-th best);
-    per (T, U, C) triple 5 (min for B*, IMUL for W*, hide lookup, FFMA + FMUL for X).
+    """Thread-instructions of the factored evaluation: grid size does not enter the
+    occupancy (Eqs. 1-5) and every point's cost is X(T,U,C) * ipar(B*, G), so the work
+    is per (T, U, C) triple: B* (min), W* (multiply), hide lookup, FFMA, lane-efficiency
+    multiply, min_G ipar lookup and multiply (the triple's cheapest point), compare with
+    the bound = 8; the grid sizes of a triple are ranked only where its cheapest point
+    can enter the top-k.
     """
     sizes = gen.space_sizes(descs)
     m = np.asarray(descs["space_mask"], dtype=np.uint64)
@@ -58,7 +61,7 @@ def algorithmic_instructions(descs, axes):
     for b in range(16):
         n_g += ((m >> np.uint64(32 + b)) & np.uint64(1)).astype(np.int64)
     triples = np.where(n_g > 0, sizes // np.maximum(n_g, 1), 0)
-    return int(2 * sizes.sum() + 5 * triples.sum())
+    return int(8 * triples.sum())
 
 
 def kernel_source_hash():

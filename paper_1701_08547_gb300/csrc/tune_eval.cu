@@ -66,6 +66,7 @@ struct CtaTables {
     unsigned short rwarps[256];      // register-limited warps by R (Eq. 4, per-warp allocation)
     unsigned short rwbmax[256];      // largest W_B whose block fits the per-block register limit, by R
     int cap_lo[4];                   // first capacity index allowed by carveout position c
+    int order_safe;                  // 1: distinct ipar values of a row differ by more than 2^-21 relative
 };
 
 struct WarpTables {
@@ -107,6 +108,7 @@ __device__ void build_cta_tables(const EvalParams& p, const tune_arch& a, CtaTab
         ct.divt[w][t] = (unsigned char)(w / wb);
     }
     int tid = threadIdx.x;
+    if (tid == 0) ct.order_safe = 1;
     __syncthreads();
     if (tid < kMaxB) {  // insertion sort of row tid by (ipar value, g position), in place
         float mn = __int_as_float(0x7f800000);
@@ -121,6 +123,13 @@ __device__ void build_cta_tables(const EvalParams& p, const tune_arch& a, CtaTab
                 --j;
             }
             ord[j] = (unsigned char)g;
+        }
+        // With distinct values this far apart, X * v keeps their order strictly for every
+        // X > 0 (no underflow), so a walk in perm order meets equal costs only from
+        // equal values, in increasing g (and index) order.
+        for (int r = 0; r + 1 < x.n_g; ++r) {
+            const float v1 = ct.ipar[tid][ord[r]], v2 = ct.ipar[tid][ord[r + 1]];
+            if (v2 != v1 && __fsub_rn(v2, v1) <= __fmul_rn(v1, 0x1p-21f)) ct.order_safe = 0;
         }
     }
     if (tid < 32) {
@@ -369,8 +378,12 @@ __global__ void __maxnreg__(64)
 
             // Merge: each candidate lane walks its triple's grid sizes in increasing
             // cost (the order of X * ipar(B*, G) over G depends on B* only); the warp
-            // repeatedly inserts the smallest head until no head can enter the list.
+            // repeatedly takes the smallest head and inserts it while it beats the k-th
+            // entry. A lane's walk is in (cost, index) order unless two nearly equal
+            // ipar values round to one cost, or X underflows; then (relaxed) equal
+            // costs are walked on until a head costs more than the k-th entry.
             auto merge = [&](bool any, int B, float X, int base) {
+                const bool relaxed = !ct.order_safe || __any_sync(kFull, any && !(X >= 0x1p-100f));
                 int r = 0;
                 float hc = kInf;
                 int hi = 0x7fffffff;
@@ -391,8 +404,10 @@ __global__ void __maxnreg__(64)
                     const unsigned mc = __reduce_min_sync(kFull, __float_as_uint(hc));
                     const float mcf = __uint_as_float(mc);
                     const unsigned mi = __reduce_min_sync(kFull, hc == mcf ? (unsigned)hi : 0xffffffffu);
-                    if (mc >= 0x7f800000u || mcf > tau0 || !key_less(mcf, (int)mi, tau_c, tau_i)) break;
-                    warp_list_insert(lc, li, tau_c, tau_i, mcf, (int)mi, k, lane);
+                    if (mc >= 0x7f800000u || mcf > tau0 || mcf > tau_c) break;
+                    const bool enters = key_less(mcf, (int)mi, tau_c, tau_i);
+                    if (!enters && !relaxed) break;
+                    if (enters) warp_list_insert(lc, li, tau_c, tau_i, mcf, (int)mi, k, lane);
                     if (hc == mcf && hi == (int)mi) advance();
                 }
             };
@@ -456,16 +471,30 @@ __global__ void __maxnreg__(64)
                     }
                 }
 
-                // ---- main pass: lanes scan the stored minima; candidates are triples whose
-                // minimum does not exceed the bound min(tau, tau0).
-                float bound = tau0;
+                // ---- candidates: the triples whose minimum does not exceed tau0 (every point
+                // of the top-k belongs to one). Their ranks are compacted in place to the
+                // front of the key array: a slot written in row r lies in rows <= r, whose
+                // keys every lane has read before the ballot.
+                int n_cand = 0;
                 for (int r = 0; r < n_rows; ++r) {
-                    const bool any = w.key[(r << 5) + lane] <= bound;
-                    if (__ballot_sync(kFull, any) == 0u) continue;
+                    const bool cand = w.key[(r << 5) + lane] <= tau0;
+                    const unsigned ball = __ballot_sync(kFull, cand);
+                    if (cand) w.key[n_cand + __popc(ball & below)] = __int_as_float((r << 5) + lane);
+                    n_cand += __popc(ball);
+                }
+                __syncwarp();
+
+                // ---- selection: candidate triples 32 at a time, one per lane; each lane walks
+                // its triple's grid sizes in increasing cost. The first batch starts from an
+                // empty list, so its points, extracted in increasing cost, are appended at
+                // list positions 0, 1, ... (a point that comes out of index order among equal
+                // costs is inserted at its place instead); later batches merge into the list.
+                for (int c0 = 0; c0 < n_cand; c0 += 32) {
+                    const bool has = c0 + lane < n_cand;
                     int B = 0, base = 0;
                     float X = 0.0f;
-                    if (any) {
-                        const int tri = (r << 5) + lane;
+                    if (has) {
+                        const int tri = __float_as_int(w.key[c0 + lane]);
                         const int t_r = small_div(tri, rcp_uc);
                         const int uc_r = tri - t_r * nUC;
                         const int u_r = small_div(uc_r, rcp_c);
@@ -475,8 +504,57 @@ __global__ void __maxnreg__(64)
                         X = __fmul_rn(__fmaf_rn(w.cm[u_r], ct.hide[B * __float_as_int(ti.x)], w.cnm[u_r]), ti.y);
                         base = t_r * g_stride + uc_r;
                     }
-                    merge(any, B, X, base);
-                    bound = fminf(tau_c, tau0);
+                    if (c0 > 0) {
+                        merge(has, B, X, base);
+                        continue;
+                    }
+                    int rg = 0;
+                    float hc = kInf;
+                    int hi = 0x7fffffff;
+                    auto advance = [&]() {
+                        hc = kInf;
+                        hi = 0x7fffffff;
+                        while (rg < x.n_g) {
+                            const int g = ct.perm[B - 1][rg++];
+                            if ((gm >> g) & 1u) {
+                                hc = __fmul_rn(X, ct.ipar[B - 1][g]);
+                                hi = base + __popc(gm & ((1u << g) - 1u)) * nUC;
+                                break;
+                            }
+                        }
+                    };
+                    if (has) advance();
+                    const bool relaxed = !ct.order_safe || __any_sync(kFull, has && !(X >= 0x1p-100f));
+                    int cnt = 0;  // list entries so far; (prev_c, prev_i) is the largest
+                    float prev_c = 0.0f;
+                    int prev_i = -1;
+                    for (;;) {
+                        const unsigned mc = __reduce_min_sync(kFull, __float_as_uint(hc));
+                        const float mcf = __uint_as_float(mc);
+                        if (mc >= 0x7f800000u || mcf > tau0 || mcf > tau_c) break;
+                        const unsigned mi = __reduce_min_sync(kFull, hc == mcf ? (unsigned)hi : 0xffffffffu);
+                        if (cnt == k && !relaxed && !key_less(mcf, (int)mi, tau_c, tau_i)) break;
+                        if (cnt < k && (cnt == 0 || key_less(prev_c, prev_i, mcf, (int)mi))) {
+                            if (lane == cnt) {  // in order: append
+                                lc = mcf;
+                                li = (int)mi;
+                            }
+                            prev_c = mcf;
+                            prev_i = (int)mi;
+                            if (++cnt == k) {
+                                tau_c = __shfl_sync(kFull, lc, k - 1);
+                                tau_i = __shfl_sync(kFull, li, k - 1);
+                            }
+                        } else if (key_less(mcf, (int)mi, tau_c, tau_i)) {
+                            // out of index order among equal costs: insert at its place
+                            warp_list_insert(lc, li, tau_c, tau_i, mcf, (int)mi, k, lane);
+                            if (cnt < k && ++cnt == k) {
+                                tau_c = __shfl_sync(kFull, lc, k - 1);
+                                tau_i = __shfl_sync(kFull, li, k - 1);
+                            }
+                        }
+                        if (hc == mcf && hi == (int)mi) advance();
+                    }
                 }
             } else {
                 // ---- emitting pass: every point's B*, W* and cost is written; lanes walk
