@@ -201,6 +201,11 @@ __device__ __forceinline__ bool key_less(float c, int i, float c2, int i2)
     return c < c2 || (c == c2 && i < i2);
 }
 
+template <int N>
+struct IntC {
+    static constexpr int value = N;
+};
+
 // floor(n / d) for 0 <= n < 8192 and 1 <= d <= 32, given rcp = 1/d rounded to
 // nearest: (n + 1/2) / d lies at least 1/64 away from an integer, far more than
 // the rounding error of the product, so truncation is exact.
@@ -429,33 +434,56 @@ __global__ void __maxnreg__(64)
                 w.key[((n_rows - 1) << 5) + lane] = __int_as_float(0x7fc00000);  // tail: no triple (NaN)
                 __syncwarp();
                 float m0 = kInf, m1 = kInf, m2 = kInf, m3 = kInf;
-                for (int j = 0; j < n_prow; ++j) {
-                    const int pr = lane + (j << 5);
-                    if (pr >= nP) break;
-                    const int t_r = small_div(pr, rcp_u);
-                    const int u_r = pr - t_r * nU;
-                    const float2 ti = w.tinfo[t_r];
-                    const int wb = __float_as_int(ti.x);
-                    const float ln = ti.y;
-                    const int gwr = w.gwr[t_r][u_r];
-                    const float cnm = w.cnm[u_r], cmv = w.cm[u_r];
-                    float* krow = &w.key[pr * nC];
-                    for (int c = 0; c < nC; ++c) {
-                        float key = __int_as_float(0x7fc00000);  // no point (NaN): never a candidate
-                        const int B = min(gwr, w.gs[c]);
-                        if (B > 0) {
-                            const float X = __fmul_rn(__fmaf_rn(cmv, ct.hide[B * wb], cnm), ln);
-                            // NaN (from infinite counts) is ranked as +inf
-                            float m = fminf(__fmul_rn(X, w.iparmin[B - 1]), kInf);
-                            key = m;
-                            float lo;
-                            lo = fminf(m0, m); m = fmaxf(m0, m); m0 = lo;
-                            lo = fminf(m1, m); m = fmaxf(m1, m); m1 = lo;
-                            lo = fminf(m2, m); m = fmaxf(m2, m); m2 = lo;
-                            m3 = fminf(m3, m);
+                // one body per carveout count, so that G_S stays in registers and a pair's
+                // minima are stored with one vector store
+                auto pairs = [&](auto nc_tag) {
+                    constexpr int NC = decltype(nc_tag)::value;
+                    int gs[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) gs[c] = w.gs[c];
+                    for (int j = 0; j < n_prow; ++j) {
+                        const int pr = lane + (j << 5);
+                        if (pr >= nP) break;
+                        const int t_r = small_div(pr, rcp_u);
+                        const int u_r = pr - t_r * nU;
+                        const float2 ti = w.tinfo[t_r];
+                        const int wb = __float_as_int(ti.x);
+                        const float ln = ti.y;
+                        const int gwr = w.gwr[t_r][u_r];
+                        const float cnm = w.cnm[u_r], cmv = w.cm[u_r];
+                        float key[NC];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            key[c] = __int_as_float(0x7fc00000);  // no point (NaN): never a candidate
+                            const int B = min(gwr, gs[c]);
+                            if (B > 0) {
+                                const float X = __fmul_rn(__fmaf_rn(cmv, ct.hide[B * wb], cnm), ln);
+                                // NaN (from infinite counts) is ranked as +inf
+                                float m = fminf(__fmul_rn(X, w.iparmin[B - 1]), kInf);
+                                key[c] = m;
+                                float lo;
+                                lo = fminf(m0, m); m = fmaxf(m0, m); m0 = lo;
+                                lo = fminf(m1, m); m = fmaxf(m1, m); m1 = lo;
+                                lo = fminf(m2, m); m = fmaxf(m2, m); m2 = lo;
+                                m3 = fminf(m3, m);
+                            }
                         }
-                        krow[c] = key;
+                        float* krow = &w.key[pr * NC];
+                        if constexpr (NC == 4) {
+                            *reinterpret_cast<float4*>(krow) = make_float4(key[0], key[1], key[2], key[3]);
+                        } else if constexpr (NC == 2) {
+                            *reinterpret_cast<float2*>(krow) = make_float2(key[0], key[1]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) krow[c] = key[c];
+                        }
                     }
+                };
+                switch (nC) {
+                    case 1: pairs(IntC<1>{}); break;
+                    case 2: pairs(IntC<2>{}); break;
+                    case 3: pairs(IntC<3>{}); break;
+                    default: pairs(IntC<4>{}); break;
                 }
                 __syncwarp();
                 for (int r = 0; r < k; ++r) {
