@@ -67,17 +67,17 @@ struct CtaTables {
     unsigned short rwbmax[256];      // largest W_B whose block fits the per-block register limit, by R
     int cap_lo[4];                   // first capacity index allowed by carveout position c
     int order_safe;                  // 1: distinct ipar values of a row differ by more than 2^-21 relative
+    int unit_shift;                  // log2 of the shared-memory allocation unit, or -1
 };
 
 struct WarpTables {
     float iparmin[kMaxB];    // min over the kernel's grid sizes of ipar(b, G)
     unsigned char gwr[32][8];  // min(G_W, G_R) by (t rank, u rank)
     float cnm[8], cm[8];     // by u rank
-    int warps_r[8];          // register-limited warps (clamped to kMaxW) by u rank
-    int wb_max[8];           // largest W_B whose block fits the per-block register limit
     int regs[8];             // R by u rank
     int gs[4];               // G_S by c rank
-    float2 tinfo[32];        // (W_B as int bits, lane efficiency) by t rank
+    int4 tinfo[32];          // by t rank: W_B, lane efficiency (float bits), t position, G_W
+    int ru[8];               // by u rank: register-limited warps | (largest W_B that fits) << 8
     int gpos[16];            // g position by g rank
     union {
         float key[32 * 32];  // ranking pass: each triple's minimum cost, by (row, lane)
@@ -108,7 +108,11 @@ __device__ void build_cta_tables(const EvalParams& p, const tune_arch& a, CtaTab
         ct.divt[w][t] = (unsigned char)(w / wb);
     }
     int tid = threadIdx.x;
-    if (tid == 0) ct.order_safe = 1;
+    if (tid == 0) {
+        ct.order_safe = 1;
+        const int u = a.smem_alloc_unit;
+        ct.unit_shift = (u & (u - 1)) == 0 ? __ffs(u) - 1 : -1;
+    }
     __syncthreads();
     if (tid < kMaxB) {  // insertion sort of row tid by (ipar value, g position), in place
         float mn = __int_as_float(0x7f800000);
@@ -167,16 +171,36 @@ __device__ void build_cta_tables(const EvalParams& p, const tune_arch& a, CtaTab
     }
 }
 
+// q = floor(n / d) for 0 <= n < 2^25 and 1 <= d < 2^25: a single-precision estimate
+// (within 2 of q) corrected with exact integer remainders.
+__device__ __forceinline__ int udiv_small(int n, int d)
+{
+    int q = __float2int_rz(__fmul_rn((float)n, __frcp_rn((float)d)));
+    int r = n - q * d;
+    while (r < 0) {
+        --q;
+        r += d;
+    }
+    while (r >= d) {
+        ++q;
+        r -= d;
+    }
+    return q;
+}
+
 // G_S (Eq. 5) as smem_blocks(), starting the capacity search at the carveout's
 // first admissible capacity (carveout position cp).
 __device__ __forceinline__ int smem_blocks_from(const tune_arch& a, const CtaTables& ct, int s0, int cp)
 {
     if (s0 > a.smem_block_max) return 0;
-    const int s_alloc = ceil_div(s0 + a.smem_reserved_block, a.smem_alloc_unit) * a.smem_alloc_unit;
+    const int need = s0 + a.smem_reserved_block;
+    const int unit = a.smem_alloc_unit;
+    const int s_alloc = ct.unit_shift >= 0 ? ((need + unit - 1) >> ct.unit_shift) << ct.unit_shift
+                                           : ceil_div(need, unit) * unit;
     if (s_alloc == 0) return a.max_blocks_sm;
     for (int i = ct.cap_lo[cp]; i < a.n_smem_caps; ++i) {
         const int ci = a.smem_caps[i];
-        if (ci >= s_alloc) return ci / s_alloc;
+        if (ci >= s_alloc) return udiv_small(ci, s_alloc);
     }
     return 0;
 }
@@ -330,27 +354,42 @@ __global__ void __maxnreg__(64)
                 const int R = r0 + 4 * (U - 1);
                 unit_costs(kd.n, kd.d, U, ct.rcp, a.work_scale, w.cnm[ur], w.cm[ur]);
                 w.regs[ur] = R;
+                int warps, wbmax;
                 if (R >= 0 && R < 256) {
-                    w.warps_r[ur] = ct.rwarps[R];
-                    w.wb_max[ur] = ct.rwbmax[R];
+                    warps = ct.rwarps[R];
+                    wbmax = ct.rwbmax[R];
                 } else {
-                    reg_params(a, R, w.warps_r[ur], w.wb_max[ur]);
+                    reg_params(a, R, warps, wbmax);
                 }
+                w.ru[ur] = warps | (wbmax << 8);
             }
             if (lane < 4 && ((cm >> lane) & 1u)) w.gs[__popc(cm & below)] = smem_blocks_from(a, ct, s0, lane);
+            // Per-warp register allocation with R > 0 for every unroll (r0 > 0): the (T, U)
+            // block limit is min(G_W, W_B > wbmax ? 0 : floor(warps / W_B)) and is formed
+            // where it is used; otherwise (per-block allocation, R = 0) it is tabulated.
+            const bool simple = !EMIT && a.reg_alloc_mode == 0 && r0 > 0;
             __syncwarp();
-            // ---- per thread count (lane = t position): W_B and lane efficiency by t rank,
-            // and the (T, U) block limit min(G_W, G_R).
+            // ---- per thread count (lane = t position): W_B, lane efficiency, G_W by t rank
+            // (and the tabulated block limit min(G_W, G_R)).
             if ((tm >> lane) & 1u) {
                 const int tr = __popc(tm & below);
                 const int wb = ct.wb[lane];
                 const int gw = ct.gw[lane];
-                w.tinfo[tr] = make_float2(__int_as_float(wb), ct.lane[lane]);
-                for (int ur = 0; ur < nU; ++ur) {
-                    const int gr = reg_blocks(a, ct, w.regs[ur], wb, lane, w.warps_r[ur], w.wb_max[ur]);
-                    w.gwr[tr][ur] = (unsigned char)min(gw, gr);
+                w.tinfo[tr] = make_int4(wb, __float_as_int(ct.lane[lane]), lane, gw);
+                if (!simple) {
+                    for (int ur = 0; ur < nU; ++ur) {
+                        const int ru = w.ru[ur];
+                        const int gr = reg_blocks(a, ct, w.regs[ur], wb, lane, ru & 0xff, ru >> 8);
+                        w.gwr[tr][ur] = (unsigned char)min(gw, gr);
+                    }
                 }
             }
+            // min(G_W, G_R) of (t rank, u rank); ti = tinfo[t rank]
+            auto block_limit = [&](int t_r, const int4& ti, int u_r) -> int {
+                if (!simple) return w.gwr[t_r][u_r];
+                const int ru = w.ru[u_r];
+                return min(ti.w, ti.x > (ru >> 8) ? 0 : (int)ct.divt[ru & 0xff][ti.z]);
+            };
             // ---- (U, C) pair table for the emitting pass; lane = pair rank.
             if (EMIT && lane < nUC) {
                 const int ur = lane / nC, cr = lane - (lane / nC) * nC;
@@ -446,10 +485,10 @@ __global__ void __maxnreg__(64)
                         if (pr >= nP) break;
                         const int t_r = small_div(pr, rcp_u);
                         const int u_r = pr - t_r * nU;
-                        const float2 ti = w.tinfo[t_r];
-                        const int wb = __float_as_int(ti.x);
-                        const float ln = ti.y;
-                        const int gwr = w.gwr[t_r][u_r];
+                        const int4 ti = w.tinfo[t_r];
+                        const int wb = ti.x;
+                        const float ln = __int_as_float(ti.y);
+                        const int gwr = block_limit(t_r, ti, u_r);
                         const float cnm = w.cnm[u_r], cmv = w.cm[u_r];
                         float key[NC];
 #pragma unroll
@@ -527,9 +566,9 @@ __global__ void __maxnreg__(64)
                         const int uc_r = tri - t_r * nUC;
                         const int u_r = small_div(uc_r, rcp_c);
                         const int c = uc_r - u_r * nC;
-                        const float2 ti = w.tinfo[t_r];
-                        B = min((int)w.gwr[t_r][u_r], w.gs[c]);
-                        X = __fmul_rn(__fmaf_rn(w.cm[u_r], ct.hide[B * __float_as_int(ti.x)], w.cnm[u_r]), ti.y);
+                        const int4 ti = w.tinfo[t_r];
+                        B = min(block_limit(t_r, ti, u_r), w.gs[c]);
+                        X = __fmul_rn(__fmaf_rn(w.cm[u_r], ct.hide[B * ti.x], w.cnm[u_r]), __int_as_float(ti.y));
                         base = t_r * g_stride + uc_r;
                     }
                     if (c0 > 0) {
@@ -600,10 +639,10 @@ __global__ void __maxnreg__(64)
                     if (t_r < nT) {
                         const float4 ucv = w.uc[uc_r];
                         const int ur = __float_as_int(ucv.z);
-                        const float2 ti = w.tinfo[t_r];
+                        const int4 ti = w.tinfo[t_r];
                         B = min((int)w.gwr[t_r][ur], __float_as_int(ucv.w));
-                        const int W = B * __float_as_int(ti.x);
-                        X = __fmul_rn(__fmaf_rn(ucv.y, ct.hide[W], ucv.x), ti.y);
+                        const int W = B * ti.x;
+                        X = __fmul_rn(__fmaf_rn(ucv.y, ct.hide[W], ucv.x), __int_as_float(ti.y));
                         base = t_r * g_stride + uc_r;
                         if (B > 0) {
                             const float* row = ipar_rows + (B - 1) * 16;
