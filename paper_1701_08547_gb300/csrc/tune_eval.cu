@@ -225,6 +225,8 @@ __device__ __forceinline__ bool key_less(float c, int i, float c2, int i2)
     return c < c2 || (c == c2 && i < i2);
 }
 
+constexpr int kListDepth = 2;  // smallest triple minima each lane keeps for the bound tau0 (2 or 4)
+
 template <int N>
 struct IntC {
     static constexpr int value = N;
@@ -460,17 +462,20 @@ __global__ void __maxnreg__(64)
                 // ---- pre-pass over (T, U) pairs, lane = pair rank mod 32, carveouts inner.
                 // Every grid size G of a triple costs X(T,U,C) * ipar(B*, G); a product by
                 // X > 0 is monotone under round-to-nearest, so the triple's cheapest point
-                // is exactly X * min_G ipar(B*, G). Each lane keeps its four smallest triple
-                // minima; the k-th smallest over the warp bounds the kernel's k-th best
+                // is exactly X * min_G ipar(B*, G). Each lane keeps its kListDepth smallest
+                // triple minima; the k-th smallest over the warp bounds the kernel's k-th best
                 // cost (k distinct triples each own a point <= tau0). Each minimum is also
                 // stored at its triple rank (t rank * nUC + u rank * nC + c rank), so that
                 // the carveouts of one (T, U) pair sit in neighbouring lanes of the scan.
                 const int nP = nT * nU;
                 const int n_prow = (nP + 31) >> 5;
-                const int n_rows = (nP * nC + 31) >> 5;
+                const int n_blk = (nP * nC + 127) >> 7;  // blocks of 128 triples for the scan
                 const float rcp_u = __frcp_rn((float)nU), rcp_c = __frcp_rn((float)nC);
                 const float rcp_uc = __frcp_rn((float)nUC);
-                w.key[((n_rows - 1) << 5) + lane] = __int_as_float(0x7fc00000);  // tail: no triple (NaN)
+                {  // tail of the last block: no triple (NaN)
+                    const float nan = __int_as_float(0x7fc00000);
+                    *reinterpret_cast<float4*>(&w.key[((n_blk - 1) << 7) + 4 * lane]) = make_float4(nan, nan, nan, nan);
+                }
                 __syncwarp();
                 float m0 = kInf, m1 = kInf, m2 = kInf, m3 = kInf;
                 // one body per carveout count, so that G_S stays in registers and a pair's
@@ -502,9 +507,13 @@ __global__ void __maxnreg__(64)
                                 key[c] = m;
                                 float lo;
                                 lo = fminf(m0, m); m = fmaxf(m0, m); m0 = lo;
-                                lo = fminf(m1, m); m = fmaxf(m1, m); m1 = lo;
-                                lo = fminf(m2, m); m = fmaxf(m2, m); m2 = lo;
-                                m3 = fminf(m3, m);
+                                if (kListDepth == 4) {
+                                    lo = fminf(m1, m); m = fmaxf(m1, m); m1 = lo;
+                                    lo = fminf(m2, m); m = fmaxf(m2, m); m2 = lo;
+                                    m3 = fminf(m3, m);
+                                } else {
+                                    m1 = fminf(m1, m);
+                                }
                             }
                         }
                         float* krow = &w.key[pr * NC];
@@ -539,15 +548,23 @@ __global__ void __maxnreg__(64)
                 }
 
                 // ---- candidates: the triples whose minimum does not exceed tau0 (every point
-                // of the top-k belongs to one). Their ranks are compacted in place to the
-                // front of the key array: a slot written in row r lies in rows <= r, whose
-                // keys every lane has read before the ballot.
+                // of the top-k belongs to one), four per lane and 128 per step. Their ranks
+                // are compacted in place to the front of the key array: a slot written in
+                // block b lies in blocks <= b, whose keys every lane has read before the
+                // ballot.
                 int n_cand = 0;
-                for (int r = 0; r < n_rows; ++r) {
-                    const bool cand = w.key[(r << 5) + lane] <= tau0;
-                    const unsigned ball = __ballot_sync(kFull, cand);
-                    if (cand) w.key[n_cand + __popc(ball & below)] = __int_as_float((r << 5) + lane);
-                    n_cand += __popc(ball);
+                for (int b = 0; b < n_blk; ++b) {
+                    const int t0 = (b << 7) + 4 * lane;  // this lane's four triples
+                    const float4 kv = *reinterpret_cast<const float4*>(&w.key[t0]);
+                    const unsigned m = (kv.x <= tau0 ? 1u : 0u) | (kv.y <= tau0 ? 2u : 0u) |
+                                       (kv.z <= tau0 ? 4u : 0u) | (kv.w <= tau0 ? 8u : 0u);
+                    if (__ballot_sync(kFull, m != 0u) == 0u) continue;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const unsigned bj = __ballot_sync(kFull, (m >> j) & 1u);
+                        if ((m >> j) & 1u) w.key[n_cand + __popc(bj & below)] = __int_as_float(t0 + j);
+                        n_cand += __popc(bj);
+                    }
                 }
                 __syncwarp();
 
