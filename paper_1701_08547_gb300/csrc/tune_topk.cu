@@ -5,8 +5,9 @@
 // flight while the current one is filtered.
 // The warp keeps one exact top-k list (lane j = j-th best, as an
 // order-preserving unsigned image of the score plus its index) and its k-th
-// key; only when a batch of 512 scores holds values at or below that key does
-// the warp merge them, in increasing (value, index) order, into the list.
+// key; only when a batch of 512 scores holds values at or below that key (one
+// minimum per lane tells) does the warp merge them, a float4 group at a time and in
+// increasing (value, index) order, into the list.
 #include <stdint.h>
 
 #include "tune_internal.h"
@@ -69,8 +70,8 @@ __device__ __forceinline__ float filter_bound(unsigned tau_k)
     return t < __int_as_float(0x7f800000) ? t : __int_as_float(0x7f7fffff);
 }
 
-// Merges the candidates of one batch (bit j of cm marks v[j]; index of v[j] is
-// idx0 + stride_of(j)) into the warp list in increasing (key, index) order, until
+// Merges the candidates of one group (bit j of cm marks v[j]; index_of(j) is its
+// index in the segment) into the warp list in increasing (key, index) order, until
 // the smallest remaining candidate can no longer enter.
 template <int N, typename IndexOf>
 __device__ __forceinline__ void merge_batch(const float (&v)[N], unsigned cm, IndexOf index_of, unsigned& lk,
@@ -81,7 +82,7 @@ __device__ __forceinline__ void merge_batch(const float (&v)[N], unsigned cm, In
         int hq = 0;
 #pragma unroll
         for (int q = N - 1; q >= 0; --q) {  // equal keys: the lower q (lower index) wins
-            const unsigned kq = order_key(v[q]);
+            const unsigned kq = order_key(v[q] + 0.0f);  // -0 ranks as +0
             if (((cm >> q) & 1u) && kq <= hk) {
                 hk = kq;
                 hq = q;
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(kThreads)
         {
             const int j = lane < head ? lane : tail0 + (lane - head);
             float v[1];
-            v[0] = (lane < head || j < len) ? __ldcs(seg + j) + 0.0f : kNaN;  // -0 -> +0; NaN pads
+            v[0] = (lane < head || j < len) ? __ldcs(seg + j) : kNaN;  // NaN pads
             const unsigned cm = v[0] <= filter_bound(tau_k) ? 1u : 0u;
             if (__ballot_sync(kFull, cm != 0u))
                 merge_batch<1>(v, cm, [&](int) { return j; }, lk, li, tau_k, tau_i, k, lane);
@@ -156,20 +157,29 @@ __global__ void __launch_bounds__(kThreads)
             float v[4 * kVec];
 #pragma unroll
             for (int q = 0; q < kVec; ++q) {
-                v[4 * q + 0] = cur[q].x + 0.0f;
-                v[4 * q + 1] = cur[q].y + 0.0f;
-                v[4 * q + 2] = cur[q].z + 0.0f;
-                v[4 * q + 3] = cur[q].w + 0.0f;
+                v[4 * q + 0] = cur[q].x;
+                v[4 * q + 1] = cur[q].y;
+                v[4 * q + 2] = cur[q].z;
+                v[4 * q + 3] = cur[q].w;
             }
-            const float tb = filter_bound(tau_k);
-            unsigned cm = 0;
+            // fast path: the lane's smallest score (fminf skips NaN) against the bound
+            float mn = v[0];
 #pragma unroll
-            for (int j = 0; j < 4 * kVec; ++j)
-                if (v[j] <= tb) cm |= 1u << j;
-            if (__ballot_sync(kFull, cm != 0u)) {
+            for (int j = 1; j < 4 * kVec; ++j) mn = fminf(mn, v[j]);
+            const float tb = filter_bound(tau_k);
+            if (__ballot_sync(kFull, mn <= tb) != 0u) {
+                // merge one float4 group at a time (four values per lane), lowest indices first
                 const int i0 = head + 4 * (f0 + lane);
-                merge_batch<4 * kVec>(v, cm, [&](int j) { return i0 + 128 * (j >> 2) + (j & 3); }, lk, li, tau_k,
-                                      tau_i, k, lane);
+#pragma unroll
+                for (int q = 0; q < kVec; ++q) {
+                    const float g[4] = {v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]};
+                    const float t = filter_bound(tau_k);
+                    const unsigned cm = (g[0] <= t ? 1u : 0u) | (g[1] <= t ? 2u : 0u) | (g[2] <= t ? 4u : 0u) |
+                                        (g[3] <= t ? 8u : 0u);
+                    if (__ballot_sync(kFull, cm != 0u) == 0u) continue;
+                    const int iq = i0 + 128 * q;
+                    merge_batch<4>(g, cm, [&](int j) { return iq + j; }, lk, li, tau_k, tau_i, k, lane);
+                }
             }
 #pragma unroll
             for (int q = 0; q < kVec; ++q) cur[q] = nxt[q];
