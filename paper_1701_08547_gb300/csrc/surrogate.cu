@@ -75,101 +75,159 @@ T* carve(char*& p, size_t count)
 
 // ---- small kernels ------------------------------------------------------------
 
-// y[mem][i] = sum_j w5[j] * H4[mem][i][j] + b5   (one warp per row)
+// y[mem][i] = sum_j w5[j] * H4[mem][i][j] + b5   (one warp per row, eight columns per lane)
 __global__ void head_fwd(const __nv_bfloat16* __restrict__ H4, const float* __restrict__ master, float* y,
                          int n, int batch)
 {
     const int mem = blockIdx.y;
     const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (row >= n) return;
-    const float* w5 = master + mem * P + OFF_W5;
-    const __nv_bfloat16* h = H4 + (long long)mem * batch * WID + (long long)row * WID;
+    const float* w5 = master + mem * P + OFF_W5 + 8 * lane;
+    const uint4 hv = reinterpret_cast<const uint4*>(H4 + (long long)mem * batch * WID + (long long)row * WID)[lane];
+    const float4 wa = *reinterpret_cast<const float4*>(w5), wb = *reinterpret_cast<const float4*>(w5 + 4);
+    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&hv);
+    const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
     float s = 0.0f;
-    for (int j = lane; j < WID; j += 32) s = fmaf(w5[j], __bfloat162float(h[j]), s);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 f = __bfloat1622float2(h2[q]);
+        s = fmaf(w[2 * q], f.x, s);
+        s = fmaf(w[2 * q + 1], f.y, s);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) y[(long long)mem * batch + row] = s + master[mem * P + OFF_B5];
 }
 
-// dy = 2 (y - t) / n; loss[mem] = mean (y - t)^2 (one block per member, deterministic)
-__global__ void loss_grad(const float* __restrict__ y, const float* __restrict__ t, float* dy, float* loss, int n,
+// dy = 2 (y - t) / n, one row per thread; lpart[mem][block] = the block's sum of (y - t)^2
+__global__ void loss_grad(const float* __restrict__ y, const float* __restrict__ t, float* dy, float* lpart, int n,
                           int batch)
 {
-    const int mem = blockIdx.x;
-    __shared__ float red[256];
+    const int mem = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ float red[8];
     float s = 0.0f;
-    for (int i = threadIdx.x; i < batch; i += blockDim.x) {
+    if (i < batch) {
         float g = 0.0f;
         if (i < n) {
             const float e = y[(long long)mem * batch + i] - t[i];
-            s += e * e;
+            s = e * e;
             g = 2.0f * e / (float)n;
         }
         dy[(long long)mem * batch + i] = g;
     }
-    red[threadIdx.x] = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.0f;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) b += red[q];
+        lpart[mem * gridDim.x + blockIdx.x] = b;
     }
-    if (threadIdx.x == 0 && loss) loss[mem] = red[0] / (float)n;
 }
 
-// dZ4[i][j] = bf16(dy[i] * w5[j] * gelu'(Z4[i][j]))
+// loss[mem] = (sum of the blocks' partial sums, in block order) / n
+__global__ void loss_reduce(const float* __restrict__ lpart, float* loss, int blocks, int n)
+{
+    const int mem = blockIdx.x;
+    if (threadIdx.x != 0 || !loss) return;
+    float s = 0.0f;
+    for (int b = 0; b < blocks; ++b) s += lpart[mem * blocks + b];
+    loss[mem] = s / (float)n;
+}
+
+// dZ4[i][j] = bf16(dy[i] * w5[j] * gelu'(Z4[i][j])), eight columns per thread
 __global__ void head_bwd_act(const float* __restrict__ dy, const float* __restrict__ master,
                              const float* __restrict__ Z4, __nv_bfloat16* dZ, int batch)
 {
     const int mem = blockIdx.y;
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long e = 8 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
     if (e >= (long long)batch * WID) return;
     const int i = (int)(e / WID), j = (int)(e % WID);
     const long long o = (long long)mem * batch * WID + e;
-    dZ[o] = __float2bfloat16_rn(dy[(long long)mem * batch + i] * master[mem * P + OFF_W5 + j] *
-                                mlp::gelu_grad(Z4[o]));
+    const float d = dy[(long long)mem * batch + i];
+    const float* w5 = master + mem * P + OFF_W5 + j;
+    const float4 za = *reinterpret_cast<const float4*>(Z4 + o), zb = *reinterpret_cast<const float4*>(Z4 + o + 4);
+    const float4 wa = *reinterpret_cast<const float4*>(w5), wb = *reinterpret_cast<const float4*>(w5 + 4);
+    const float z[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+    const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+    uint32_t out[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(d * w[2 * q] * mlp::gelu_grad(z[2 * q]),
+                                                        d * w[2 * q + 1] * mlp::gelu_grad(z[2 * q + 1]));
+        out[q] = *reinterpret_cast<const uint32_t*>(&b2);
+    }
+    *reinterpret_cast<uint4*>(dZ + o) = make_uint4(out[0], out[1], out[2], out[3]);
 }
 
 // Column sums over rows in two stages (deterministic): stage 1 sums slices of
 // kRowSlice rows into part[mem][slice][WID + 1]; stage 2 adds the slices.
-constexpr int kRowSlice = 256;
+constexpr int kRowSlice = 64;
 
-// part[.][.][j] = sum over the slice of dy[i] H4[i][j] (j < 256) and of dy[i] (j = 256)
+// part[.][.][j] = sum over the slice of dy[i] H4[i][j] (j < 256) and of dy[i] (j = 256);
+// four independent partial sums (rows i mod 4), added at the end
 __global__ void head_bwd_partial(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ H4, float* part,
                                  int rows, int batch, int slices)
 {
     const int mem = blockIdx.y, sl = blockIdx.x, j = threadIdx.x;
     const float* d = dy + (long long)mem * batch;
     const __nv_bfloat16* h = H4 + (long long)mem * batch * WID;
-    float s = 0.0f, sb = 0.0f;
-    const int i1 = min(rows, (sl + 1) * kRowSlice);
-    for (int i = sl * kRowSlice; i < i1; ++i) {
-        s = fmaf(d[i], __bfloat162float(h[(long long)i * WID + j]), s);
-        sb += d[i];
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int i0 = sl * kRowSlice, i1 = min(rows, i0 + kRowSlice);
+    int i = i0;
+    for (; i + 4 <= i1; i += 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            s[q] = fmaf(d[i + q], __bfloat162float(h[(long long)(i + q) * WID + j]), s[q]);
+            sb[q] += d[i + q];
+        }
+    }
+    for (; i < i1; ++i) {
+        s[0] = fmaf(d[i], __bfloat162float(h[(long long)i * WID + j]), s[0]);
+        sb[0] += d[i];
     }
     float* o = part + ((long long)mem * slices + sl) * (WID + 1);
-    o[j] = s;
-    if (j == 0) o[WID] = sb;
+    o[j] = (s[0] + s[1]) + (s[2] + s[3]);
+    if (j == 0) o[WID] = (sb[0] + sb[1]) + (sb[2] + sb[3]);
 }
 
-// part[.][.][j] = sum over the slice of dZ[i][j]
+// part[.][.][j] = sum over the slice of dZ[i][j] (four independent partial sums)
 __global__ void bias_partial(const __nv_bfloat16* __restrict__ dZ, float* part, int rows, int batch, int slices)
 {
     const int mem = blockIdx.y, sl = blockIdx.x, j = threadIdx.x;
     const __nv_bfloat16* d = dZ + (long long)mem * batch * WID;
-    float s = 0.0f;
-    const int i1 = min(rows, (sl + 1) * kRowSlice);
-    for (int i = sl * kRowSlice; i < i1; ++i) s += __bfloat162float(d[(long long)i * WID + j]);
-    part[((long long)mem * slices + sl) * (WID + 1) + j] = s;
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int i0 = sl * kRowSlice, i1 = min(rows, i0 + kRowSlice);
+    int i = i0;
+    for (; i + 4 <= i1; i += 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[q] += __bfloat162float(d[(long long)(i + q) * WID + j]);
+    }
+    for (; i < i1; ++i) s[0] += __bfloat162float(d[(long long)i * WID + j]);
+    part[((long long)mem * slices + sl) * (WID + 1) + j] = (s[0] + s[1]) + (s[2] + s[3]);
 }
 
-// grad[mem * P + off + j] = sum over slices of part[mem][slice][j], j < cols
+// grad[mem * P + off + j] = sum over slices of part[mem][slice][j], j < cols. Block =
+// 32 columns x 8 warps; warp w adds slices w, w + 8, ... in order, then the eight
+// partial sums are added in warp order (deterministic).
 __global__ void slices_reduce(const float* __restrict__ part, float* grad, long long off, int cols, int slices)
 {
-    const int mem = blockIdx.x, j = threadIdx.x;
-    if (j >= cols) return;
+    const int mem = blockIdx.y, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + (threadIdx.x & 31);
+    __shared__ float red[8][32];
     float s = 0.0f;
-    for (int q = 0; q < slices; ++q) s += part[((long long)mem * slices + q) * (WID + 1) + j];
-    grad[mem * P + off + j] = s;
+    if (j < cols)
+        for (int q = w; q < slices; q += 8) s += part[((long long)mem * slices + q) * (WID + 1) + j];
+    red[w][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (w == 0 && j < cols) {
+        float t = red[0][threadIdx.x];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) t += red[q][threadIdx.x];
+        grad[mem * P + off + j] = t;
+    }
 }
 
 // grad W[o][i] = sum over splits of part[split][o][i]
@@ -480,11 +538,13 @@ int forward(tune_surrogate* h, int n_pad, cudaStream_t s, const __nv_bfloat16* x
 int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
 {
     const int B = h->batch;
-    loss_grad<<<h->members, 256, 0, s>>>(h->y, h->lbl, h->dy, h->loss, n, B);
+    const int lblocks = (B + 255) / 256;
+    loss_grad<<<dim3(lblocks, h->members), 256, 0, s>>>(h->y, h->lbl, h->dy, h->part, n, B);
+    loss_reduce<<<h->members, 32, 0, s>>>(h->part, h->loss, lblocks, n);
     const int slices = (n_pad + kRowSlice - 1) / kRowSlice;
     head_bwd_partial<<<dim3(slices, h->members), WID, 0, s>>>(h->dy, h->H[NL - 1], h->part, n_pad, B, slices);
-    slices_reduce<<<h->members, WID + 32, 0, s>>>(h->part, h->grad, OFF_W5, WID + 1, slices);
-    head_bwd_act<<<dim3((unsigned)(((long long)B * WID + 255) / 256), h->members), 256, 0, s>>>(
+    slices_reduce<<<dim3((WID + 1 + 31) / 32, h->members), 256, 0, s>>>(h->part, h->grad, OFF_W5, WID + 1, slices);
+    head_bwd_act<<<dim3((unsigned)(((long long)B * WID / 8 + 255) / 256), h->members), 256, 0, s>>>(
         h->dy, h->master, h->Z[NL - 1], h->dZ[0], B);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: head backward launch");
     int cur = 0;
@@ -515,7 +575,7 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
         split_reduce<<<dim3((WID * kin + 255) / 256, h->members), 256, 0, s>>>(h->part, h->grad, OFF_W(l), kin,
                                                                                splits);
         bias_partial<<<dim3(slices, h->members), WID, 0, s>>>(dz, h->part, n_pad, B, slices);
-        slices_reduce<<<h->members, WID, 0, s>>>(h->part, h->grad, OFF_B(l), WID, slices);
+        slices_reduce<<<dim3(WID / 32, h->members), 256, 0, s>>>(h->part, h->grad, OFF_B(l), WID, slices);
         TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: reduce launch");
         if (l == 0) break;
         // input gradient of layer l, times gelu' of layer l-1: dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1})
