@@ -609,6 +609,24 @@ __global__ void __maxnreg__(64)
                     };
                     if (has) advance();
                     const bool relaxed = !ct.order_safe || __any_sync(kFull, has && !(X >= 0x1p-100f));
+                    if (!relaxed) {
+                        // every lane's walk is in (cost, index) order: the r-th extraction is the
+                        // r-th best of the batch (points above tau0 cannot be among the top k)
+                        for (int r = 0; r < k; ++r) {
+                            const unsigned mc = __reduce_min_sync(kFull, __float_as_uint(hc));
+                            const float mcf = __uint_as_float(mc);
+                            if (mc >= 0x7f800000u || mcf > tau0) break;
+                            const unsigned mi = __reduce_min_sync(kFull, hc == mcf ? (unsigned)hi : 0xffffffffu);
+                            if (lane == r) {
+                                lc = mcf;
+                                li = (int)mi;
+                            }
+                            if (hc == mcf && hi == (int)mi) advance();
+                        }
+                        tau_c = __shfl_sync(kFull, lc, k - 1);
+                        tau_i = __shfl_sync(kFull, li, k - 1);
+                        continue;
+                    }
                     int cnt = 0;  // list entries so far; (prev_c, prev_i) is the largest
                     float prev_c = 0.0f;
                     int prev_i = -1;
