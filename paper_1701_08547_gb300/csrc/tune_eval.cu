@@ -263,7 +263,7 @@ __device__ __forceinline__ void warp_list_insert(float& lc, int& li, float& tau_
     tau_i = __shfl_sync(kFull, li, k - 1);
 }
 
-template <bool EMIT>
+template <bool EMIT, bool MULTI>
 __global__ void __maxnreg__(64)
     tune_eval_kernel(const __grid_constant__ EvalParams p, const int4* __restrict__ descs,
                      int32_t* __restrict__ topk_idx, float* __restrict__ topk_cost,
@@ -273,12 +273,14 @@ __global__ void __maxnreg__(64)
 {
     __shared__ CtaTables ct;
     __shared__ WarpTables wts[kWarps];
-    // blockIdx.y selects the architecture row; its results and work queue follow those of
-    // the rows before it
-    const tune_arch& a = p.a[blockIdx.y];
-    topk_idx += (int64_t)blockIdx.y * p.n_kernels * p.k;
-    topk_cost += (int64_t)blockIdx.y * p.n_kernels * p.k;
-    queue += blockIdx.y;
+    // with several architecture rows, blockIdx.y selects the row; its results and work queue
+    // follow those of the rows before it (one row: the row's fields are kernel constants)
+    const tune_arch& a = p.a[MULTI ? blockIdx.y : 0];
+    if (MULTI) {
+        topk_idx += (int64_t)blockIdx.y * p.n_kernels * p.k;
+        topk_cost += (int64_t)blockIdx.y * p.n_kernels * p.k;
+        queue += blockIdx.y;
+    }
     build_cta_tables(p, a, ct);
     __syncthreads();
 
@@ -498,13 +500,18 @@ __global__ void __maxnreg__(64)
                         float key[NC];
 #pragma unroll
                         for (int c = 0; c < NC; ++c) {
-                            key[c] = __int_as_float(0x7fc00000);  // no point (NaN): never a candidate
+                            // branch-free: a triple without a valid configuration (B* = 0) is
+                            // priced with B* = 1, then keyed NaN (never a candidate) and ranked
+                            // +inf (no effect on the bound)
                             const int B = min(gwr, gs[c]);
-                            if (B > 0) {
-                                const float X = __fmul_rn(__fmaf_rn(cmv, ct.hide[B * wb], cnm), ln);
-                                // NaN (from infinite counts) is ranked as +inf
-                                float m = fminf(__fmul_rn(X, w.iparmin[B - 1]), kInf);
-                                key[c] = m;
+                            const int Bv = max(B, 1);
+                            // (W* <= kMaxW for a valid triple; the clamp only keeps the B* = 0 lookup in range)
+                            const float X = __fmul_rn(__fmaf_rn(cmv, ct.hide[min(Bv * wb, kMaxW)], cnm), ln);
+                            // NaN (from infinite counts) is ranked as +inf
+                            float m = fminf(__fmul_rn(X, w.iparmin[Bv - 1]), kInf);
+                            key[c] = B > 0 ? m : __int_as_float(0x7fc00000);
+                            m = B > 0 ? m : kInf;
+                            {
                                 float lo;
                                 lo = fminf(m0, m); m = fmaxf(m0, m); m0 = lo;
                                 if (kListDepth == 4) {
@@ -596,6 +603,17 @@ __global__ void __maxnreg__(64)
                     float hc = kInf;
                     int hi = 0x7fffffff;
                     auto advance = [&]() {
+                        if (g_dense) {  // every axis grid size present: rank = position
+                            if (rg < x.n_g) {
+                                const int g = ct.perm[B - 1][rg++];
+                                hc = __fmul_rn(X, ct.ipar[B - 1][g]);
+                                hi = base + g * nUC;
+                            } else {
+                                hc = kInf;
+                                hi = 0x7fffffff;
+                            }
+                            return;
+                        }
                         hc = kInf;
                         hi = 0x7fffffff;
                         while (rg < x.n_g) {
@@ -960,11 +978,11 @@ int launch_thread(const EvalParams& p, const tune_kernel_desc* descs, int32_t* t
     return TUNE_OK;
 }
 
-template <bool EMIT>
-int launch(const EvalParams& p, const tune_kernel_desc* descs, int32_t* ti, float* tc, int32_t* pb,
-           int32_t* pw, float* pc, const int64_t* po, int* status, cudaStream_t s, int ctas_per_sm = 0)
+template <bool EMIT, bool MULTI>
+int launch_rows(const EvalParams& p, const tune_kernel_desc* descs, int32_t* ti, float* tc, int32_t* pb,
+                int32_t* pw, float* pc, const int64_t* po, int* status, cudaStream_t s, int ctas_per_sm)
 {
-    auto kern = tune_eval_kernel<EMIT>;
+    auto kern = tune_eval_kernel<EMIT, MULTI>;
     static int per_sm = 0;
     if (per_sm == 0) {
         TUNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0),
@@ -984,6 +1002,14 @@ int launch(const EvalParams& p, const tune_kernel_desc* descs, int32_t* ti, floa
                                                   status, queue);
     TUNE_CUDA_TRY(cudaGetLastError(), "tune_eval: kernel launch");
     return TUNE_OK;
+}
+
+template <bool EMIT>
+int launch(const EvalParams& p, const tune_kernel_desc* descs, int32_t* ti, float* tc, int32_t* pb,
+           int32_t* pw, float* pc, const int64_t* po, int* status, cudaStream_t s, int ctas_per_sm = 0)
+{
+    return p.n_arch > 1 ? launch_rows<EMIT, true>(p, descs, ti, tc, pb, pw, pc, po, status, s, ctas_per_sm)
+                        : launch_rows<EMIT, false>(p, descs, ti, tc, pb, pw, pc, po, status, s, ctas_per_sm);
 }
 
 int validate(const tune_arch* a, const tune_axes* x, int32_t k)
