@@ -546,12 +546,11 @@ __global__ void __maxnreg__(64)
                     tau0 = __uint_as_float(mb);
                     if (mb >= 0x7f800000u) break;
                     const unsigned who = __ballot_sync(kFull, __float_as_uint(m0) == mb);
-                    if (lane == __ffs(who) - 1) {
-                        m0 = m1;
-                        m1 = m2;
-                        m2 = m3;
-                        m3 = kInf;
-                    }
+                    const bool me = lane == __ffs(who) - 1;  // the lane whose smallest was taken
+                    m0 = me ? m1 : m0;
+                    m1 = me ? m2 : m1;
+                    m2 = me ? m3 : m2;
+                    m3 = me ? kInf : m3;
                 }
 
                 // ---- candidates: the triples whose minimum does not exceed tau0 (every point
@@ -635,11 +634,22 @@ __global__ void __maxnreg__(64)
                             const float mcf = __uint_as_float(mc);
                             if (mc >= 0x7f800000u || mcf > tau0) break;
                             const unsigned mi = __reduce_min_sync(kFull, hc == mcf ? (unsigned)hi : 0xffffffffu);
-                            if (lane == r) {
-                                lc = mcf;
-                                li = (int)mi;
+                            lc = lane == r ? mcf : lc;
+                            li = lane == r ? (int)mi : li;
+                            const bool win = hc == mcf && hi == (int)mi;
+                            if (g_dense) {
+                                // straight-line advance of the winning lane (every lane computes; B
+                                // and the position are clamped into range for the others)
+                                const int Bv = max(B, 1) - 1;
+                                const int g = ct.perm[Bv][min(rg, x.n_g - 1)];
+                                const float nh = __fmul_rn(X, ct.ipar[Bv][g]);
+                                const bool more = rg < x.n_g;
+                                hc = win ? (more ? nh : kInf) : hc;
+                                hi = win ? (more ? base + g * nUC : 0x7fffffff) : hi;
+                                rg += win ? 1 : 0;
+                            } else if (win) {
+                                advance();
                             }
-                            if (hc == mcf && hi == (int)mi) advance();
                         }
                         tau_c = __shfl_sync(kFull, lc, k - 1);
                         tau_i = __shfl_sync(kFull, li, k - 1);
