@@ -38,12 +38,16 @@ WORKLOADS = {
     "uneven": (1_000_000, "uneven", 5, 3),
     "topk": (100_000, None, 10, 11),
     "surfwd": (1 << 20, None, 0, 12),
+    "search": (100_000, "dense", 1, 2),
 }
 ISSUE_LANES_PER_SM_CLK = 4 * 32  # 4 schedulers x 32 lanes per SM and clock
 # The hot-path scope table's per-point figure for a per-point evaluation after the
 # per-kernel hoists (decode ~3, 2 IMNMX, 1 IMAD, 2 table loads, 1 FFMA + 2 FMUL, 1
 # compare); reported beside the headline for reference.
 SURVEY_INSTR_PER_POINT = 12
+# The scope table's unhoisted per-point figure: one evaluation of a search prices a
+# point from scratch (occupancy limits, cost sums, launch-shape terms).
+UNHOISTED_INSTR_PER_POINT = 60
 L2_FLUSH_BYTES = 256 << 20       # larger than the 126.5 MB L2
 
 
@@ -465,6 +469,73 @@ def run_surfwd(args):
             "paths": out}
 
 
+def run_search(args):
+    """Random and Nelder-Mead search per kernel with the static cost as the objective, over
+    the full space and over the statically pruned one (T*): kernels searched per second and
+    how often the search finds the exhaustive optimum (tune_eval's top-1)."""
+    import torch
+
+    import paper_1701_08547_gb300 as T
+    from paper_1701_08547_gb300 import build as B
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    n, space, _, seed = WORKLOADS["search"]
+    n = args.kernels or n
+    a, ax = archs.arch("sm_103"), gen.axes()
+    descs = gen.descriptors(n, seed, space)
+    d_dev = T.descs_to_device(descs, dev)
+    budget = args.budget
+    ws = T.workspace(0, n, 1, dev)
+    opt_i, opt_c = T.tune_eval(a, ax, d_dev, 1, workspace_buf=ws)
+    keep = T.tune_suggest(a, ax, d_dev)["t_star"]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    peaks, kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * ISSUE_LANES_PER_SM_CLK * peaks["sm_max_mhz"] * 1e6 / 1e12
+    out = {}
+    for method in ("random", "nelder_mead"):
+        for pruned in (False, True):
+            kt = keep if pruned else None
+            for _ in range(args.warmup):
+                T.tune_search(a, ax, d_dev, method, budget, 1, t_keep=kt, workspace_buf=ws)
+            torch.cuda.synchronize()
+            times, evals = [], 0
+            for i in range(args.steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                bi, bc, ev = T.tune_search(a, ax, d_dev, method, budget, 100 + i, t_keep=kt, workspace_buf=ws)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+                evals = int(ev.sum().item())
+            T.tune_check(ws)
+            ms = sum(times) / len(times)
+            valid = torch.isfinite(opt_c[:, 0])
+            hit = float(((bi == opt_i[:, 0]) & valid).sum().item() / max(1, int(valid.sum().item())))
+            ratio = (bc / opt_c[:, 0])[valid & torch.isfinite(bc)]
+            achieved = UNHOISTED_INSTR_PER_POINT * evals / (ms * 1e-3) / 1e12
+            out[f"{method}{'_pruned' if pruned else ''}"] = {
+                "ms": ms, "kernels_per_s": n / (ms * 1e-3), "evaluations_per_s": evals / (ms * 1e-3),
+                "evals_per_kernel": evals / n, "hit_exhaustive_top1": hit,
+                "median_cost_ratio": float(ratio.median().item()) if ratio.numel() else None,
+                "p90_cost_ratio": float(ratio.quantile(0.9).item()) if ratio.numel() else None,
+                "frac_issue_at_60_per_eval": achieved / peak}
+    head = out["nelder_mead"]
+    return {"metric": "kernels searched/sec (Nelder-Mead, static cost objective)", "value": head["kernels_per_s"],
+            "unit": "kernels/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32",
+            "data": "synthetic",
+            "config": {"workload": f"search: {n} dense kernels x 16384 points, budget {budget} evaluations per kernel",
+                       "l2": "flushed between timed steps"},
+            "roofline": {"bound": "alu", "achieved": UNHOISTED_INSTR_PER_POINT * head["evaluations_per_s"] / 1e12,
+                         "peak": peak, "unit": "Tinstr/s", "frac": head["frac_issue_at_60_per_eval"],
+                         "traffic": None, "instr_per_point": UNHOISTED_INSTR_PER_POINT,
+                         "peak_source": f"{sms} SMs x 128 lanes x {peaks['sm_max_mhz']} MHz ({kind})"},
+            "methods": out, "gpu_launches": args.steps}
+
+
 def run_topk(args):
     """Segmented top-k over external scores: 100,000 segments x 16,384 float32
     scores (the dense workload's point count), top-10; HBM-bound."""
@@ -598,6 +669,7 @@ def main():
     p.add_argument("--sur-infer-kernels", type=int, default=500, help="dense kernels scored by the ensemble")
     p.add_argument("--sur-eval", type=int, default=150, help="held-out kernels with fully timed spaces")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--budget", type=int, default=128, help="search workload: evaluations per kernel")
     args = p.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -607,6 +679,8 @@ def main():
         line = run_topk(args)
     elif args.workload == "surfwd":
         line = run_surfwd(args)
+    elif args.workload == "search":
+        line = run_search(args)
     else:
         line = run_ours(args)
     if line is not None:

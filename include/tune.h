@@ -357,6 +357,50 @@ int tune_suggest(const tune_arch* arch, const tune_axes* axes, const tune_kernel
                  int32_t* s_star, uint32_t* t_rule, void* workspace, size_t ws_bytes,
                  tune_stream_t stream);
 
+/*
+ * tune_search — random or Nelder-Mead simplex search over each kernel's tuning
+ * space, with the static model's cost as the objective. The paper's autotuner
+ * explores the space left after static pruning with one of its search methods
+ * (Section III-C lists its methods; Section IV-C: exhaustive, or random or
+ * Nelder-Mead simplex to bound the tuning time); with the model as the
+ * objective no variant is run.
+ *   method   TUNE_SEARCH_RANDOM or TUNE_SEARCH_NELDER_MEAD
+ *   budget   objective evaluations per kernel, 1..2^20
+ *   seed     random draws: draw j of kernel i is the SplitMix64 output of the state
+ *            mix64(seed) + (i 2^32 + j + 1) 0x9E3779B97F4A7C15, mapped to [0, n) as
+ *            ((x >> 32) n) >> 32
+ *   t_keep   device uint32[n_kernels] or NULL: thread-count positions to search
+ *            (e.g. tune_suggest's t_star or t_rule), intersected with the kernel's
+ *            mask; NULL searches the whole space
+ * A point is a rank vector over the searched lists (thread counts, grid sizes,
+ * unroll factors, carveouts); its objective is the FP32 cost of the point as
+ * tune_eval computes it (+inf without a valid configuration), points ordered by
+ * (cost, canonical index in the kernel's full space).
+ *   random: evaluation j draws rank d from draw 4 j + d.
+ *   Nelder-Mead: five vertices in fixed point (8 fractional bits), rounded to the
+ *   nearest rank (floor of v + 1/2) and clamped; start x0 from draws 0..3, vertex
+ *   d + 1 = x0 moved max(1, n_d / 4) ranks along axis d (backwards where forwards
+ *   leaves the list); vertices ordered by (cost, index, vertex number); centroid c
+ *   of the best four (sum >> 2); reflection 2c - w; if it beats the best,
+ *   expansion 3c - 2w (the better of the two replaces w); else if it beats the
+ *   second worst it replaces w; else contraction c + ((r - c) >> 1) if the
+ *   reflection r beats w, else c + ((w - c) >> 1), replacing w if it beats the
+ *   better of r and w (resp. w); else every vertex moves halfway to the best
+ *   (v = b + ((v - b) >> 1)) and is evaluated. Every evaluation counts; the
+ *   search stops when the budget is spent or a shrink leaves all vertices on one
+ *   point.
+ * Outputs (device, [n_kernels]): best_idx (canonical index of the best point seen,
+ * -1 if no evaluated point has a valid configuration), best_cost (+inf then),
+ * evals (evaluations made). Asynchronous on
+ * `stream`; workspace: the 256-byte header (status word; malformed descriptors set
+ * TUNE_EINVAL, read with tune_check).
+ */
+#define TUNE_SEARCH_RANDOM 1
+#define TUNE_SEARCH_NELDER_MEAD 2
+int tune_search(const tune_arch* arch, const tune_axes* axes, const tune_kernel_desc* descs, int64_t n_kernels,
+                int32_t method, int32_t budget, uint64_t seed, const uint32_t* t_keep, int32_t* best_idx,
+                float* best_cost, int32_t* evals, void* workspace, size_t ws_bytes, tune_stream_t stream);
+
 /* Bytes of device workspace the call needs (at least 256). */
 size_t tune_workspace_bytes(int call, int64_t n, int32_t k);
 

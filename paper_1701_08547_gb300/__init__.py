@@ -12,7 +12,7 @@ from . import native
 from .native import (TUNE_EMIT_POINTS, TUNE_SCHED_CHUNK, TUNE_SCHED_CTAS,  # noqa: F401
                      TUNE_SCHED_THREAD, TUNE_SCHED_WARP, TuneError)
 
-__all__ = ["tune_eval", "tune_eval_archs", "tune_topk", "tune_autotune", "tune_features", "tune_suggest", "tune_workspace_bytes", "tune_check",
+__all__ = ["tune_eval", "tune_eval_archs", "tune_topk", "tune_autotune", "tune_features", "tune_suggest", "tune_search", "tune_workspace_bytes", "tune_check",
            "descs_to_device", "TUNE_EMIT_POINTS", "TUNE_SCHED_WARP", "TUNE_SCHED_THREAD",
            "TUNE_SCHED_CHUNK", "TUNE_SCHED_CTAS", "TuneError"]
 
@@ -182,6 +182,29 @@ def tune_suggest(arch, axes, descs, workspace_buf=None, stream=None):
                         workspace_buf.numel(), _stream(stream))
     native.check(rc)
     return out
+
+
+def tune_search(arch, axes, descs, method, budget, seed, t_keep=None, workspace_buf=None, stream=None):
+    """Random (method "random") or Nelder-Mead ("nelder_mead") search per kernel with the
+    static cost as the objective; t_keep: optional device uint32 mask per kernel of the
+    thread-count positions to search. Returns (best_idx, best_cost, evals) device tensors."""
+    torch = _torch()
+    L = native.load()
+    m = {"random": native.TUNE_SEARCH_RANDOM, "nelder_mead": native.TUNE_SEARCH_NELDER_MEAD}[method]
+    n = descs.numel() * descs.element_size() // 64
+    dev = descs.device
+    best_idx = torch.empty(n, dtype=torch.int32, device=dev)
+    best_cost = torch.empty(n, dtype=torch.float32, device=dev)
+    evals = torch.empty(n, dtype=torch.int32, device=dev)
+    if workspace_buf is None:
+        workspace_buf = workspace(native.TUNE_CALL_EVAL, 0, 1, dev)
+    a = native.make_arch(arch)
+    x = native.make_axes(axes)
+    rc = L.tune_search(C.byref(a), C.byref(x), _ptr(descs), n, int(m), int(budget), int(seed) & (2 ** 64 - 1),
+                       _ptr(t_keep) if t_keep is not None else None, _ptr(best_idx), _ptr(best_cost), _ptr(evals),
+                       _ptr(workspace_buf), workspace_buf.numel(), _stream(stream))
+    native.check(rc)
+    return best_idx, best_cost, evals
 
 
 def tune_check(workspace_buf, stream=None):

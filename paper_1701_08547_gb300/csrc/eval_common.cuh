@@ -123,5 +123,42 @@ __device__ __forceinline__ bool desc_bad(const Desc& k, const tune_axes& x)
     return bad;
 }
 
+// Occupancy (Eqs. 1-5) and FP32 cost (Eq. 6 with the launch-shape terms, in the
+// library's fixed operation order) of one point (T, G, U, C): B* and W* are returned,
+// the cost is +inf where B* = 0. The same arithmetic as the evaluation kernels' tables.
+__device__ __forceinline__ float point_cost(const tune_arch& a, const Desc& kd, int T, int G, int U, int C, int& B,
+                                            int& W)
+{
+    const int R = kd.r0 + 4 * (U - 1);
+    const int wb = ceil_div(T, 32);
+    const int gw = T <= a.max_threads_block ? min(a.max_blocks_sm, a.max_warps_sm / wb) : 0;
+    int gr;
+    if (R > a.regs_thread_max) {
+        gr = 0;
+    } else if (R <= 0) {
+        gr = a.max_blocks_sm;
+    } else if (a.reg_alloc_mode == 0) {
+        int warps, wbmax;
+        reg_params(a, R, warps, wbmax);
+        gr = wb > wbmax ? 0 : warps / wb;
+    } else {
+        const long long rpb = (long long)ceil_div(R * 32 * wb, a.reg_alloc_unit) * a.reg_alloc_unit;
+        gr = rpb > a.regs_block_max ? 0 : (int)(a.regs_sm / rpb);
+    }
+    B = min(gw, min(gr, smem_blocks(a, kd.s0, C)));
+    W = B * wb;
+    if (B <= 0) return __int_as_float(0x7f800000);
+    float rcp[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) rcp[c] = __fdiv_rn(1.0f, a.ipc[c]);
+    float cnm, cm;
+    unit_costs(kd.n, kd.d, U, rcp, a.work_scale, cnm, cm);
+    const float hide = fmaxf(1.0f, __fdiv_rn((float)a.w_sat, (float)W));
+    const float lane = __fdiv_rn((float)(32 * wb), (float)T);
+    const float X = __fmul_rn(__fmaf_rn(cm, hide, cnm), lane);
+    const int slots = a.n_sm * B;
+    const int waves = ceil_div(G, slots);
+    return __fmul_rn(X, __fdiv_rn((float)(waves * slots), (float)(a.n_sm * G)));
+}
 
 }  // namespace tune_dev

@@ -6,8 +6,6 @@
 #include <stdint.h>
 #include <string.h>
 
-#include <vector>
-
 #include "features.cuh"
 #include "tune_internal.h"
 
@@ -58,31 +56,45 @@ __global__ void features_samples(const __grid_constant__ tune_arch a, const __gr
     write_row(out + i * IN, f);
 }
 
-// Features of every point of kernels [k0, k1); rows at pt_off[kid] - pt_off[k0] + p. One warp per kernel.
-__global__ void features_all(const __grid_constant__ tune_arch a, const __grid_constant__ tune_axes x,
-                             const int4* __restrict__ descs, const int64_t* __restrict__ pt_off, int64_t k0,
-                             int64_t k1, __nv_bfloat16* out, int* status)
+// Features of every point of kernels [k0, k1): one thread per point, row i of the chunk
+// = global point p0 + i (p0 = pt_off[k0]); the point's kernel is found by a binary
+// search over the offsets (the chunk's few offsets stay in L1).
+__global__ void features_points(const __grid_constant__ tune_arch a, const __grid_constant__ tune_axes x,
+                                const int4* __restrict__ descs, const int64_t* __restrict__ pt_off, int64_t k0,
+                                int64_t k1, int64_t p0, int64_t np, __nv_bfloat16* out, int* status)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t kid = k0 + (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (kid >= k1) return;
-    Desc kd;
-    load_desc(descs, kid, kd);
-    const int64_t base = pt_off[kid] - pt_off[k0];
-    const int size = (int)(pt_off[kid + 1] - pt_off[kid]);
-    const bool bad = desc_bad(kd, x);
-    if (bad && lane == 0) atomicOr(status, tune::kStatusInvalid);
-    for (int p = lane; p < size; p += 32) {
-        float f[kFeatures];
-        if (bad) {
-            for (int j = 0; j < kFeatures; ++j) f[j] = 0.0f;
-        } else {
-            int tp, gp, up, cp;
-            decode_point(kd, p, tp, gp, up, cp);
-            point_features(a, kd, x.t[tp], x.g[gp], x.u[up], x.c[cp], f);
-        }
-        write_row(out + (base + p) * IN, f);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const int64_t gp_ = p0 + i;
+    int64_t lo = k0, hi = k1;  // pt_off[lo] <= gp_ < pt_off[hi]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (pt_off[mid] <= gp_)
+            lo = mid;
+        else
+            hi = mid;
     }
+    Desc kd;
+    load_desc(descs, lo, kd);
+    const int64_t p = gp_ - pt_off[lo];
+    const int size = __popc(kd.tm) * __popc(kd.gm) * __popc(kd.um) * __popc(kd.cm);
+    float f[kFeatures];
+    if (desc_bad(kd, x) || p >= size) {
+        atomicOr(status, tune::kStatusInvalid);
+        for (int j = 0; j < kFeatures; ++j) f[j] = 0.0f;
+    } else {
+        int tp, gp, up, cp;
+        decode_point(kd, (int)p, tp, gp, up, cp);
+        point_features(a, kd, x.t[tp], x.g[gp], x.u[up], x.c[cp], f);
+    }
+    write_row(out + i * IN, f);
+}
+
+// Chunk-relative segment offsets: rel[j] = pt_off[k0 + j] - pt_off[k0], j = 0..nk.
+__global__ void rebase_offsets(const int64_t* __restrict__ pt_off, int64_t k0, int64_t nk, int64_t* rel)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j <= nk) rel[j] = pt_off[k0 + j] - pt_off[k0];
 }
 
 // Per point: runtime estimate = mean over members of exp(prediction); spread = std / mean;
@@ -217,7 +229,6 @@ extern "C" int surrogate_infer(tune_surrogate* h, const tune_arch* arch, const t
     if (rc) return rc;
     TUNE_CUDA_TRY(cudaMemcpyAsync(d_off, pt_offsets_host, (n_kernels + 1) * 8, cudaMemcpyHostToDevice, s),
                   "surrogate_infer: offsets");
-    std::vector<int64_t> rel;
     int64_t k0 = 0;
     while (k0 < n_kernels) {
         // Chunk: as many whole kernels as fit kChunkPoints (and the offsets scratch).
@@ -227,28 +238,30 @@ extern "C" int surrogate_infer(tune_surrogate* h, const tune_arch* arch, const t
             ++k1;
         if (k1 == k0) return tune::fail(TUNE_EINVAL, "surrogate_infer: a space larger than the chunk");
         const int64_t np = pt_offsets_host[k1] - pt_offsets_host[k0];
-        rel.resize(k1 - k0 + 1);
-        for (int64_t i = k0; i <= k1; ++i) rel[i - k0] = pt_offsets_host[i] - pt_offsets_host[k0];
-        TUNE_CUDA_TRY(cudaMemcpyAsync(coff, rel.data(), rel.size() * 8, cudaMemcpyHostToDevice, s),
-                      "surrogate_infer: chunk offsets");
         const int64_t nk = k1 - k0;
-        features_all<<<(unsigned)((nk + 7) / 8), 256, 0, s>>>(*arch, *axes, reinterpret_cast<const int4*>(descs),
-                                                              d_off, k0, k1, feats, status);
-        TUNE_CUDA_TRY(cudaGetLastError(), "surrogate_infer: features launch");
-        rc = surrogate_forward(h, reinterpret_cast<const uint16_t*>(feats), np, pred, stream);
-        if (rc) return rc;
-        score_points<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(pred, feats, np, members, score, spread);
-        TUNE_CUDA_TRY(cudaGetLastError(), "surrogate_infer: score launch");
+        // Everything below is stream-ordered: the chunk buffers are reused without a host wait.
+        rebase_offsets<<<(unsigned)((nk + 1 + 255) / 256), 256, 0, s>>>(d_off, k0, nk, coff);
+        TUNE_CUDA_TRY(cudaGetLastError(), "surrogate_infer: offsets launch");
+        if (np > 0) {
+            features_points<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(
+                *arch, *axes, reinterpret_cast<const int4*>(descs), d_off, k0, k1, pt_offsets_host[k0], np, feats,
+                status);
+            TUNE_CUDA_TRY(cudaGetLastError(), "surrogate_infer: features launch");
+            rc = surrogate_forward(h, reinterpret_cast<const uint16_t*>(feats), np, pred, stream);
+            if (rc) return rc;
+            score_points<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(pred, feats, np, members, score, spread);
+            TUNE_CUDA_TRY(cudaGetLastError(), "surrogate_infer: score launch");
+        }
         rc = tune_topk(score, coff, nk, k, s_idx, s_val, inner, tune::kWorkspaceHeader, stream);
         if (rc) return rc;
         apply_fallback<<<(unsigned)((nk + 127) / 128), 128, 0, s>>>(s_idx, s_val, a_idx, a_val, spread, d_off, k0, nk,
                                                                    k, thresh, topk_idx, topk_score, used_fallback);
         TUNE_CUDA_TRY(cudaGetLastError(), "surrogate_infer: fallback launch");
-        TUNE_CUDA_TRY(cudaStreamSynchronize(s), "surrogate_infer: chunk sync");  // rel is reused
         k0 = k1;
     }
     int st = 0;
-    TUNE_CUDA_TRY(cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost), "surrogate_infer: status");
+    TUNE_CUDA_TRY(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s), "surrogate_infer: status");
+    TUNE_CUDA_TRY(cudaStreamSynchronize(s), "surrogate_infer: sync");
     if (st) return tune::fail(TUNE_EINVAL, "surrogate_infer: a descriptor was malformed");
     return TUNE_OK;
 }

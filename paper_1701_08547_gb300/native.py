@@ -88,8 +88,14 @@ def load():
     L.tune_features.restype = C.c_int
     L.tune_suggest.argtypes = [C.POINTER(TuneArch), C.POINTER(TuneAxes), vp, i64, vp, vp, vp, vp, vp, vp, sz, vp]
     L.tune_suggest.restype = C.c_int
+    L.tune_search.argtypes = [C.POINTER(TuneArch), C.POINTER(TuneAxes), vp, i64, i32, i32, C.c_uint64, vp, vp, vp,
+                              vp, vp, sz, vp]
+    L.tune_search.restype = C.c_int
     _lib = L
     return L
+
+
+TUNE_SEARCH_RANDOM, TUNE_SEARCH_NELDER_MEAD = 1, 2
 
 
 def make_arch(row):

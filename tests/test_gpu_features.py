@@ -94,3 +94,36 @@ def test_infer_ranking_and_fallback(dev, oracle):
         chosen = gi[kk]
         assert len(set(chosen.tolist())) == k and np.all(chosen >= 0)
         assert np.all(score[chosen] <= kth * 1.05 + 1e-12), (kk, score[chosen], kth)
+
+
+def test_infer_several_chunks_and_empty_spaces(dev, oracle):
+    """20,000 kernels of 128 points (2.56 M points) take three inference chunks; some
+    spaces are empty. Fallback everywhere must reproduce the analytic top-k; without
+    fallback, sampled kernels on both sides of each chunk boundary rank validly."""
+    from paper_1701_08547_gb300.surrogate import Surrogate
+    import paper_1701_08547_gb300 as T
+
+    a, ax = archs.arch("sm_103"), gen.axes()
+    d = gen.descriptors(20000, 33, "dense128")
+    empty = [5, 8191, 8192, 12000]
+    d["space_mask"][empty] = np.uint64(0)
+    off = gen.point_offsets(d)
+    members, k = 2, 5
+    s = Surrogate(members=members, batch=4096)
+    flat = L.init_params(members, [13, 14])
+    s.set_params(flat)
+    dd = T.descs_to_device(d, dev)
+    idx, val, fb = s.infer(a, ax, dd, off, k, thresh=0.0)
+    o = oracle.evaluate(a, ax, d, k)
+    assert np.array_equal(idx.cpu().numpy(), o["idx"])
+    assert np.array_equal(val.cpu().numpy().view(np.uint32), o["cost"].view(np.uint32))
+    idx, val, fb = s.infer(a, ax, dd, off, k, thresh=1e30)
+    gi, gv = idx.cpu().numpy(), val.cpu().numpy()
+    for kk in empty:
+        assert np.all(gi[kk] == -1) and np.all(np.isinf(gv[kk]))
+    for kk in [0, 1, 8190, 8193, 16383, 16384, 16385, 19999]:
+        score, _ = _oracle_scores(oracle, a, ax, d[kk], flat, members)
+        kth = np.sort(score)[k - 1]
+        chosen = gi[kk]
+        assert len(set(chosen.tolist())) == k and np.all(chosen >= 0)
+        assert np.all(score[chosen] <= kth * 1.05 + 1e-12), (kk, score[chosen], kth)
