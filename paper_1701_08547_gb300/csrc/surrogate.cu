@@ -427,19 +427,19 @@ int refresh_fp8(tune_surrogate* h, cudaStream_t s)
     return TUNE_OK;
 }
 
-template <bool FP8>
+template <bool FP8, bool TRAIN = false>
 int launch_fused(const CUtensorMap& tx, const CUtensorMap& tw1, const CUtensorMap& tw, const tcm::Args& g,
                  unsigned grid, cudaStream_t s)
 {
     constexpr int smem = tcm::Cfg<FP8>::smem;
     static bool attr = false;
     if (!attr) {
-        TUNE_CUDA_TRY(cudaFuncSetAttribute(tcm::mlp_infer_kernel<FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           smem),
+        TUNE_CUDA_TRY(cudaFuncSetAttribute(tcm::mlp_infer_kernel<FP8, TRAIN>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                       "surrogate: fused smem attribute");
         attr = true;
     }
-    tcm::mlp_infer_kernel<FP8><<<grid, tcm::kThreads, smem, s>>>(tx, tw1, tw, g);
+    tcm::mlp_infer_kernel<FP8, TRAIN><<<grid, tcm::kThreads, smem, s>>>(tx, tw1, tw, g);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: fused launch");
     return TUNE_OK;
 }
@@ -489,10 +489,59 @@ int fused_forward(tune_surrogate* h, const __nv_bfloat16* feats, int64_t n, floa
     g.off_b5 = OFF_B5;
     g.wscale_half = h->wscale_half;
     g.pred = pred;
+    g.pred_stride = n;
+    for (int l = 0; l < NL; ++l) {
+        g.z_out[l] = nullptr;
+        g.h_out[l] = nullptr;
+    }
+    g.act_stride = 0;
     g.status = h->status;
     const long long sms = tune::device_sm_count();
     const unsigned grid = (unsigned)(g.units < sms ? g.units : sms);
     return fp8 ? launch_fused<true>(tx, tw1, tw, g, grid, s) : launch_fused<false>(tx, tw1, tw, g, grid, s);
+}
+
+// Training forward of rows [0, n_pad) of h->xin through the fused kernel (BF16), keeping
+// every layer's pre-activations Z and activations H for the backward pass and the head
+// outputs in h->y.
+int fused_train_forward(tune_surrogate* h, int n_pad, cudaStream_t s)
+{
+    CUtensorMap tx, tw1, tw;
+    const auto u64 = CU_TENSOR_MAP_DATA_TYPE_UINT64;
+    const cuuint64_t xd[2] = {IN * 2 / 8, (cuuint64_t)n_pad}, xs[1] = {IN * 2};
+    const cuuint32_t xb[2] = {16, tcm::kRows};
+    int rc = make_map_nd(&tx, u64, 2, h->xin, xd, xs, xb);
+    if (rc) return rc;
+    const cuuint64_t d1[3] = {IN * 2 / 8, WID, (cuuint64_t)h->members}, s1[2] = {IN * 2, PB * 2};
+    const cuuint32_t b1[3] = {16, WID, 1};
+    rc = make_map_nd(&tw1, u64, 3, h->wbf, d1, s1, b1);
+    if (rc) return rc;
+    const cuuint32_t bw[4] = {16, WID, 1, 1};
+    const cuuint64_t dw[4] = {WID * 2 / 8, WID, NL - 1, (cuuint64_t)h->members};
+    const cuuint64_t sw[3] = {WID * 2, WID * WID * 2, PB * 2};
+    rc = make_map_nd(&tw, u64, 4, h->wbf + BOFF_W(1), dw, sw, bw);
+    if (rc) return rc;
+    tcm::Args g;
+    g.n = n_pad;
+    g.members = h->members;
+    g.units = (long long)(n_pad / tcm::kRows) * h->members;
+    g.master = h->master;
+    g.P = P;
+    for (int l = 0; l < NL; ++l) g.off_b[l] = OFF_B(l);
+    g.off_w5 = OFF_W5;
+    g.off_b5 = OFF_B5;
+    g.wscale_half = h->wscale_half;
+    g.pred = h->y;
+    g.pred_stride = h->batch;
+    for (int l = 0; l < NL; ++l) {
+        g.z_out[l] = h->Z[l];
+        g.h_out[l] = h->H[l];
+    }
+    g.act_stride = (long long)h->batch * WID;
+    g.status = h->status;
+    const long long sms = tune::device_sm_count();
+    const unsigned grid = (unsigned)(g.units < sms ? g.units : sms);
+    return launch_fused<false, true>(tx, tw1, tw, g, grid, s);
 }
 
 // Forward through all members for rows [0, n_pad) of h->xin (n_pad a multiple of 128).
@@ -503,6 +552,8 @@ int forward(tune_surrogate* h, int n_pad, cudaStream_t s, const __nv_bfloat16* x
 {
     if (!x_in) x_in = h->xin;
     if (n_valid < 0) n_valid = n_pad;
+    // training with tcgen05 and the fused forward selected: one launch for all layers and the head
+    if (store_z && h->use_tc && h->fwd_mode == 1 && x_in == h->xin) return fused_train_forward(h, n_pad, s);
     for (int l = 0; l < NL; ++l) {
         if (h->use_tc) {
             int rc = tc_layer(h, l, n_pad, s, x_in, n_valid, store_z);

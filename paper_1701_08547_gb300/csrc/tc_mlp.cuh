@@ -69,7 +69,13 @@ struct Args {
     long long off_b[kLayers];
     long long off_w5, off_b5;
     const float* wscale_half;  // FP8: [members][3][256] halves of the per-row scales of W2..W4
-    float* pred;            // [members][n]
+    float* pred;            // [members][pred_stride]
+    long long pred_stride;  // member stride of pred (n for inference)
+    // training (BF16 only): per layer the pre-activations z (FP32) and activations h = gelu(z)
+    // (BF16) of every row < n, [members][act_stride] with rows of 256; null: not kept
+    float* z_out[kLayers];
+    __nv_bfloat16* h_out[kLayers];
+    long long act_stride;
     int* status;
 };
 
@@ -174,7 +180,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 
 // grid: min(SMs, units) persistent CTAs; CTA b runs units b, b + gridDim.x, ...;
 // its j-th unit goes to chain j % 2. Unit u = (tile u / members, member u % members).
-template <bool FP8>
+template <bool FP8, bool TRAIN = false>
 __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtensorMap tx,
                                                                 const __grid_constant__ CUtensorMap tw1,
                                                                 const __grid_constant__ CUtensorMap tw,
@@ -354,6 +360,13 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                         tmem_ld16(taddr + (uint32_t)n0, v);
 #pragma unroll
                         for (int i = 0; i < 16; ++i) v[i] = fmaf(v[i], f8 ? ss[i] : acc_mul, bb[i]);
+                        const long long arow = (long long)mem * g.act_stride + (long long)(tile * kRows + r) * kWid + n0;
+                        if (TRAIN && !FP8 && g.z_out[l]) {  // training: keep z for the backward pass
+                            float4* zo = reinterpret_cast<float4*>(g.z_out[l] + arow);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                zo[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                        }
                         // 2 gelu(z) = z (1 + tanh u) in FP32: one multi-function-unit tanh per element
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
@@ -367,6 +380,16 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                             for (int qd = 0; qd < 4; ++qd) w[qd] = pack_e4m3(v[4 * qd], v[4 * qd + 1], v[4 * qd + 2], v[4 * qd + 3]);
                             st_shared_v4(act + (n0 >> 7) * kChunkA + swz(r, (n0 & 127) >> 4), w[0], w[1], w[2], w[3]);
                             continue;
+                        }
+                        if (TRAIN && !FP8 && g.h_out[l]) {
+                            // training: h = bf16(gelu(z)) = bf16(2 gelu(z)) / 2 exactly
+                            uint4* ho = reinterpret_cast<uint4*>(g.h_out[l] + arow);
+#pragma unroll
+                            for (int hh = 0; hh < 2; ++hh) {
+                                const float* x = v + 8 * hh;
+                                ho[hh] = make_uint4(pack_bf16(0.5f * x[0], 0.5f * x[1]), pack_bf16(0.5f * x[2], 0.5f * x[3]),
+                                                    pack_bf16(0.5f * x[4], 0.5f * x[5]), pack_bf16(0.5f * x[6], 0.5f * x[7]));
+                            }
                         }
                         if (head) {
                             // head on 2 h4; the sum is halved with b5 added below
@@ -399,7 +422,7 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                         if (!(ok = wait_bar(&head_bar[s], (uint32_t)(k & 1), g.status, abort_v))) break;
                         const int row = tile * kRows + r;
                         const float sum = ((yh + head_part[s][0][r]) + head_part[s][1][r]) + head_part[s][2][r];
-                        if (row < g.n) g.pred[(long long)mem * g.n + row] = fmaf(sum, 0.5f, prm[g.off_b5]);
+                        if (row < g.n) g.pred[(long long)mem * g.pred_stride + row] = fmaf(sum, 0.5f, prm[g.off_b5]);
                     }
                 }
             }

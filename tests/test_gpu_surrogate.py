@@ -106,6 +106,30 @@ def test_gradients_match_oracle(dev):
             assert rel <= 3e-2, (m, name, rel)
 
 
+def test_training_forward_paths_agree(dev):
+    """Training runs its forward through the fused kernel (one launch, Z and H written for
+    the backward pass) by default and layer by layer on request; the gradients agree to
+    FP32 summation order and one-step BF16 rounding differences."""
+    import torch
+
+    X = to_dev(feats(900, 12), dev)
+    t = torch.tensor(np.random.default_rng(4).standard_normal(900), dtype=torch.float32, device=dev)
+    grads = []
+    for mode in ("fused", "layered"):
+        s, _ = make(3, 1024, seed0=21)
+        if mode == "layered":
+            s.set_forward_mode(s.FWD_LAYERED)
+        s.train_step(X, t, apply_update=False)
+        s.check()
+        grads.append(s.get(s.GET_GRADS).reshape(3, L.P))
+    for m in range(3):
+        a, b = L.unpack(grads[0][m], 1)[0], L.unpack(grads[1][m], 1)[0]
+        for name in a:
+            x, y = np.asarray(a[name], np.float64), np.asarray(b[name], np.float64)
+            rel = np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-30)
+            assert rel <= 2e-2, (m, name, rel)
+
+
 def test_adam_steps_match_oracle(dev):
     import torch
 
