@@ -176,8 +176,21 @@ __global__ void __launch_bounds__(kThreads)
                     const float t = filter_bound(tau_k);
                     const unsigned cm = (g[0] <= t ? 1u : 0u) | (g[1] <= t ? 2u : 0u) | (g[2] <= t ? 4u : 0u) |
                                         (g[3] <= t ? 8u : 0u);
-                    if (__ballot_sync(kFull, cm != 0u) == 0u) continue;
+                    const unsigned who = __ballot_sync(kFull, cm != 0u);
+                    if (who == 0u) continue;
                     const int iq = i0 + 128 * q;
+                    // one lane with one candidate (the common case once the list has filled):
+                    // insert it directly, without the reduction rounds of a merge
+                    const int src = __ffs(who) - 1;
+                    const unsigned cm_src = __shfl_sync(kFull, cm, src);
+                    if ((who & (who - 1u)) == 0u && (cm_src & (cm_src - 1u)) == 0u) {
+                        const int j = __ffs(cm_src) - 1;
+                        const float gv = j == 0 ? g[0] : j == 1 ? g[1] : j == 2 ? g[2] : g[3];
+                        const unsigned ck = __shfl_sync(kFull, order_key(gv + 0.0f), src);  // -0 ranks as +0
+                        const int ci = __shfl_sync(kFull, iq + j, src);
+                        if (key_less(ck, ci, tau_k, tau_i)) list_insert(lk, li, tau_k, tau_i, ck, ci, k, lane);
+                        continue;
+                    }
                     merge_batch<4>(g, cm, [&](int j) { return iq + j; }, lk, li, tau_k, tau_i, k, lane);
                 }
             }
