@@ -398,6 +398,12 @@ def surrogate_section(args, dev, a, ax, peaks):
     ev = SD.evaluate(sur, a, ax, held_out, dev, k=5, thresh=0.1)
     ev_nofb = SD.evaluate(sur, a, ax, held_out, dev, k=5, thresh=1e30)
     pruning = SD.evaluate_pruning(a, ax, held_out, dev)
+    from paper_1701_08547_gb300 import realkernels as RK
+
+    t0 = time.perf_counter()
+    real = RK.evaluate(a, ax, dev, n=args.real_n, surrogate=inf_sur)
+    real["seconds"] = time.perf_counter() - t0
+    real["matrix_order"] = args.real_n
     peak = peaks.get("bf16_tflops", 1900.0)
     return {
         "members": members,
@@ -412,6 +418,7 @@ def surrogate_section(args, dev, a, ax, peaks):
         "top5_vs_analytic": {"overlap": agree_overlap, "analytic_best_in_surrogate_top5": agree_hit},
         "top5_vs_measured_best": {"thresh_0.1": ev, "no_fallback": ev_nofb},
         "static_pruning_vs_measured_best": pruning,
+        "real_kernels": real,
     }
 
 
@@ -670,6 +677,7 @@ def main():
     p.add_argument("--sur-eval", type=int, default=150, help="held-out kernels with fully timed spaces")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--budget", type=int, default=128, help="search workload: evaluations per kernel")
+    p.add_argument("--real-n", type=int, default=4096, help="matrix order of the real-kernel variants")
     args = p.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -401,6 +401,29 @@ int tune_search(const tune_arch* arch, const tune_axes* axes, const tune_kernel_
                 int32_t method, int32_t budget, uint64_t seed, const uint32_t* t_keep, int32_t* best_idx,
                 float* best_cost, int32_t* evals, void* workspace, size_t ws_bytes, tune_stream_t stream);
 
+/*
+ * tune_real_measure — the paper's dense benchmark kernels (Section IV-A, Table
+ * "Kernel specifications") as tuning variants timed on this GPU: matVec2D y = A x,
+ * ATAX y = A^T (A x), BiCG q = A p and s = A^T r, for an n x n FP32 matrix.
+ * Each product is a grid-stride loop over output elements (a thread per row of A x,
+ * per column of A^T x) whose inner loop over n is unrolled U times. Variant v runs
+ * the kernel's launches with G[v] blocks of T[v] threads at carveout C[v] percent:
+ * one untimed run, then `reps` runs timed with CUDA events; us[v] = median run time
+ * in microseconds (NaN where the configuration cannot launch), regs[v] = registers
+ * per thread of the unroll's module. Operands are fixed: A[i][j] = ((7i + 13j) mod
+ * 17 - 8) / 8, x = p: ((5j) mod 11 - 5) / 4, r: ((5j + 3) mod 11 - 5) / 4.
+ * result: NULL or host float[n] (matVec2D: y; ATAX: y) / [2n] (BiCG: q then s), the
+ * outputs of variant 0. Arrays T, G, U, C, us, regs are host memory; the call
+ * allocates the operands (n^2 + 4n floats) for its duration and is synchronous.
+ * Returns TUNE_ECOMPILE if a module fails to compile.
+ */
+#define TUNE_REAL_MATVEC 0
+#define TUNE_REAL_ATAX 1
+#define TUNE_REAL_BICG 2
+int tune_real_measure(int32_t kernel, int32_t n, const int32_t* T, const int32_t* G, const int32_t* U,
+                      const int32_t* C, int32_t n_variants, int32_t reps, float* us, int32_t* regs, float* result,
+                      tune_stream_t stream);
+
 /* Bytes of device workspace the call needs (at least 256). */
 size_t tune_workspace_bytes(int call, int64_t n, int32_t k);
 

@@ -91,11 +91,14 @@ def load():
     L.tune_search.argtypes = [C.POINTER(TuneArch), C.POINTER(TuneAxes), vp, i64, i32, i32, C.c_uint64, vp, vp, vp,
                               vp, vp, sz, vp]
     L.tune_search.restype = C.c_int
+    L.tune_real_measure.argtypes = [i32, i32, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp]
+    L.tune_real_measure.restype = C.c_int
     _lib = L
     return L
 
 
 TUNE_SEARCH_RANDOM, TUNE_SEARCH_NELDER_MEAD = 1, 2
+TUNE_REAL_MATVEC, TUNE_REAL_ATAX, TUNE_REAL_BICG = 0, 1, 2
 
 
 def make_arch(row):
