@@ -183,6 +183,24 @@ def dist_env():
     return rank, world, local
 
 
+def shard(n, seed, space, rank):
+    """Rank r's kernels: descriptors r n .. (r + 1) n - 1 of the seeded workload (weak
+    scaling; kernels are independent, so the ranks exchange no data)."""
+    return gen.descriptors(n, seed, space, first=rank * n)
+
+
+def max_over_ranks(value, world, device):
+    """The largest of the ranks' values (the step time of the slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -208,7 +226,7 @@ def run_ours(args):
     n, space, k, seed = WORKLOADS[args.workload]
     n = args.kernels or n
     a, ax = archs.arch("sm_103"), gen.axes()
-    descs = gen.descriptors(n, seed, space, first=rank * n)
+    descs = shard(n, seed, space, rank)
     points = int(gen.space_sizes(descs).sum())
     algo_instr = algorithmic_instructions(descs, ax)
     triple_instr = triple_instructions(descs)
@@ -268,11 +286,7 @@ def run_ours(args):
         dist.barrier()
     T.tune_check(ws, stream)
     step_ms = [s_.elapsed_time(e) for s_, e in zip(starts, ends)]
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
 
     # ---- end to end through the public API with host buffers (pinned), copies timed.
     host_d = torch.from_numpy(np.ascontiguousarray(descs).view(np.uint8).reshape(-1, 64)).pin_memory()
@@ -293,11 +307,8 @@ def run_ours(args):
         if i >= args.warmup:
             e_end[i - args.warmup].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_start, e_end)) / args.steps
+    e2e_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(e_start, e_end)) / args.steps, world, dev)
     if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
         dist.destroy_process_group()
     if rank != 0:
         return None
