@@ -236,3 +236,24 @@ def test_all_arch_rows_in_one_launch(dev, oracle, flags):
         o = oracle.evaluate(a, ax, d, 6)
         assert np.array_equal(idx[i], o["idx"]), (names[i], np.argwhere(idx[i] != o["idx"])[:5])
         assert np.array_equal(cost[i].view(np.uint32), o["cost"].view(np.uint32)), names[i]
+
+
+@pytest.mark.parametrize("k", [3, 16])
+def test_equal_cost_walks(dev, oracle, k):
+    """Spaces where many points share one cost, so that the order of equal costs decides the
+    top-k: all counts zero (every valid point costs 0 and the k lowest valid indices win),
+    tiny counts (costs underflow towards zero), and a single FP32 count class (many exact
+    ties across carveouts and grid sizes). Dense and uneven masks, thread and warp
+    schedules."""
+    a, ax = archs.arch("sm_103"), gen.axes()
+    d = gen.descriptors(96, 71, "uneven")
+    d["space_mask"][:32] = np.uint64(gen.MASK_DENSE)
+    d["n"][0:48] = 0.0
+    d["n"][48:64] = np.float32(1e-37)
+    d["n"][64:96, 1:] = 0.0
+    g = gpu_eval(dev, a, ax, d, k, emit=True)  # both schedules and the emitting pass
+    o = oracle.evaluate(a, ax, d, k, emit=True, offsets=gen.point_offsets(d))
+    assert_same_topk(g, o)
+    # per point bit for bit (costs of zero or subnormal size have no meaningful FP64 ratio)
+    assert np.array_equal(g["B"], o["B"]) and np.array_equal(g["W"], o["W"])
+    assert np.array_equal(g["cost32"].view(np.uint32), o["cost32"].view(np.uint32))
