@@ -424,6 +424,27 @@ int tune_real_measure(int32_t kernel, int32_t n, const int32_t* T, const int32_t
                       const int32_t* C, int32_t n_variants, int32_t reps, float* us, int32_t* regs, float* result,
                       tune_stream_t stream);
 
+/*
+ * tune_eval_host — tune_eval with the descriptors and the top-k results in host
+ * memory: the kernels are cut into chunks of `chunk`; chunk i is copied to the device
+ * on a library stream, evaluated on `stream`, and its results copied back on a second
+ * library stream while chunk i + 1 is copied in and evaluated, so that the transfers
+ * overlap the evaluation (two staging buffers in dev_scratch). Host buffers should be
+ * pinned for the copies to run asynchronously. Results equal tune_eval's bit for bit.
+ *   host_descs      host tune_kernel_desc[n_kernels]
+ *   host_topk_idx   host int32[n_kernels * k];  host_topk_cost  host float[n_kernels * k]
+ *   dev_scratch     device memory, 256-byte aligned, of tune_eval_host_scratch_bytes(chunk, k)
+ *                   bytes; its first 256 bytes are the status header (read with tune_check)
+ *   flags           TUNE_SCHED_WARP with its chunk / CTA fields
+ * Enqueues the work and returns; `stream` completes once the last result is in host
+ * memory. Calls on one device use the same two library streams and must not run
+ * concurrently from several host threads.
+ */
+size_t tune_eval_host_scratch_bytes(int64_t chunk, int32_t k);
+int tune_eval_host(const tune_arch* arch, const tune_axes* axes, const tune_kernel_desc* host_descs, int64_t n_kernels,
+                   int32_t k, uint32_t flags, int32_t* host_topk_idx, float* host_topk_cost, int64_t chunk,
+                   void* dev_scratch, size_t scratch_bytes, tune_stream_t stream);
+
 /* Bytes of device workspace the call needs (at least 256). */
 size_t tune_workspace_bytes(int call, int64_t n, int32_t k);
 

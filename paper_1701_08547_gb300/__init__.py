@@ -12,7 +12,7 @@ from . import native
 from .native import (TUNE_EMIT_POINTS, TUNE_SCHED_CHUNK, TUNE_SCHED_CTAS,  # noqa: F401
                      TUNE_SCHED_THREAD, TUNE_SCHED_WARP, TuneError)
 
-__all__ = ["tune_eval", "tune_eval_archs", "tune_topk", "tune_autotune", "tune_features", "tune_suggest", "tune_search", "tune_workspace_bytes", "tune_check",
+__all__ = ["tune_eval", "tune_eval_archs", "tune_topk", "tune_autotune", "tune_features", "tune_suggest", "tune_search", "tune_eval_host", "tune_workspace_bytes", "tune_check",
            "descs_to_device", "TUNE_EMIT_POINTS", "TUNE_SCHED_WARP", "TUNE_SCHED_THREAD",
            "TUNE_SCHED_CHUNK", "TUNE_SCHED_CTAS", "TuneError"]
 
@@ -205,6 +205,26 @@ def tune_search(arch, axes, descs, method, budget, seed, t_keep=None, workspace_
                        _ptr(workspace_buf), workspace_buf.numel(), _stream(stream))
     native.check(rc)
     return best_idx, best_cost, evals
+
+
+def tune_eval_host(arch, axes, host_descs, k, chunk, topk_idx, topk_cost, scratch=None, flags=0, stream=None):
+    """tune_eval from and to host memory with the copies overlapping the evaluation.
+    host_descs: host uint8 tensor [n, 64] (pinned for overlap); topk_idx / topk_cost: host
+    int32 / float32 tensors [n, k] (pinned); scratch: device uint8 tensor of
+    tune_eval_host_scratch_bytes(chunk, k) bytes (allocated here if None). Enqueues on
+    `stream`; returns the scratch (its header holds the status word)."""
+    torch = _torch()
+    L = native.load()
+    n = host_descs.numel() // 64
+    nbytes = L.tune_eval_host_scratch_bytes(int(chunk), int(k))
+    if scratch is None:
+        scratch = torch.empty(nbytes, dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
+    a = native.make_arch(arch)
+    x = native.make_axes(axes)
+    rc = L.tune_eval_host(C.byref(a), C.byref(x), _ptr(host_descs), n, int(k), int(flags), _ptr(topk_idx),
+                          _ptr(topk_cost), int(chunk), _ptr(scratch), scratch.numel(), _stream(stream))
+    native.check(rc)
+    return scratch
 
 
 def tune_check(workspace_buf, stream=None):

@@ -93,6 +93,10 @@ def load():
     L.tune_search.restype = C.c_int
     L.tune_real_measure.argtypes = [i32, i32, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp]
     L.tune_real_measure.restype = C.c_int
+    L.tune_eval_host_scratch_bytes.argtypes = [i64, i32]
+    L.tune_eval_host_scratch_bytes.restype = sz
+    L.tune_eval_host.argtypes = [C.POINTER(TuneArch), C.POINTER(TuneAxes), vp, i64, i32, u32, vp, vp, i64, vp, sz, vp]
+    L.tune_eval_host.restype = C.c_int
     _lib = L
     return L
 
