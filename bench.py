@@ -87,12 +87,13 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+def recorded_profile(workload):
+    """Figures of the committed ncu summary of this workload's launch, if it was taken on
+    the current kernel source (else {}): bytes_per_launch (DRAM read + write) and
+    issue_active (fraction of issue slots used)."""
     path = os.path.join(ROOT, "profiles", f"tune_eval_{workload}.md")
     if not os.path.exists(path):
-        return None
+        return {}
     vals = {}
     with open(path) as f:
         for line in f:
@@ -101,8 +102,13 @@ def recorded_traffic(workload):
                     k, v = kv.split("=")
                     vals[k] = v
     if vals.get("source_sha256") != kernel_source_hash():
-        return None
-    return float(vals["bytes_per_launch"]) if "bytes_per_launch" in vals else None
+        return {}
+    return {k: float(v) for k, v in vals.items() if k != "source_sha256"}
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch from the committed ncu summary (None if stale or absent)."""
+    return recorded_profile(workload).get("bytes_per_launch")
 
 
 class ClockSampler:
@@ -347,6 +353,7 @@ def run_ours(args):
                      "instr_per_point": algo_instr / points,
                      "instr_definition": "2 per point (cost multiply, compare) + 5 per (T,U,C) triple",
                      "frac_12_per_point": achieved_12 / peak,
+                     "issue_active_ncu": recorded_profile(args.workload).get("issue_active"),
                      "frac_8_per_triple": achieved_triple / peak},
         "e2e": {"value": world * points / (e2e_ms * 1e-3), "unit": "points/s",
                 "h2d_bytes_per_step": n * 64, "d2h_bytes_per_step": n * k * 8,
