@@ -24,6 +24,12 @@ constexpr size_t kWorkspaceHeader = 256;
 // Number of SMs of the current device (cached per device).
 int device_sm_count();
 
+// tune_eval's warp-schedule launch for one architecture row (flags: TUNE_SCHED_WARP
+// with its chunk / CTA fields), with a caller-chosen status word and queue counter.
+int eval_launch(const tune_arch* arch, const tune_axes* axes, const tune_kernel_desc* descs, int64_t n_kernels,
+                int32_t k, uint32_t flags, int32_t* topk_idx, float* topk_cost, int* status,
+                unsigned long long* queue, cudaStream_t s);
+
 }  // namespace tune
 
 #define TUNE_CUDA_TRY(call, what)                                         \
