@@ -16,6 +16,7 @@
 #include "mlp_gemm.cuh"
 #include "tc_gemm.cuh"
 #include "tc_mlp.cuh"
+#include "tc_mlp_bwd.cuh"
 #include "tune_internal.h"
 
 using mlp::GemmArgs;
@@ -50,13 +51,15 @@ struct tune_surrogate {
     __nv_bfloat16* xin = nullptr;       // [batch x IN]
     float* Z[NL] = {};                  // [members][batch x WID]
     __nv_bfloat16* H[NL] = {};          // [members][batch x WID]
-    __nv_bfloat16* dZ[2] = {};          // ping-pong [members][batch x WID]
+    __nv_bfloat16* dZ[NL] = {};         // [members][batch x WID]: dZ of layer l (fused chain) or ping-pong
+    __nv_bfloat16* wbfT = nullptr;      // W2..W4 transposed, [members][3][WID][WID] (fused input gradients)
     float *y = nullptr, *dy = nullptr, *lbl = nullptr, *loss = nullptr;  // [members][batch] / [members]
     float* part = nullptr;              // [members][KSPLIT][WID x WID]
     void* block = nullptr;              // the one device allocation
     int* status = nullptr;              // device status word (timeouts of bounded waits)
     int use_tc = 1;                     // forward layers on tcgen05 (1) or mma.sync (0)
     int fwd_mode = 1;                   // surrogate_forward: 0 layer by layer, 1 fused BF16, 2 fused FP8
+    int bwd_mode = 1;                   // input gradients: 0 one GEMM per layer, 1 fused chain (tcgen05)
     uint8_t* w8 = nullptr;              // E4M3 codes of W2..W4 [members][3][256][256]
     float* wscale = nullptr;            // their per-row scales [members][3][256]
     float* wscale_half = nullptr;       // the scales halved (the fused epilogue's multipliers)
@@ -272,6 +275,21 @@ __global__ void cast_weights(const float* master, __nv_bfloat16* wbf, int member
     int l = NL - 1;
     while (l > 0 && q < BOFF_W(l)) --l;
     wbf[e] = __float2bfloat16_rn(master[mem * P + OFF_W(l) + (q - BOFF_W(l))]);
+}
+
+// wbfT[mem][l - 1][i][o] = wbf[mem][W_l][o][i] for l = 1..3 (W2..W4): the K-major B operands
+// of the fused input-gradient chain. 32 x 32 tiles through shared memory; grid (8, 8, 3 members)
+// x (32, 8).
+__global__ void transpose_weights(const __nv_bfloat16* __restrict__ wbf, __nv_bfloat16* wbfT)
+{
+    __shared__ __nv_bfloat16 t[32][33];
+    const int mem = blockIdx.z / (NL - 1), l = blockIdx.z % (NL - 1) + 1;
+    const __nv_bfloat16* src = wbf + (long long)mem * PB + BOFF_W(l);
+    __nv_bfloat16* dst = wbfT + ((long long)mem * (NL - 1) + (l - 1)) * WID * WID;
+    const int o0 = blockIdx.y * 32, i0 = blockIdx.x * 32;
+    for (int y = threadIdx.y; y < 32; y += 8) t[y][threadIdx.x] = src[(o0 + y) * WID + i0 + threadIdx.x];
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) dst[(i0 + y) * WID + o0 + threadIdx.x] = t[threadIdx.x][y];
 }
 
 // Per-row E4M3 quantisation of W2..W4 (FP32, as the oracle mirrors it): s = max |w| / 448
@@ -544,6 +562,48 @@ int fused_train_forward(tune_surrogate* h, int n_pad, cudaStream_t s)
     return launch_fused<false, true>(tx, tw1, tw, g, grid, s);
 }
 
+// Input gradients of layers 4, 3 and 2 in one persistent launch (tc_mlp_bwd.cuh):
+// dz[l - 1] = bf16((dz[l] W_l) * gelu'(Z[l - 1])) for l = 3, 2, 1 (0-based), rows [0, n_pad).
+int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaStream_t s)
+{
+    transpose_weights<<<dim3(WID / 32, WID / 32, (NL - 1) * h->members), dim3(32, 8), 0, s>>>(h->wbf, h->wbfT);
+    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: transpose launch");
+    CUtensorMap tdz, twt;
+    const auto u64 = CU_TENSOR_MAP_DATA_TYPE_UINT64;
+    const cuuint64_t dd[3] = {WID * 2 / 8, (cuuint64_t)n_pad, (cuuint64_t)h->members};
+    const cuuint64_t ds[2] = {WID * 2, (cuuint64_t)h->batch * WID * 2};
+    const cuuint32_t db[3] = {16, tcm::kRows, 1};
+    int rc = make_map_nd(&tdz, u64, 3, dz[NL - 1], dd, ds, db);
+    if (rc) return rc;
+    const cuuint64_t dw[4] = {WID * 2 / 8, WID, NL - 1, (cuuint64_t)h->members};
+    const cuuint64_t sw[3] = {WID * 2, WID * WID * 2, (NL - 1) * WID * WID * 2};
+    const cuuint32_t bw[4] = {16, WID, 1, 1};
+    rc = make_map_nd(&twt, u64, 4, h->wbfT, dw, sw, bw);
+    if (rc) return rc;
+    tcm::BwdArgs g;
+    g.rows = n_pad;
+    g.members = h->members;
+    g.units = (long long)(n_pad / tcm::kRows) * h->members;
+    for (int j = 0; j < tcm::kBwdStages; ++j) {
+        g.z[j] = h->Z[NL - 2 - j];
+        g.dz[j] = dz[NL - 2 - j];
+    }
+    g.act_stride = (long long)h->batch * WID;
+    g.status = h->status;
+    constexpr int smem = tcm::Cfg<false>::smem;
+    static bool attr = false;
+    if (!attr) {
+        TUNE_CUDA_TRY(cudaFuncSetAttribute(tcm::mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                      "surrogate: fused backward smem attribute");
+        attr = true;
+    }
+    const long long sms = tune::device_sm_count();
+    const unsigned grid = (unsigned)(g.units < sms ? g.units : sms);
+    tcm::mlp_bwd_kernel<<<grid, tcm::kThreads, smem, s>>>(tdz, twt, g);
+    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: fused backward launch");
+    return TUNE_OK;
+}
+
 // Forward through all members for rows [0, n_pad) of h->xin (n_pad a multiple of 128).
 // x_in: layer-1 input rows (h->xin, or the caller's features on the tcgen05 path);
 // n_valid rows of it exist; store_z keeps the pre-activations for a backward pass.
@@ -595,12 +655,20 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
     const int slices = (n_pad + kRowSlice - 1) / kRowSlice;
     head_bwd_partial<<<dim3(slices, h->members), WID, 0, s>>>(h->dy, h->H[NL - 1], h->part, n_pad, B, slices);
     slices_reduce<<<dim3((WID + 1 + 31) / 32, h->members), 256, 0, s>>>(h->part, h->grad, OFF_W5, WID + 1, slices);
+    // dZ of layer l: a buffer per layer when the input-gradient chain runs fused, else two
+    // buffers in turn (each is consumed by its weight gradient before it is overwritten)
+    const bool fused = h->use_tc && h->bwd_mode == 1;
+    __nv_bfloat16* dzl[NL];
+    for (int l = 0; l < NL; ++l) dzl[l] = h->dZ[fused ? l : (l & 1)];
     head_bwd_act<<<dim3((unsigned)(((long long)B * WID / 8 + 255) / 256), h->members), 256, 0, s>>>(
-        h->dy, h->master, h->Z[NL - 1], h->dZ[0], B);
+        h->dy, h->master, h->Z[NL - 1], dzl[NL - 1], B);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: head backward launch");
-    int cur = 0;
+    if (fused) {
+        int rc = fused_backward(h, n_pad, dzl, s);
+        if (rc) return rc;
+    }
     for (int l = NL - 1; l >= 0; --l) {
-        const __nv_bfloat16* dz = h->dZ[cur];
+        const __nv_bfloat16* dz = dzl[l];
         const int kin = (int)fan_in(l);
         // weight gradient: dW[o][i] = sum_r dZ[r][o] * Hprev[r][i]   (split over the batch)
         GemmArgs g = gargs();
@@ -628,7 +696,7 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
         bias_partial<<<dim3(slices, h->members), WID, 0, s>>>(dz, h->part, n_pad, B, slices);
         slices_reduce<<<dim3(WID / 32, h->members), 256, 0, s>>>(h->part, h->grad, OFF_B(l), WID, slices);
         TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: reduce launch");
-        if (l == 0) break;
+        if (l == 0 || fused) continue;
         // input gradient of layer l, times gelu' of layer l-1: dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1})
         GemmArgs d = gargs();
         d.A = dz;
@@ -642,12 +710,11 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
         d.K = WID;
         d.Z = h->Z[l - 1];
         d.sZ = (long long)B * WID;
-        d.H = h->dZ[cur ^ 1];
+        d.H = dzl[l - 1];
         d.sH = (long long)B * WID;
         d.ldc = WID;
         rc = gemm<false, true, mlp::EPI_GELU_GRAD>(d, h->members, s);
         if (rc) return rc;
-        cur ^= 1;
     }
     return TUNE_OK;
 }
@@ -693,6 +760,11 @@ int surrogate_set_option(tune_surrogate* h, int option, int value)
         h->fwd_mode = value;
         return TUNE_OK;
     }
+    if (option == 2) {
+        if (value < 0 || value > 1) return tune::fail(TUNE_EINVAL, "surrogate_set_option: backward mode outside 0..1");
+        h->bwd_mode = value;
+        return TUNE_OK;
+    }
     return tune::fail(TUNE_EINVAL, "surrogate_set_option: unknown option %d", option);
 }
 
@@ -728,8 +800,8 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     add(B * IN * 2);
     for (int l = 0; l < NL; ++l) add(M * B * WID * 4);
     for (int l = 0; l < NL; ++l) add(M * B * WID * 2);
-    add(M * B * WID * 2);
-    add(M * B * WID * 2);
+    for (int l = 0; l < NL; ++l) add(M * B * WID * 2);
+    add(M * (NL - 1) * WID * WID * 2);
     add(M * B * 4);
     add(M * B * 4);
     add(B * 4);
@@ -754,8 +826,8 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     h->xin = carve<__nv_bfloat16>(p, B * IN);
     for (int l = 0; l < NL; ++l) h->Z[l] = carve<float>(p, M * B * WID);
     for (int l = 0; l < NL; ++l) h->H[l] = carve<__nv_bfloat16>(p, M * B * WID);
-    h->dZ[0] = carve<__nv_bfloat16>(p, M * B * WID);
-    h->dZ[1] = carve<__nv_bfloat16>(p, M * B * WID);
+    for (int l = 0; l < NL; ++l) h->dZ[l] = carve<__nv_bfloat16>(p, M * B * WID);
+    h->wbfT = carve<__nv_bfloat16>(p, M * (NL - 1) * WID * WID);
     h->y = carve<float>(p, M * B);
     h->dy = carve<float>(p, M * B);
     h->lbl = carve<float>(p, B);

@@ -55,6 +55,7 @@ class Surrogate:
 
     GET_PARAMS, GET_GRADS, GET_M, GET_V, GET_LOSS, GET_PRED, GET_FP8_CODES, GET_FP8_SCALES = range(8)
     FWD_LAYERED, FWD_FUSED_BF16, FWD_FUSED_FP8 = range(3)
+    BWD_LAYERED, BWD_FUSED = range(2)
 
     def __init__(self, members=5, batch=8192, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         self.L = _lib()
@@ -87,6 +88,11 @@ class Surrogate:
         """forward()/infer(): layer by layer (0), one fused launch in BF16 (1, the default),
         or fused with layers 2-4 on E4M3 codes (2)."""
         self.set_option(1, mode)
+
+    def set_backward_mode(self, mode):
+        """Input gradients of layers 4, 3 and 2: one GEMM per layer (0) or one fused
+        tcgen05 launch for the chain (1, the default; needs the tcgen05 option)."""
+        self.set_option(2, mode)
 
     def check(self):
         native.check(self.L.surrogate_status(self.h))

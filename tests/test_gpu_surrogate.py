@@ -130,6 +130,33 @@ def test_training_forward_paths_agree(dev):
             assert rel <= 2e-2, (m, name, rel)
 
 
+def test_training_backward_paths_agree(dev):
+    """The input gradients of layers 4..2 run as one fused tcgen05 chain by default and as
+    one GEMM per layer on request; with the same forward the gradients agree to FP32
+    summation order (BF16 rounding of dZ may differ in the last place)."""
+    import torch
+
+    # (members, batch, rows): one unit per CTA; and 315 units on at most 152 CTAs, so that
+    # both chains and a chain's second unit run
+    for members, batch, n in ((3, 1024, 900), (3, 1024, 1024), (5, 8192, 8000)):
+        X = to_dev(feats(n, 13), dev)
+        t = torch.tensor(np.random.default_rng(5).standard_normal(n), dtype=torch.float32, device=dev)
+        grads = []
+        for mode in ("fused", "layered"):
+            s, _ = make(members, batch, seed0=23)
+            if mode == "layered":
+                s.set_backward_mode(s.BWD_LAYERED)
+            s.train_step(X, t, apply_update=False)
+            s.check()
+            grads.append(s.get(s.GET_GRADS).reshape(members, L.P))
+        for m in range(members):
+            a, b = L.unpack(grads[0][m], 1)[0], L.unpack(grads[1][m], 1)[0]
+            for name in a:
+                x, y = np.asarray(a[name], np.float64), np.asarray(b[name], np.float64)
+                rel = np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-30)
+                assert rel <= 1e-2, (n, m, name, rel)
+
+
 def test_adam_steps_match_oracle(dev):
     import torch
 
