@@ -266,9 +266,11 @@ int surrogate_members(const tune_surrogate* h);
  * 0 layer by layer (option 0 picks the GEMM), 1 fused BF16 (default), 2 fused with
  * layers 2-4 on E4M3 codes: W2..W4 quantised per output row (scale = max |w| / 448,
  * nearest-even, saturating), activations with unit scale, FP32 accumulation;
- * 2 = input gradients of training: 0 one GEMM per layer, 1 (default, with option 0 on)
- * the chain dZ4 -> dZ3 -> dZ2 -> dZ1 (products with W4, W3, W2) in one fused
- * tcgen05 launch. */
+ * 2 = training's backward pass: 0 one mma.sync GEMM per input and weight gradient;
+ * 1 (default, with option 0 on) the chain dZ4 -> dZ3 -> dZ2 -> dZ1 (products with W4,
+ * W3, W2) in one fused tcgen05 launch and the weight gradients on tcgen05 (both
+ * operands MN-major), split over the batch and reduced in split order;
+ * 3 = batch splits per member of those weight gradients (0, the default: SMs / (2 members)). */
 int surrogate_set_option(tune_surrogate* h, int option, int value);
 /* Synchronous: TUNE_ETIMEOUT if a bounded wait inside a surrogate kernel gave up. */
 int surrogate_status(tune_surrogate* h);

@@ -8,6 +8,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include <cuda_fp8.h>
@@ -17,6 +18,7 @@
 #include "tc_gemm.cuh"
 #include "tc_mlp.cuh"
 #include "tc_mlp_bwd.cuh"
+#include "tc_wgrad.cuh"
 #include "tune_internal.h"
 
 using mlp::GemmArgs;
@@ -54,12 +56,14 @@ struct tune_surrogate {
     __nv_bfloat16* dZ[NL] = {};         // [members][batch x WID]: dZ of layer l (fused chain) or ping-pong
     __nv_bfloat16* wbfT = nullptr;      // W2..W4 transposed, [members][3][WID][WID] (fused input gradients)
     float *y = nullptr, *dy = nullptr, *lbl = nullptr, *loss = nullptr;  // [members][batch] / [members]
-    float* part = nullptr;              // [members][KSPLIT][WID x WID]
+    float* part = nullptr;              // split-K partials: part_slices x [WID x WID]
+    int part_slices = 0;                // at least members x KSPLIT and the SM count
     void* block = nullptr;              // the one device allocation
     int* status = nullptr;              // device status word (timeouts of bounded waits)
     int use_tc = 1;                     // forward layers on tcgen05 (1) or mma.sync (0)
     int fwd_mode = 1;                   // surrogate_forward: 0 layer by layer, 1 fused BF16, 2 fused FP8
-    int bwd_mode = 1;                   // input gradients: 0 one GEMM per layer, 1 fused chain (tcgen05)
+    int bwd_mode = 1;                   // backward: 0 mma.sync GEMMs, 1 fused input gradients + tcgen05 dW
+    int wgrad_splits = 0;               // tcgen05 weight gradients: batch splits per member (0: SMs / 2 members)
     uint8_t* w8 = nullptr;              // E4M3 codes of W2..W4 [members][3][256][256]
     float* wscale = nullptr;            // their per-row scales [members][3][256]
     float* wscale_half = nullptr;       // the scales halved (the fused epilogue's multipliers)
@@ -233,16 +237,26 @@ __global__ void slices_reduce(const float* __restrict__ part, float* grad, long 
     }
 }
 
-// grad W[o][i] = sum over splits of part[split][o][i]
-__global__ void split_reduce(const float* __restrict__ part, float* grad, long long off_w, int cols, int splits)
+// grad W[o][i] = sum over splits of part[split][o][i], added in split order; four
+// consecutive elements per thread (member m's partials start at part + m * mstride,
+// partial q at + q * qstride; both strides multiples of 4)
+__global__ void split_reduce(const float* __restrict__ part, float* grad, long long off_w, int cols, int splits,
+                             long long mstride, long long qstride)
 {
     const int mem = blockIdx.y;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (e >= WID * cols) return;
-    const float* p = part + (long long)mem * KSPLIT * WID * WID;
-    float s = 0.0f;
-    for (int q = 0; q < splits; ++q) s += p[(long long)q * WID * WID + e];
-    grad[mem * P + off_w + e] = s;
+    const float* p = part + (long long)mem * mstride + e;
+    float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 8
+    for (int q = 0; q < splits; ++q) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p + (long long)q * qstride));
+        s.x += t.x;
+        s.y += t.y;
+        s.z += t.z;
+        s.w += t.w;
+    }
+    *reinterpret_cast<float4*>(grad + mem * P + off_w + e) = s;
 }
 
 // Adam on FP32 master weights, then the BF16 copies of W1..W4.
@@ -604,6 +618,51 @@ int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaS
     return TUNE_OK;
 }
 
+// Weight gradient of layer l on tcgen05 (tc_wgrad.cuh): one CTA per (batch split, member)
+// with both operands MN-major, then the split reduction into grad.
+int wgrad_tc(tune_surrogate* h, int l, int n_pad, const __nv_bfloat16* dz, cudaStream_t s)
+{
+    const int kin = (int)fan_in(l), M = h->members;
+    const int chunks = n_pad / tcw::kChunkRows;
+    // default: half the SMs per member (measured: 15 splits of an 8,192-row batch for 5 members
+    // beat 30, whose partials cost more to reduce than the extra CTAs gain)
+    int splits = h->wgrad_splits > 0 ? h->wgrad_splits : tune::device_sm_count() / (2 * M);
+    splits = std::max(1, std::min(std::min(splits, chunks), h->part_slices / M));
+    CUtensorMap ta, tb;
+    const auto u64 = CU_TENSOR_MAP_DATA_TYPE_UINT64;
+    const cuuint32_t box[3] = {16, tcw::kChunkRows, 1};
+    const cuuint64_t da[3] = {WID * 2 / 8, (cuuint64_t)n_pad, (cuuint64_t)M};
+    const cuuint64_t sa[2] = {WID * 2, (cuuint64_t)h->batch * WID * 2};
+    int rc = make_map_nd(&ta, u64, 3, dz, da, sa, box);
+    if (rc) return rc;
+    if (l == 0) {
+        const cuuint64_t db[3] = {IN * 2 / 8, (cuuint64_t)n_pad, 1};
+        const cuuint64_t sb[2] = {IN * 2, (cuuint64_t)n_pad * IN * 2};
+        rc = make_map_nd(&tb, u64, 3, h->xin, db, sb, box);
+    } else {
+        rc = make_map_nd(&tb, u64, 3, h->H[l - 1], da, sa, box);
+    }
+    if (rc) return rc;
+    tcw::Args g;
+    g.kin = kin;
+    g.chunks = chunks;
+    g.splits = splits;
+    g.part = h->part;
+    g.status = h->status;
+    static bool attr = false;
+    if (!attr) {
+        TUNE_CUDA_TRY(cudaFuncSetAttribute(tcw::wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcw::kSmem),
+                      "surrogate: weight-gradient smem attribute");
+        attr = true;
+    }
+    tcw::wgrad_kernel<<<dim3(splits, M), tcw::kThreads, tcw::kSmem, s>>>(ta, tb, g, l != 0);
+    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: weight-gradient launch");
+    split_reduce<<<dim3((WID * kin / 4 + 255) / 256, M), 256, 0, s>>>(h->part, h->grad, OFF_W(l), kin, splits,
+                                                                  (long long)splits * WID * kin, (long long)WID * kin);
+    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: split reduce launch");
+    return TUNE_OK;
+}
+
 // Forward through all members for rows [0, n_pad) of h->xin (n_pad a multiple of 128).
 // x_in: layer-1 input rows (h->xin, or the caller's features on the tcgen05 path);
 // n_valid rows of it exist; store_z keeps the pre-activations for a backward pass.
@@ -646,6 +705,37 @@ int forward(tune_surrogate* h, int n_pad, cudaStream_t s, const __nv_bfloat16* x
 }
 
 // Backward for the batch in h->xin / h->lbl (n valid rows, n_pad rows computed); grads into h->grad.
+// Weight gradient of layer l as a split-K mma.sync GEMM (mlp_gemm.cuh) and its reduction into grad.
+int wgrad_mma(tune_surrogate* h, int l, int n_pad, const __nv_bfloat16* dz, cudaStream_t s)
+{
+    const int B = h->batch;
+    const int kin = (int)fan_in(l);
+    GemmArgs g = gargs();
+    g.A = dz;
+    g.sA = (long long)B * WID;
+    g.lda = WID;
+    g.B = l == 0 ? h->xin : h->H[l - 1];
+    g.sB = l == 0 ? 0 : (long long)B * WID;
+    g.ldb = kin;
+    g.M = WID;
+    g.N = kin;
+    g.K = n_pad;
+    g.F = h->part;
+    g.sF = (long long)KSPLIT * WID * WID;
+    g.ldc = kin;
+    // split the batch (K) so every split is a multiple of 32 rows: n_pad / 32 is a multiple of 4
+    int splits = KSPLIT;
+    while ((n_pad / 32) % splits) splits >>= 1;
+    g.k_split = splits;
+    g.sSplit = (long long)WID * WID;
+    const int rc = gemm<true, true, mlp::EPI_F32>(g, h->members, s);
+    if (rc) return rc;
+    split_reduce<<<dim3((WID * kin / 4 + 255) / 256, h->members), 256, 0, s>>>(
+        h->part, h->grad, OFF_W(l), kin, splits, (long long)KSPLIT * WID * WID, (long long)WID * WID);
+    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: split reduce launch");
+    return TUNE_OK;
+}
+
 int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
 {
     const int B = h->batch;
@@ -671,28 +761,13 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
         const __nv_bfloat16* dz = dzl[l];
         const int kin = (int)fan_in(l);
         // weight gradient: dW[o][i] = sum_r dZ[r][o] * Hprev[r][i]   (split over the batch)
-        GemmArgs g = gargs();
-        g.A = dz;
-        g.sA = (long long)B * WID;
-        g.lda = WID;
-        g.B = l == 0 ? h->xin : h->H[l - 1];
-        g.sB = l == 0 ? 0 : (long long)B * WID;
-        g.ldb = kin;
-        g.M = WID;
-        g.N = kin;
-        g.K = n_pad;
-        g.F = h->part;
-        g.sF = (long long)KSPLIT * WID * WID;
-        g.ldc = kin;
-        // split the batch (K) so every split is a multiple of 32 rows: n_pad / 32 is a multiple of 4
-        int splits = KSPLIT;
-        while ((n_pad / 32) % splits) splits >>= 1;
-        g.k_split = splits;
-        g.sSplit = (long long)WID * WID;
-        int rc = gemm<true, true, mlp::EPI_F32>(g, h->members, s);
-        if (rc) return rc;
-        split_reduce<<<dim3((WID * kin + 255) / 256, h->members), 256, 0, s>>>(h->part, h->grad, OFF_W(l), kin,
-                                                                               splits);
+        if (fused) {
+            const int rc = wgrad_tc(h, l, n_pad, dz, s);
+            if (rc) return rc;
+        } else {
+            const int rc = wgrad_mma(h, l, n_pad, dz, s);
+            if (rc) return rc;
+        }
         bias_partial<<<dim3(slices, h->members), WID, 0, s>>>(dz, h->part, n_pad, B, slices);
         slices_reduce<<<dim3(WID / 32, h->members), 256, 0, s>>>(h->part, h->grad, OFF_B(l), WID, slices);
         TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: reduce launch");
@@ -713,7 +788,7 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
         d.H = dzl[l - 1];
         d.sH = (long long)B * WID;
         d.ldc = WID;
-        rc = gemm<false, true, mlp::EPI_GELU_GRAD>(d, h->members, s);
+        const int rc = gemm<false, true, mlp::EPI_GELU_GRAD>(d, h->members, s);
         if (rc) return rc;
     }
     return TUNE_OK;
@@ -765,6 +840,11 @@ int surrogate_set_option(tune_surrogate* h, int option, int value)
         h->bwd_mode = value;
         return TUNE_OK;
     }
+    if (option == 3) {
+        if (value < 0 || value > 1024) return tune::fail(TUNE_EINVAL, "surrogate_set_option: splits outside 0..1024");
+        h->wgrad_splits = value;
+        return TUNE_OK;
+    }
     return tune::fail(TUNE_EINVAL, "surrogate_set_option: unknown option %d", option);
 }
 
@@ -806,7 +886,8 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     add(M * B * 4);
     add(B * 4);
     add(M * 4);
-    add(M * KSPLIT * WID * WID * 4);
+    const size_t part_slices = std::max<size_t>(M * KSPLIT, (size_t)tune::device_sm_count());
+    add(part_slices * WID * WID * 4);
     add(256);
     add(M * (NL - 1) * WID * WID);
     add(M * (NL - 1) * WID * 4);
@@ -832,7 +913,8 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     h->dy = carve<float>(p, M * B);
     h->lbl = carve<float>(p, B);
     h->loss = carve<float>(p, M);
-    h->part = carve<float>(p, M * KSPLIT * WID * WID);
+    h->part = carve<float>(p, part_slices * WID * WID);
+    h->part_slices = (int)part_slices;
     h->status = carve<int>(p, 64);
     h->w8 = carve<uint8_t>(p, M * (NL - 1) * WID * WID);
     h->wscale = carve<float>(p, M * (NL - 1) * WID);

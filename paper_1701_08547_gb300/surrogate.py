@@ -90,9 +90,14 @@ class Surrogate:
         self.set_option(1, mode)
 
     def set_backward_mode(self, mode):
-        """Input gradients of layers 4, 3 and 2: one GEMM per layer (0) or one fused
-        tcgen05 launch for the chain (1, the default; needs the tcgen05 option)."""
+        """Backward pass: one mma.sync GEMM per input and weight gradient (0), or the fused
+        tcgen05 input-gradient chain and tcgen05 weight gradients (1, the default; needs
+        the tcgen05 option)."""
         self.set_option(2, mode)
+
+    def set_wgrad_splits(self, splits):
+        """Batch splits per member of the tcgen05 weight gradients (0: SMs / (2 members))."""
+        self.set_option(3, splits)
 
     def check(self):
         native.check(self.L.surrogate_status(self.h))
