@@ -580,6 +580,7 @@ int fused_train_forward(tune_surrogate* h, int n_pad, cudaStream_t s)
 // dz[l - 1] = bf16((dz[l] W_l) * gelu'(Z[l - 1])) for l = 3, 2, 1 (0-based), rows [0, n_pad).
 int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaStream_t s)
 {
+    if (n_pad % tcm::kRows) return tune::fail(TUNE_EINVAL, "surrogate: fused backward needs whole 128-row tiles");
     transpose_weights<<<dim3(WID / 32, WID / 32, (NL - 1) * h->members), dim3(32, 8), 0, s>>>(h->wbf, h->wbfT);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: transpose launch");
     CUtensorMap tdz, twt;

@@ -164,6 +164,22 @@ __device__ __forceinline__ void ld16(const float* p, float (&x)[16])
     }
 }
 
+// 256-bit global store of eight 32-bit words (address 32-byte aligned).
+__device__ __forceinline__ void st_global_v8(void* p, const uint32_t (&w)[8])
+{
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"l"(p), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
+// 256-bit global load of eight floats (address 32-byte aligned; data not written by this kernel).
+__device__ __forceinline__ void ld_global_v8(const float* p, float* x)
+{
+    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                 : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
+                 : "l"(p));
+}
+
 // 16 consecutive accumulator columns of this thread's TMEM lane (row), then the wait.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
@@ -362,10 +378,13 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                         for (int i = 0; i < 16; ++i) v[i] = fmaf(v[i], f8 ? ss[i] : acc_mul, bb[i]);
                         const long long arow = (long long)mem * g.act_stride + (long long)(tile * kRows + r) * kWid + n0;
                         if (TRAIN && !FP8 && g.z_out[l]) {  // training: keep z for the backward pass
-                            float4* zo = reinterpret_cast<float4*>(g.z_out[l] + arow);
 #pragma unroll
-                            for (int i = 0; i < 4; ++i)
-                                zo[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                            for (int i = 0; i < 2; ++i) {
+                                uint32_t w[8];
+#pragma unroll
+                                for (int t = 0; t < 8; ++t) w[t] = __float_as_uint(v[8 * i + t]);
+                                st_global_v8(g.z_out[l] + arow + 8 * i, w);
+                            }
                         }
                         // 2 gelu(z) = z (1 + tanh u) in FP32: one multi-function-unit tanh per element
 #pragma unroll
@@ -383,13 +402,10 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                         }
                         if (TRAIN && !FP8 && g.h_out[l]) {
                             // training: h = bf16(gelu(z)) = bf16(2 gelu(z)) / 2 exactly
-                            uint4* ho = reinterpret_cast<uint4*>(g.h_out[l] + arow);
+                            uint32_t w[8];
 #pragma unroll
-                            for (int hh = 0; hh < 2; ++hh) {
-                                const float* x = v + 8 * hh;
-                                ho[hh] = make_uint4(pack_bf16(0.5f * x[0], 0.5f * x[1]), pack_bf16(0.5f * x[2], 0.5f * x[3]),
-                                                    pack_bf16(0.5f * x[4], 0.5f * x[5]), pack_bf16(0.5f * x[6], 0.5f * x[7]));
-                            }
+                            for (int t = 0; t < 8; ++t) w[t] = pack_bf16(0.5f * v[2 * t], 0.5f * v[2 * t + 1]);
+                            st_global_v8(g.h_out[l] + arow, w);
                         }
                         if (head) {
                             // head on 2 h4; the sum is halved with b5 added below

@@ -27,7 +27,7 @@ namespace tcm {
 constexpr int kBwdStages = kLayers - 1;  // products with W4, W3, W2
 
 struct BwdArgs {
-    int rows;                         // rows per member (a multiple of 128)
+    int rows;                         // rows per member (a multiple of 128: every unit's rows exist)
     int members;
     long long units;                  // rows / 128 * members
     const float* z[kBwdStages];       // stage j: Z_{3-j}, [members][act_stride]
@@ -35,6 +35,13 @@ struct BwdArgs {
     long long act_stride;             // member stride of z and dz (elements); rows of 256
     int* status;
 };
+
+// 16 pre-activations of a row; 32-byte aligned.
+__device__ __forceinline__ void load_z(const float* p, float (&z)[16])
+{
+    ld_global_v8(p, z);
+    ld_global_v8(p + 8, z + 8);
+}
 
 // grid: min(SMs, units) persistent CTAs; CTA b runs units b, b + gridDim.x, ...; its
 // j-th unit goes to chain j % 2. Unit u = (tile u / members, member u % members).
@@ -106,6 +113,16 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
                                 tc::tma_load_3d(act + c * kChunkA, &tdz, c * 16, tile * kRows, mem, &x_full[s]);
                             x_last[s] = jj;
                         }
+                        {
+                            // the epilogue of this (unit, stage) reads a 128 KB tile of
+                            // pre-activations: request it into L2 while the MMAs run
+                            const char* zt = reinterpret_cast<const char*>(
+                                g.z[l] + (long long)mem * g.act_stride + (long long)tile * kRows * kWid);
+                            for (int q = 0; q < 4; ++q)
+                                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(zt + q * 32768),
+                                             "r"(32768)
+                                             : "memory");
+                        }
                         for (int c = 0; c < kChunks; ++c, ++seq) {
                             const int st = (int)(seq % C::stages);
                             const long long use = seq / C::stages;
@@ -174,7 +191,7 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
         // stage, to the chain's activation buffer as the next product's A operand ----
         const int e = warp - 2, q = warp & 3, cq = e >> 2;
         const int r = q * 32 + lane;
-        const int c_beg = cq * (kWid / 4), c_end = c_beg + kWid / 4;
+        const int c_beg = cq * (kWid / 4);
         bool ok = true;
         for (long long j = 0; j < my_units && ok; j += 2) {
             for (int l = 0; l < kBwdStages && ok; ++l) {
@@ -186,36 +203,32 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
                     const long long u = blockIdx.x + jj * gridDim.x;
                     const int tile = (int)(u / g.members), mem = (int)(u % g.members);
                     const int row = tile * kRows + r;
-                    const bool live = row < g.rows;
                     const long long arow = (long long)mem * g.act_stride + (long long)row * kWid;
                     const float* zr = g.z[l] + arow;
                     __nv_bfloat16* dzr = g.dz[l] + arow;
                     uint8_t* act = smem + s * C::act_bytes;
                     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * kWid);
                     const bool last = l == kBwdStages - 1;
+                    // pre-activations of two 16-column blocks in flight: the first two are
+                    // requested before the accumulator wait, each later one when a buffer frees
+                    float zb[2][16];
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) load_z(zr + c_beg + 16 * b, zb[b]);
                     if (!(ok = wait_bar(&acc_full[s], (uint32_t)((kBwdStages * k + l) & 1), g.status, abort_v)))
                         break;
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    for (int n0 = c_beg; n0 < c_end; n0 += 16) {
-                        float zz[16];
-                        if (live) {
-                            ld16(zr + n0, zz);
-                        } else {
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) zz[i] = 0.0f;
-                        }
+                    for (int b = 0; b < kWid / 4 / 16; ++b) {
+                        const int n0 = c_beg + 16 * b;
                         float v[16];
                         tmem_ld16(taddr + (uint32_t)n0, v);
                         uint32_t w[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
-                            w[i] = pack_bf16(v[2 * i] * mlp::gelu_grad(zz[2 * i]),
-                                             v[2 * i + 1] * mlp::gelu_grad(zz[2 * i + 1]));
-                        if (live) {
-                            uint4* o = reinterpret_cast<uint4*>(dzr + n0);
-                            o[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                            o[1] = make_uint4(w[4], w[5], w[6], w[7]);
-                        }
+                            w[i] = pack_bf16(v[2 * i] * mlp::gelu_grad(zb[b & 1][2 * i]),
+                                             v[2 * i + 1] * mlp::gelu_grad(zb[b & 1][2 * i + 1]));
+                        if (b + 2 < kWid / 4 / 16) load_z(zr + n0 + 32, zb[b & 1]);
+                        st_global_v8(dzr + n0, w);
                         if (!last) {
                             // 16 columns = two 16-byte units of K chunk n0 / 64
                             uint8_t* base = act + (n0 >> 6) * kChunkA;
