@@ -239,11 +239,21 @@ __global__ void slices_reduce(const float* __restrict__ part, float* grad, long 
 
 // grad W[o][i] = sum over splits of part[split][o][i], added in split order; four
 // consecutive elements per thread (member m's partials start at part + m * mstride,
-// partial q at + q * qstride; both strides multiples of 4)
+// partial q at + q * qstride; both strides multiples of 4). With bpart, the grid has
+// one more block (256 threads), which forms the bias gradient grad b[o] = sum over the
+// brows rows of bpart[m][.][o], in row order.
 __global__ void split_reduce(const float* __restrict__ part, float* grad, long long off_w, int cols, int splits,
-                             long long mstride, long long qstride)
+                             long long mstride, long long qstride, const float* __restrict__ bpart = nullptr,
+                             long long off_b = 0, int brows = 0)
 {
     const int mem = blockIdx.y;
+    if (bpart && blockIdx.x == gridDim.x - 1) {
+        const float* b = bpart + (long long)mem * brows * WID + threadIdx.x;
+        float s = 0.0f;
+        for (int q = 0; q < brows; ++q) s += b[(long long)q * WID];
+        grad[mem * P + off_b + threadIdx.x] = s;
+        return;
+    }
     const int e = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (e >= WID * cols) return;
     const float* p = part + (long long)mem * mstride + e;
@@ -619,8 +629,8 @@ int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaS
     return TUNE_OK;
 }
 
-// Weight gradient of layer l on tcgen05 (tc_wgrad.cuh): one CTA per (batch split, member)
-// with both operands MN-major, then the split reduction into grad.
+// Weight and bias gradients of layer l on tcgen05 (tc_wgrad.cuh): one CTA per (batch
+// split, member) with both operands MN-major, then the split reduction into grad.
 int wgrad_tc(tune_surrogate* h, int l, int n_pad, const __nv_bfloat16* dz, cudaStream_t s)
 {
     const int kin = (int)fan_in(l), M = h->members;
@@ -628,7 +638,10 @@ int wgrad_tc(tune_surrogate* h, int l, int n_pad, const __nv_bfloat16* dz, cudaS
     // default: half the SMs per member (measured: 15 splits of an 8,192-row batch for 5 members
     // beat 30, whose partials cost more to reduce than the extra CTAs gain)
     int splits = h->wgrad_splits > 0 ? h->wgrad_splits : tune::device_sm_count() / (2 * M);
-    splits = std::max(1, std::min(std::min(splits, chunks), h->part_slices / M));
+    // the weight partials [M][splits][WID][kin] and the bias partials [M][splits][2][WID]
+    // share the partial buffer
+    const long long cap = (long long)h->part_slices * WID * WID / ((long long)M * WID * (kin + 2));
+    splits = std::max(1, (int)std::min<long long>(std::min(splits, chunks), cap));
     CUtensorMap ta, tb;
     const auto u64 = CU_TENSOR_MAP_DATA_TYPE_UINT64;
     const cuuint32_t box[3] = {16, tcw::kChunkRows, 1};
@@ -649,6 +662,7 @@ int wgrad_tc(tune_surrogate* h, int l, int n_pad, const __nv_bfloat16* dz, cudaS
     g.chunks = chunks;
     g.splits = splits;
     g.part = h->part;
+    g.bpart = h->part + (long long)M * splits * WID * kin;
     g.status = h->status;
     static bool attr = false;
     if (!attr) {
@@ -658,8 +672,9 @@ int wgrad_tc(tune_surrogate* h, int l, int n_pad, const __nv_bfloat16* dz, cudaS
     }
     tcw::wgrad_kernel<<<dim3(splits, M), tcw::kThreads, tcw::kSmem, s>>>(ta, tb, g, l != 0);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: weight-gradient launch");
-    split_reduce<<<dim3((WID * kin / 4 + 255) / 256, M), 256, 0, s>>>(h->part, h->grad, OFF_W(l), kin, splits,
-                                                                  (long long)splits * WID * kin, (long long)WID * kin);
+    split_reduce<<<dim3((WID * kin / 4 + 255) / 256 + 1, M), 256, 0, s>>>(
+        h->part, h->grad, OFF_W(l), kin, splits, (long long)splits * WID * kin, (long long)WID * kin, g.bpart, OFF_B(l),
+        2 * splits);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: split reduce launch");
     return TUNE_OK;
 }
@@ -769,9 +784,11 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
             const int rc = wgrad_mma(h, l, n_pad, dz, s);
             if (rc) return rc;
         }
-        bias_partial<<<dim3(slices, h->members), WID, 0, s>>>(dz, h->part, n_pad, B, slices);
-        slices_reduce<<<dim3(WID / 32, h->members), 256, 0, s>>>(h->part, h->grad, OFF_B(l), WID, slices);
-        TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: reduce launch");
+        if (!fused) {  // the tcgen05 weight-gradient pass forms the bias gradient too
+            bias_partial<<<dim3(slices, h->members), WID, 0, s>>>(dz, h->part, n_pad, B, slices);
+            slices_reduce<<<dim3(WID / 32, h->members), 256, 0, s>>>(h->part, h->grad, OFF_B(l), WID, slices);
+            TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: reduce launch");
+        }
         if (l == 0 || fused) continue;
         // input gradient of layer l, times gelu' of layer l-1: dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1})
         GemmArgs d = gargs();

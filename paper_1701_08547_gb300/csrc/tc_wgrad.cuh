@@ -9,7 +9,9 @@
 //
 // Grid (splits, members): CTA (s, m) sums a contiguous range of 64-row chunks for
 // member m and writes its FP32 partial [256][kin] to part[m][s]; split_reduce adds
-// the partials in split order (deterministic). A CTA keeps both 128-row halves of the
+// the partials in split order (deterministic). The bias gradient db_l[o] = sum over r
+// of dZ_l[r][o] comes from the same pass: the epilogue warps, idle until the last MMA,
+// add up each stage's dZ columns from shared memory before the stage is released. A CTA keeps both 128-row halves of the
 // output in tensor memory (2 x 256 columns), so each chunk of dZ and Hprev is read
 // once. Roles: warp 0 issues the TMA copies through a ring of three 64 KB stages,
 // warp 1 issues the MMAs (per 16-row K step, one per output half), warps 2-9 read the
@@ -41,6 +43,7 @@ struct Args {
     int chunks;       // batch rows / 64
     int splits;       // CTAs per member; split s sums chunks [s chunks / splits, (s + 1) chunks / splits)
     float* part;      // [members][splits][256][kin]
+    float* bpart;     // [members][splits][2][256]: column sums of dZ over the split's rows, two row halves
     int* status;
 };
 
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
     if (threadIdx.x == 32) {
         for (int i = 0; i < kStages; ++i) {
             tc::mbar_init(&full[i], 1);
-            tc::mbar_init(&empty[i], 1);
+            tc::mbar_init(&empty[i], 1 + kEpiWarps);  // the MMAs' commit and each epilogue warp
         }
         tc::mbar_init(&acc_full, 1);
         tc::mbar_init(&drain, 1);
@@ -148,7 +151,36 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
             tc::mbar_wait(&drain, 0, g.status);
         }
     } else {
-        // ---- epilogue: partial[o][c] for o = h 128 + q 32 + lane ----
+        // ---- epilogue warps, while the MMAs run: column sums of dZ (the bias gradient) from
+        // each stage's dZ boxes; thread et sums columns o, o + 1 (o = 2 (et % 128)) over rows
+        // 32 (et / 128) .. + 31 of every chunk, then releases the stage with its warp ----
+        const int et = threadIdx.x - 64;
+        const int bo = 2 * (et & 127), rh = et >> 7;
+        {
+            float s0 = 0.0f, s1 = 0.0f;
+            const int unit = (bo & 63) >> 3, byte = (bo & 7) * 2;
+            for (int i = 0; i < n; ++i) {
+                const int st = i % kStages;
+                if (!tcm::wait_bar(&full[st], (uint32_t)((i / kStages) & 1), g.status, abort_v)) break;
+                const uint8_t* box = smem + st * kStage + (bo >> 6) * kBox;
+#pragma unroll 8
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int r = 32 * rh + rr;
+                    // 128-byte swizzle: 16-byte unit u of row r sits at unit u ^ (r % 8)
+                    const uint32_t w = *reinterpret_cast<const uint32_t*>(box + r * 128 + ((unit ^ (r & 7)) << 4) + byte);
+                    s0 += __uint_as_float(w << 16);
+                    s1 += __uint_as_float(w & 0xffff0000u);
+                }
+                __syncwarp();
+                if (lane == 0) tcm::mbar_arrive(&empty[st]);
+            }
+            *reinterpret_cast<float2*>(g.bpart + (((long long)mem * g.splits + split) * 2 + rh) * 256 + bo) =
+                make_float2(s0, s1);
+        }
+        // the accumulator read-back below reuses the stage ring: every epilogue warp has
+        // finished reading it (all 256 epilogue threads reach this barrier once, on every path)
+        asm volatile("bar.sync 1, %0;\n" ::"n"(32 * kEpiWarps) : "memory");
+        // ---- then partial[o][c] for o = h 128 + q 32 + lane ----
         const int e = warp - 2, q = warp & 3, ch = e >> 2;
         const int ncol = g.kin / 2, col0 = ch * ncol;
         float* out = g.part + ((long long)mem * g.splits + split) * 256 * g.kin;
