@@ -38,6 +38,7 @@ WORKLOADS = {
     "uneven": (1_000_000, "uneven", 5, 3),
     "topk": (100_000, None, 10, 11),
     "surfwd": (1 << 20, None, 0, 12),
+    "surtrain": (1 << 16, None, 0, 13),
     "search": (100_000, "dense", 1, 2),
 }
 ISSUE_LANES_PER_SM_CLK = 4 * 32  # 4 schedulers x 32 lanes per SM and clock
@@ -496,6 +497,81 @@ def run_surfwd(args):
             "paths": out}
 
 
+def train_step_bytes(rows, members):
+    """Algorithmic HBM bytes of one training step of the tcgen05 path (what the design must
+    move): forward X read, Z (FP32) and H (BF16) of four layers written; head backward Z4 and
+    H4 read, dZ4 written; fused input gradients dZ4 and Z3..Z1 read, dZ3..dZ1 written; weight
+    gradients dZ of four layers and their inputs (H1..H3, X) read; Adam over the parameters
+    (master, gradient and both moments read, master, moments and the BF16 copy written)."""
+    from workloads import mlp as L
+
+    act = rows * members * L.WID  # elements of one layer's activations
+    x = rows * 128 * 2
+    fwd = x + 4 * act * 4 + 4 * act * 2
+    head = act * 4 + act * 2 + act * 2
+    bwd = act * 2 + 3 * act * 4 + 3 * act * 2
+    wgrad = 4 * act * 2 + 3 * act * 2 + x
+    adam = members * L.P * (16 + 14)
+    return fwd + head + bwd + wgrad + adam
+
+
+def run_surtrain(args):
+    """Surrogate training throughput: 5 members, 8,192-row batches of 65,536 synthetic rows
+    (48 standard-normal features zero-padded to 128, standard-normal labels), one step =
+    forward, MSE loss, backward and Adam for every member (tcgen05 path), CUDA events per
+    step; against the HBM roofline of the step's algorithmic bytes (the step moves far more
+    bytes than its 0.2 TFLOP needs tensor time for)."""
+    import torch
+
+    from paper_1701_08547_gb300 import build as B
+    from paper_1701_08547_gb300.surrogate import Surrogate
+    from workloads import mlp as L
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    members, batch = 5, 8192
+    n = args.kernels or (1 << 16)
+    n -= n % batch
+    sur = Surrogate(members=members, batch=batch)
+    sur.set_params(L.init_params(members))
+    g = torch.Generator(device=dev)
+    g.manual_seed(13)
+    X = torch.zeros(n, 128, device=dev)
+    X[:, :L.FEATURES] = torch.randn(n, L.FEATURES, generator=g, device=dev)
+    X = X.to(torch.bfloat16)
+    y = torch.randn(n, generator=g, device=dev)
+    nb = n // batch
+
+    def step(i):
+        b = i % nb
+        sur.train_step(X[b * batch:(b + 1) * batch], y[b * batch:(b + 1) * batch], apply_update=True)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    for i in range(args.steps):
+        ev[2 * i].record()
+        step(args.warmup + i)
+        ev[2 * i + 1].record()
+    torch.cuda.synchronize()
+    sur.check()
+    ms = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)) / args.steps
+    peaks, kind = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bytes_step = train_step_bytes(batch, members)
+    gbs = bytes_step / (ms * 1e-3) / 1e9
+    tflops = batch * members * MLP_TRAIN_FLOP / (ms * 1e-3) / 1e12
+    return {"metric": "surrogate training samples/sec (5 members)", "value": batch / (ms * 1e-3),
+            "unit": "samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"surtrain: {n} rows in {batch}-row steps x {members} members, "
+                                   "128 -> 256 x 4 -> 1, tcgen05 forward and backward, Adam"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "traffic": None, "algorithmic_bytes_per_step": bytes_step, "peak_source": kind},
+            "tflops": tflops, "frac_bf16_peak": tflops / peaks.get("bf16_tflops", 1900.0)}
+
+
 def run_search(args):
     """Random and Nelder-Mead search per kernel with the static cost as the objective, over
     the full space and over the statically pruned one (T*): kernels searched per second and
@@ -708,6 +784,8 @@ def main():
         line = run_topk(args)
     elif args.workload == "surfwd":
         line = run_surfwd(args)
+    elif args.workload == "surtrain":
+        line = run_surtrain(args)
     elif args.workload == "search":
         line = run_search(args)
     else:
