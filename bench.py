@@ -499,17 +499,18 @@ def run_surfwd(args):
 
 def train_step_bytes(rows, members):
     """Algorithmic HBM bytes of one training step of the tcgen05 path (what the design must
-    move): forward X read, Z (FP32) and H (BF16) of four layers written; head backward Z4 and
-    H4 read, dZ4 written; fused input gradients dZ4 and Z3..Z1 read, dZ3..dZ1 written; weight
-    gradients dZ of four layers and their inputs (H1..H3, X) read; Adam over the parameters
-    (master, gradient and both moments read, master, moments and the BF16 copy written)."""
+    move): forward X read, G = gelu'(Z) (FP16) and H (BF16) of four layers written; head
+    backward G4 and H4 read, dZ4 written; fused input gradients dZ4 and G3..G1 read, dZ3..dZ1
+    written; weight gradients dZ of four layers and their inputs (H1..H3, X) read; Adam over
+    the parameters (master, gradient and both moments read, master, moments and the BF16 copy
+    written)."""
     from workloads import mlp as L
 
     act = rows * members * L.WID  # elements of one layer's activations
     x = rows * 128 * 2
-    fwd = x + 4 * act * 4 + 4 * act * 2
-    head = act * 4 + act * 2 + act * 2
-    bwd = act * 2 + 3 * act * 4 + 3 * act * 2
+    fwd = x + 4 * act * 2 + 4 * act * 2
+    head = act * 2 + act * 2 + act * 2
+    bwd = act * 2 + 3 * act * 2 + 3 * act * 2
     wgrad = 4 * act * 2 + 3 * act * 2 + x
     adam = members * L.P * (16 + 14)
     return fwd + head + bwd + wgrad + adam

@@ -29,12 +29,17 @@ __device__ __forceinline__ float gelu(float z)
     return fmaf(hz, t, hz);
 }
 
+// gelu'(z) from z, z^2 and t = tanh(u) (shared with gelu(z) where both are formed)
+__device__ __forceinline__ float gelu_grad_t(float z, float z2, float t)
+{
+    const float du = kGeluK * fmaf(3.0f * kGeluC, z2, 1.0f);
+    return fmaf(0.5f * z * du, fmaf(-t, t, 1.0f), 0.5f * (1.0f + t));
+}
+
 __device__ __forceinline__ float gelu_grad(float z)
 {
     const float z2 = z * z;
-    const float t = tanh_hw(gelu_u(z, z2));
-    const float du = kGeluK * fmaf(3.0f * kGeluC, z2, 1.0f);
-    return fmaf(0.5f * z * du, fmaf(-t, t, 1.0f), 0.5f * (1.0f + t));
+    return gelu_grad_t(z, z2, tanh_hw(gelu_u(z, z2)));
 }
 
 }  // namespace mlp

@@ -13,6 +13,7 @@
 #include "gelu.cuh"
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 namespace mlp {
@@ -21,8 +22,8 @@ constexpr int GBM = 128, GBN = 128, GBK = 32;
 constexpr int kGemmThreads = 256;
 
 enum Epilogue : int {
-    EPI_BIAS_GELU = 0,  // z = acc + bias[n]; Z[m][n] = z (fp32, optional); H[m][n] = bf16(gelu(z))
-    EPI_GELU_GRAD = 1,  // D[m][n] = bf16(acc * gelu'(Z[m][n]))
+    EPI_BIAS_GELU = 0,  // z = acc + bias[n]; G[m][n] = fp16(gelu'(z)) (optional); H[m][n] = bf16(gelu(z))
+    EPI_GELU_GRAD = 1,  // D[m][n] = bf16(acc * G[m][n])
     EPI_F32 = 2,        // F[m][n] = acc (fp32)
 };
 
@@ -34,13 +35,13 @@ struct GemmArgs {
     // epilogue operands (per-batch strides in elements)
     const float* bias;
     long long sBias;
-    float* Z;          // EPI_BIAS_GELU: pre-activation out (may be null); EPI_GELU_GRAD: pre-activation in
-    long long sZ;
+    __half* G;         // EPI_BIAS_GELU: gelu'(pre-activation) out (may be null); EPI_GELU_GRAD: its input
+    long long sG;
     __nv_bfloat16* H;  // bf16 output
     long long sH;
     float* F;          // fp32 output
     long long sF;
-    int ldc;           // leading dimension of Z / H / F
+    int ldc;           // leading dimension of G / H / F
     int k_split;       // split-K: blockIdx.z = batch * k_split + split; F gets [split] slices
     long long sSplit;  // stride between split slices of F
 };
@@ -213,13 +214,15 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(const __grid_co
                 if (EPI == EPI_BIAS_GELU) {
                     const float z0 = v0 + g.bias[batch * g.sBias + n];
                     const float z1 = v1 + g.bias[batch * g.sBias + n + 1];
-                    if (g.Z) *reinterpret_cast<float2*>(g.Z + batch * g.sZ + off) = make_float2(z0, z1);
+                    if (g.G)
+                        *reinterpret_cast<__half2*>(g.G + batch * g.sG + off) =
+                            __floats2half2_rn(gelu_grad(z0), gelu_grad(z1));
                     *reinterpret_cast<__nv_bfloat162*>(g.H + batch * g.sH + off) =
                         __floats2bfloat162_rn(gelu(z0), gelu(z1));
                 } else if (EPI == EPI_GELU_GRAD) {
-                    const float2 z = *reinterpret_cast<const float2*>(g.Z + batch * g.sZ + off);
+                    const float2 d = __half22float2(*reinterpret_cast<const __half2*>(g.G + batch * g.sG + off));
                     *reinterpret_cast<__nv_bfloat162*>(g.H + batch * g.sH + off) =
-                        __floats2bfloat162_rn(v0 * gelu_grad(z.x), v1 * gelu_grad(z.y));
+                        __floats2bfloat162_rn(v0 * d.x, v1 * d.y);
                 } else {
                     *reinterpret_cast<float2*>(g.F + batch * g.sF + split * g.sSplit + off) = make_float2(v0, v1);
                 }

@@ -51,7 +51,7 @@ struct tune_surrogate {
     float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     __nv_bfloat16* wbf = nullptr;
     __nv_bfloat16* xin = nullptr;       // [batch x IN]
-    float* Z[NL] = {};                  // [members][batch x WID]
+    __half* G[NL] = {};                 // gelu' of each layer's pre-activations, FP16 [members][batch x WID]
     __nv_bfloat16* H[NL] = {};          // [members][batch x WID]
     __nv_bfloat16* dZ[NL] = {};         // [members][batch x WID]: dZ of layer l (fused chain) or ping-pong
     __nv_bfloat16* wbfT = nullptr;      // W2..W4 transposed, [members][3][WID][WID] (fused input gradients)
@@ -144,9 +144,9 @@ __global__ void loss_reduce(const float* __restrict__ lpart, float* loss, int bl
     loss[mem] = s / (float)n;
 }
 
-// dZ4[i][j] = bf16(dy[i] * w5[j] * gelu'(Z4[i][j])), eight columns per thread
+// dZ4[i][j] = bf16(dy[i] * w5[j] * G4[i][j]) with G4 = gelu'(Z4) (FP16), eight columns per thread
 __global__ void head_bwd_act(const float* __restrict__ dy, const float* __restrict__ master,
-                             const float* __restrict__ Z4, __nv_bfloat16* dZ, int batch)
+                             const __half* __restrict__ G4, __nv_bfloat16* dZ, int batch)
 {
     const int mem = blockIdx.y;
     const long long e = 8 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
@@ -155,15 +155,15 @@ __global__ void head_bwd_act(const float* __restrict__ dy, const float* __restri
     const long long o = (long long)mem * batch * WID + e;
     const float d = dy[(long long)mem * batch + i];
     const float* w5 = master + mem * P + OFF_W5 + j;
-    const float4 za = *reinterpret_cast<const float4*>(Z4 + o), zb = *reinterpret_cast<const float4*>(Z4 + o + 4);
+    const uint4 gv = *reinterpret_cast<const uint4*>(G4 + o);
+    const __half2* g2 = reinterpret_cast<const __half2*>(&gv);
     const float4 wa = *reinterpret_cast<const float4*>(w5), wb = *reinterpret_cast<const float4*>(w5 + 4);
-    const float z[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
     const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
     uint32_t out[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const __nv_bfloat162 b2 = __floats2bfloat162_rn(d * w[2 * q] * mlp::gelu_grad(z[2 * q]),
-                                                        d * w[2 * q + 1] * mlp::gelu_grad(z[2 * q + 1]));
+        const float2 gd = __half22float2(g2[q]);
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(d * w[2 * q] * gd.x, d * w[2 * q + 1] * gd.y);
         out[q] = *reinterpret_cast<const uint32_t*>(&b2);
     }
     *reinterpret_cast<uint4*>(dZ + o) = make_uint4(out[0], out[1], out[2], out[3]);
@@ -408,7 +408,7 @@ int make_map(CUtensorMap* map, const void* base, uint64_t K, uint64_t rows, uint
     return TUNE_OK;
 }
 
-// One forward layer for every member: H = gelu(A W^T + b) (and Z = A W^T + b) with tcgen05.
+// One forward layer for every member: H = gelu(A W^T + b) (and G = gelu'(A W^T + b)) with tcgen05.
 int tc_layer(tune_surrogate* h, int l, int n_pad, cudaStream_t s, const __nv_bfloat16* x_in, int n_valid,
              bool store_z)
 {
@@ -429,8 +429,8 @@ int tc_layer(tune_surrogate* h, int l, int n_pad, cudaStream_t s, const __nv_bfl
     g.batched_a = l != 0;
     g.bias = h->master + OFF_B(l);
     g.sBias = P;
-    g.Z = store_z ? h->Z[l] : nullptr;
-    g.sZ = (long long)h->batch * WID;
+    g.G = store_z ? h->G[l] : nullptr;
+    g.sG = (long long)h->batch * WID;
     g.H = h->H[l];
     g.sH = (long long)h->batch * WID;
     g.status = h->status;
@@ -533,7 +533,7 @@ int fused_forward(tune_surrogate* h, const __nv_bfloat16* feats, int64_t n, floa
     g.pred = pred;
     g.pred_stride = n;
     for (int l = 0; l < NL; ++l) {
-        g.z_out[l] = nullptr;
+        g.g_out[l] = nullptr;
         g.h_out[l] = nullptr;
     }
     g.act_stride = 0;
@@ -544,7 +544,7 @@ int fused_forward(tune_surrogate* h, const __nv_bfloat16* feats, int64_t n, floa
 }
 
 // Training forward of rows [0, n_pad) of h->xin through the fused kernel (BF16), keeping
-// every layer's pre-activations Z and activations H for the backward pass and the head
+// every layer's gelu'(Z) (FP16) and activations H for the backward pass and the head
 // outputs in h->y.
 int fused_train_forward(tune_surrogate* h, int n_pad, cudaStream_t s)
 {
@@ -576,7 +576,7 @@ int fused_train_forward(tune_surrogate* h, int n_pad, cudaStream_t s)
     g.pred = h->y;
     g.pred_stride = h->batch;
     for (int l = 0; l < NL; ++l) {
-        g.z_out[l] = h->Z[l];
+        g.g_out[l] = h->G[l];
         g.h_out[l] = h->H[l];
     }
     g.act_stride = (long long)h->batch * WID;
@@ -587,7 +587,8 @@ int fused_train_forward(tune_surrogate* h, int n_pad, cudaStream_t s)
 }
 
 // Input gradients of layers 4, 3 and 2 in one persistent launch (tc_mlp_bwd.cuh):
-// dz[l - 1] = bf16((dz[l] W_l) * gelu'(Z[l - 1])) for l = 3, 2, 1 (0-based), rows [0, n_pad).
+// dz[l - 1] = bf16((dz[l] W_l) * G[l - 1]) for l = 3, 2, 1 (0-based), rows [0, n_pad),
+// G = gelu'(Z) as the forward pass kept it.
 int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaStream_t s)
 {
     if (n_pad % tcm::kRows) return tune::fail(TUNE_EINVAL, "surrogate: fused backward needs whole 128-row tiles");
@@ -610,7 +611,7 @@ int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaS
     g.members = h->members;
     g.units = (long long)(n_pad / tcm::kRows) * h->members;
     for (int j = 0; j < tcm::kBwdStages; ++j) {
-        g.z[j] = h->Z[NL - 2 - j];
+        g.g[j] = h->G[NL - 2 - j];
         g.dz[j] = dz[NL - 2 - j];
     }
     g.act_stride = (long long)h->batch * WID;
@@ -681,7 +682,7 @@ int wgrad_tc(tune_surrogate* h, int l, int n_pad, const __nv_bfloat16* dz, cudaS
 
 // Forward through all members for rows [0, n_pad) of h->xin (n_pad a multiple of 128).
 // x_in: layer-1 input rows (h->xin, or the caller's features on the tcgen05 path);
-// n_valid rows of it exist; store_z keeps the pre-activations for a backward pass.
+// n_valid rows of it exist; store_z keeps gelu' of the pre-activations for a backward pass.
 int forward(tune_surrogate* h, int n_pad, cudaStream_t s, const __nv_bfloat16* x_in = nullptr, int n_valid = -1,
             bool store_z = true)
 {
@@ -707,8 +708,8 @@ int forward(tune_surrogate* h, int n_pad, cudaStream_t s, const __nv_bfloat16* x
         g.K = (int)fan_in(l);
         g.bias = h->master + OFF_B(l);
         g.sBias = P;
-        g.Z = h->Z[l];
-        g.sZ = (long long)h->batch * WID;
+        g.G = h->G[l];
+        g.sG = (long long)h->batch * WID;
         g.H = h->H[l];
         g.sH = (long long)h->batch * WID;
         g.ldc = WID;
@@ -767,7 +768,7 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
     __nv_bfloat16* dzl[NL];
     for (int l = 0; l < NL; ++l) dzl[l] = h->dZ[fused ? l : (l & 1)];
     head_bwd_act<<<dim3((unsigned)(((long long)B * WID / 8 + 255) / 256), h->members), 256, 0, s>>>(
-        h->dy, h->master, h->Z[NL - 1], dzl[NL - 1], B);
+        h->dy, h->master, h->G[NL - 1], dzl[NL - 1], B);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: head backward launch");
     if (fused) {
         int rc = fused_backward(h, n_pad, dzl, s);
@@ -801,8 +802,8 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
         d.M = n_pad;
         d.N = kin;
         d.K = WID;
-        d.Z = h->Z[l - 1];
-        d.sZ = (long long)B * WID;
+        d.G = h->G[l - 1];
+        d.sG = (long long)B * WID;
         d.H = dzl[l - 1];
         d.sH = (long long)B * WID;
         d.ldc = WID;
@@ -896,7 +897,7 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     for (int i = 0; i < 4; ++i) add(M * P * 4);
     add(M * PB * 2);
     add(B * IN * 2);
-    for (int l = 0; l < NL; ++l) add(M * B * WID * 4);
+    for (int l = 0; l < NL; ++l) add(M * B * WID * 2);
     for (int l = 0; l < NL; ++l) add(M * B * WID * 2);
     for (int l = 0; l < NL; ++l) add(M * B * WID * 2);
     add(M * (NL - 1) * WID * WID * 2);
@@ -923,7 +924,7 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     h->v = carve<float>(p, M * P);
     h->wbf = carve<__nv_bfloat16>(p, M * PB);
     h->xin = carve<__nv_bfloat16>(p, B * IN);
-    for (int l = 0; l < NL; ++l) h->Z[l] = carve<float>(p, M * B * WID);
+    for (int l = 0; l < NL; ++l) h->G[l] = carve<__half>(p, M * B * WID);
     for (int l = 0; l < NL; ++l) h->H[l] = carve<__nv_bfloat16>(p, M * B * WID);
     for (int l = 0; l < NL; ++l) h->dZ[l] = carve<__nv_bfloat16>(p, M * B * WID);
     h->wbfT = carve<__nv_bfloat16>(p, M * (NL - 1) * WID * WID);
@@ -1016,7 +1017,7 @@ int surrogate_forward(tune_surrogate* h, const uint16_t* feats, int64_t n, float
         const int nb = (int)((n - r0) < h->batch ? (n - r0) : h->batch);
         const int n_pad = (nb + 127) / 128 * 128;
         int rc;
-        if (h->use_tc) {  // layer 1 reads the caller's rows directly; no pre-activations kept
+        if (h->use_tc) {  // layer 1 reads the caller's rows directly; no gelu' kept
             rc = forward(h, n_pad, s, f + r0 * IN, nb, false);
         } else {
             rc = load_batch(h, f + r0 * IN, h->lbl /*unused labels*/, nullptr, nb, s);

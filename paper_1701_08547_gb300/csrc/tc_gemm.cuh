@@ -6,7 +6,7 @@
 // a fused bias + GELU epilogue.
 //
 //   C[m][n] = sum_k A[m][k] * B[n][k]   (both operands K-major, BF16)
-//   H[m][n] = bf16(gelu(C[m][n] + bias[n])), optionally Z[m][n] = C[m][n] + bias[n]
+//   H[m][n] = bf16(gelu(C[m][n] + bias[n])), optionally G[m][n] = fp16(gelu'(C[m][n] + bias[n]))
 //
 // Every wait is bounded: on timeout the kernel records TUNE_ETIMEOUT's status
 // bit, waits (bounded) for its own copies and MMAs, frees its tensor memory
@@ -15,6 +15,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "gelu.cuh"
@@ -31,8 +32,8 @@ struct Args {
     int batched_a;          // A has a member coordinate (else member 0 for all)
     const float* bias;      // [members][N] at member stride sBias
     long long sBias;
-    float* Z;               // optional [members][M][N]
-    long long sZ;
+    __half* G;              // optional [members][M][N]: gelu' of the pre-activations (backward pass)
+    long long sG;
     __nv_bfloat16* H;       // [members][M][N]
     long long sH;
     int* status;            // bit 2 (timeout) set on a wait that gives up
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) gemm_fwd_kernel(const __grid_constan
         const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
         const float* bias = g.bias + member * g.sBias;
         __nv_bfloat16* H = g.H + member * g.sH + (long long)row * g.N;
-        float* Z = g.Z ? g.Z + member * g.sZ + (long long)row * g.N : nullptr;
+        __half* G = g.G ? g.G + member * g.sG + (long long)row * g.N : nullptr;
         const int c_beg = half * (g.N / 2), c_end = c_beg + g.N / 2;
         for (int c0 = c_beg; c0 < c_end; c0 += 32) {
             float v[32];
@@ -228,10 +229,18 @@ __global__ void __launch_bounds__(kThreads) gemm_fwd_kernel(const __grid_constan
                 v[i + 2] += b4.z;
                 v[i + 3] += b4.w;
             }
-            if (Z) {
+            if (G) {
 #pragma unroll
-                for (int i = 0; i < 32; i += 4)
-                    *reinterpret_cast<float4*>(Z + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                for (int i = 0; i < 32; i += 8) {
+                    uint4 pk;
+                    uint32_t* q = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const __half2 d = __floats2half2_rn(mlp::gelu_grad(v[i + 2 * t]), mlp::gelu_grad(v[i + 2 * t + 1]));
+                        q[t] = *reinterpret_cast<const uint32_t*>(&d);
+                    }
+                    *reinterpret_cast<uint4*>(G + c0 + i) = pk;
+                }
             }
 #pragma unroll
             for (int i = 0; i < 32; i += 8) {

@@ -36,6 +36,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <stdint.h>
 
@@ -71,9 +72,10 @@ struct Args {
     const float* wscale_half;  // FP8: [members][3][256] halves of the per-row scales of W2..W4
     float* pred;            // [members][pred_stride]
     long long pred_stride;  // member stride of pred (n for inference)
-    // training (BF16 only): per layer the pre-activations z (FP32) and activations h = gelu(z)
-    // (BF16) of every row < n, [members][act_stride] with rows of 256; null: not kept
-    float* z_out[kLayers];
+    // training (BF16 only): per layer gelu'(z) of the pre-activations (FP16) and the
+    // activations h = gelu(z) (BF16) of every row < n, [members][act_stride] with rows of
+    // 256; null: not kept
+    __half* g_out[kLayers];
     __nv_bfloat16* h_out[kLayers];
     long long act_stride;
     int* status;
@@ -177,6 +179,14 @@ __device__ __forceinline__ void ld_global_v8(const float* p, float* x)
 {
     asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
                  : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
+                 : "l"(p));
+}
+
+// 256-bit global load of eight 32-bit words (address 32-byte aligned; data not written by this kernel).
+__device__ __forceinline__ void ld_global_v8u(const void* p, uint32_t (&x)[8])
+{
+    asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                 : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]), "=r"(x[7])
                  : "l"(p));
 }
 
@@ -377,21 +387,25 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
 #pragma unroll
                         for (int i = 0; i < 16; ++i) v[i] = fmaf(v[i], f8 ? ss[i] : acc_mul, bb[i]);
                         const long long arow = (long long)mem * g.act_stride + (long long)(tile * kRows + r) * kWid + n0;
-                        if (TRAIN && !FP8 && g.z_out[l]) {  // training: keep z for the backward pass
+                        // 2 gelu(z) = z (1 + tanh u) in FP32: one multi-function-unit tanh per element;
+                        // training also keeps gelu'(z), from the same tanh, in FP16 for the backward pass
+                        uint32_t gd[8];
 #pragma unroll
-                            for (int i = 0; i < 2; ++i) {
-                                uint32_t w[8];
+                        for (int i = 0; i < 16; i += 2) {
+                            float dd[2];
 #pragma unroll
-                                for (int t = 0; t < 8; ++t) w[t] = __float_as_uint(v[8 * i + t]);
-                                st_global_v8(g.z_out[l] + arow + 8 * i, w);
+                            for (int k2 = 0; k2 < 2; ++k2) {
+                                const float z = v[i + k2], z2 = z * z;
+                                const float t = mlp::tanh_hw(mlp::gelu_u(z, z2));
+                                if (TRAIN) dd[k2] = mlp::gelu_grad_t(z, z2, t);
+                                v[i + k2] = fmaf(z, t, z);
+                            }
+                            if (TRAIN) {
+                                const __half2 d2 = __floats2half2_rn(dd[0], dd[1]);
+                                gd[i / 2] = *reinterpret_cast<const uint32_t*>(&d2);
                             }
                         }
-                        // 2 gelu(z) = z (1 + tanh u) in FP32: one multi-function-unit tanh per element
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const float t = mlp::tanh_hw(mlp::gelu_u(v[i], v[i] * v[i]));
-                            v[i] = fmaf(v[i], t, v[i]);
-                        }
+                        if (TRAIN && !FP8 && g.g_out[l]) st_global_v8(g.g_out[l] + arow, gd);
                         if (FP8 && !head) {
                             // E4M3 codes of 2 h: 16 columns = one 16-byte unit
                             uint32_t w[4];

@@ -4,8 +4,8 @@
 //   dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1}),   l = 4, 3, 2,
 // every dZ rounded to BF16 (the operand precision of the next product) and stored
 // for the weight gradients. Work unit = (tile of 128 rows, member); stage j of a unit
-// is the product with W_{4-j} followed by the epilogue that multiplies in gelu' of the
-// pre-activations Z_{3-j} (FP32, read from global memory) and writes dZ_{3-j}.
+// is the product with W_{4-j} followed by the epilogue that multiplies in gelu'(Z_{3-j})
+// (FP16, kept by the training forward pass) and writes dZ_{3-j}.
 //
 // The structure is the inference kernel's (tc_mlp.cuh): warp 0 streams the unit's
 // dZ4 rows and 32 KB K chunks of the weights with TMA, warp 1 issues the MMAs of two
@@ -30,18 +30,12 @@ struct BwdArgs {
     int rows;                         // rows per member (a multiple of 128: every unit's rows exist)
     int members;
     long long units;                  // rows / 128 * members
-    const float* z[kBwdStages];       // stage j: Z_{3-j}, [members][act_stride]
+    const __half* g[kBwdStages];      // stage j: gelu'(Z_{3-j}), [members][act_stride]
     __nv_bfloat16* dz[kBwdStages];    // stage j: dZ_{3-j}, same layout
     long long act_stride;             // member stride of z and dz (elements); rows of 256
     int* status;
 };
 
-// 16 pre-activations of a row; 32-byte aligned.
-__device__ __forceinline__ void load_z(const float* p, float (&z)[16])
-{
-    ld_global_v8(p, z);
-    ld_global_v8(p + 8, z + 8);
-}
 
 // grid: min(SMs, units) persistent CTAs; CTA b runs units b, b + gridDim.x, ...; its
 // j-th unit goes to chain j % 2. Unit u = (tile u / members, member u % members).
@@ -114,12 +108,12 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
                             x_last[s] = jj;
                         }
                         {
-                            // the epilogue of this (unit, stage) reads a 128 KB tile of
-                            // pre-activations: request it into L2 while the MMAs run
-                            const char* zt = reinterpret_cast<const char*>(
-                                g.z[l] + (long long)mem * g.act_stride + (long long)tile * kRows * kWid);
-                            for (int q = 0; q < 4; ++q)
-                                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(zt + q * 32768),
+                            // the epilogue of this (unit, stage) reads a 64 KB tile of gelu'(Z):
+                            // request it into L2 while the MMAs run
+                            const char* gt = reinterpret_cast<const char*>(
+                                g.g[l] + (long long)mem * g.act_stride + (long long)tile * kRows * kWid);
+                            for (int q = 0; q < 2; ++q)
+                                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gt + q * 32768),
                                              "r"(32768)
                                              : "memory");
                         }
@@ -204,16 +198,16 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
                     const int tile = (int)(u / g.members), mem = (int)(u % g.members);
                     const int row = tile * kRows + r;
                     const long long arow = (long long)mem * g.act_stride + (long long)row * kWid;
-                    const float* zr = g.z[l] + arow;
+                    const __half* gr = g.g[l] + arow;
                     __nv_bfloat16* dzr = g.dz[l] + arow;
                     uint8_t* act = smem + s * C::act_bytes;
                     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * kWid);
                     const bool last = l == kBwdStages - 1;
-                    // pre-activations of two 16-column blocks in flight: the first two are
-                    // requested before the accumulator wait, each later one when a buffer frees
-                    float zb[2][16];
+                    // gelu'(Z) of the thread's 64 columns (FP16, four 32-byte loads) is requested
+                    // before the accumulator wait
+                    uint32_t gw[kWid / 4 / 16][8];
 #pragma unroll
-                    for (int b = 0; b < 2; ++b) load_z(zr + c_beg + 16 * b, zb[b]);
+                    for (int b = 0; b < kWid / 4 / 16; ++b) ld_global_v8u(gr + c_beg + 16 * b, gw[b]);
                     if (!(ok = wait_bar(&acc_full[s], (uint32_t)((kBwdStages * k + l) & 1), g.status, abort_v)))
                         break;
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -224,10 +218,10 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
                         tmem_ld16(taddr + (uint32_t)n0, v);
                         uint32_t w[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            w[i] = pack_bf16(v[2 * i] * mlp::gelu_grad(zb[b & 1][2 * i]),
-                                             v[2 * i + 1] * mlp::gelu_grad(zb[b & 1][2 * i + 1]));
-                        if (b + 2 < kWid / 4 / 16) load_z(zr + n0 + 32, zb[b & 1]);
+                        for (int i = 0; i < 8; ++i) {
+                            const float2 d = __half22float2(*reinterpret_cast<const __half2*>(&gw[b][i]));
+                            w[i] = pack_bf16(v[2 * i] * d.x, v[2 * i + 1] * d.y);
+                        }
                         st_global_v8(dzr + n0, w);
                         if (!last) {
                             // 16 columns = two 16-byte units of K chunk n0 / 64
