@@ -631,17 +631,16 @@ int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaS
 }
 
 // Weight and bias gradients of layer l on tcgen05 (tc_wgrad.cuh): one CTA per (batch
-// split, member) with both operands MN-major, then the split reduction into grad.
+// split, output half, member) with both operands MN-major, then the split reduction into grad.
 int wgrad_tc(tune_surrogate* h, int l, int n_pad, const __nv_bfloat16* dz, cudaStream_t s)
 {
     const int kin = (int)fan_in(l), M = h->members;
     const int chunks = n_pad / tcw::kChunkRows;
-    // default: half the SMs per member (measured: 15 splits of an 8,192-row batch for 5 members
-    // beat 30, whose partials cost more to reduce than the extra CTAs gain)
+    // default: one CTA per SM, two (the output halves) per split
     int splits = h->wgrad_splits > 0 ? h->wgrad_splits : tune::device_sm_count() / (2 * M);
-    // the weight partials [M][splits][WID][kin] and the bias partials [M][splits][2][WID]
+    // the weight partials [M][splits][WID][kin] and the bias partials [M][splits][4][WID]
     // share the partial buffer
-    const long long cap = (long long)h->part_slices * WID * WID / ((long long)M * WID * (kin + 2));
+    const long long cap = (long long)h->part_slices * WID * WID / ((long long)M * WID * (kin + tcw::kBiasRows));
     splits = std::max(1, (int)std::min<long long>(std::min(splits, chunks), cap));
     CUtensorMap ta, tb;
     const auto u64 = CU_TENSOR_MAP_DATA_TYPE_UINT64;
@@ -671,11 +670,11 @@ int wgrad_tc(tune_surrogate* h, int l, int n_pad, const __nv_bfloat16* dz, cudaS
                       "surrogate: weight-gradient smem attribute");
         attr = true;
     }
-    tcw::wgrad_kernel<<<dim3(splits, M), tcw::kThreads, tcw::kSmem, s>>>(ta, tb, g, l != 0);
+    tcw::wgrad_kernel<<<dim3(2 * splits, M), tcw::kThreads, tcw::kSmem, s>>>(ta, tb, g, l != 0);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: weight-gradient launch");
     split_reduce<<<dim3((WID * kin / 4 + 255) / 256 + 1, M), 256, 0, s>>>(
         h->part, h->grad, OFF_W(l), kin, splits, (long long)splits * WID * kin, (long long)WID * kin, g.bpart, OFF_B(l),
-        2 * splits);
+        tcw::kBiasRows * splits);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: split reduce launch");
     return TUNE_OK;
 }
