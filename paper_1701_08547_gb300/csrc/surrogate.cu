@@ -144,59 +144,44 @@ __global__ void loss_reduce(const float* __restrict__ lpart, float* loss, int bl
     loss[mem] = s / (float)n;
 }
 
-// dZ4[i][j] = bf16(dy[i] * w5[j] * G4[i][j]) with G4 = gelu'(Z4) (FP16), eight columns per thread
-__global__ void head_bwd_act(const float* __restrict__ dy, const float* __restrict__ master,
-                             const __half* __restrict__ G4, __nv_bfloat16* dZ, int batch)
-{
-    const int mem = blockIdx.y;
-    const long long e = 8 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
-    if (e >= (long long)batch * WID) return;
-    const int i = (int)(e / WID), j = (int)(e % WID);
-    const long long o = (long long)mem * batch * WID + e;
-    const float d = dy[(long long)mem * batch + i];
-    const float* w5 = master + mem * P + OFF_W5 + j;
-    const uint4 gv = *reinterpret_cast<const uint4*>(G4 + o);
-    const __half2* g2 = reinterpret_cast<const __half2*>(&gv);
-    const float4 wa = *reinterpret_cast<const float4*>(w5), wb = *reinterpret_cast<const float4*>(w5 + 4);
-    const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-    uint32_t out[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float2 gd = __half22float2(g2[q]);
-        const __nv_bfloat162 b2 = __floats2bfloat162_rn(d * w[2 * q] * gd.x, d * w[2 * q + 1] * gd.y);
-        out[q] = *reinterpret_cast<const uint32_t*>(&b2);
-    }
-    *reinterpret_cast<uint4*>(dZ + o) = make_uint4(out[0], out[1], out[2], out[3]);
-}
-
 // Column sums over rows in two stages (deterministic): stage 1 sums slices of
 // kRowSlice rows into part[mem][slice][WID + 1]; stage 2 adds the slices.
 constexpr int kRowSlice = 64;
+constexpr int kRedWarps = 32;  // warps per block of the slice sums
 
-// part[.][.][j] = sum over the slice of dy[i] H4[i][j] (j < 256) and of dy[i] (j = 256);
-// four independent partial sums (rows i mod 4), added at the end
-__global__ void head_bwd_partial(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ H4, float* part,
-                                 int rows, int batch, int slices)
+// Head backward in one pass over a slice of srows rows (block = (slice, member), 128
+// threads, two columns each; short slices so that enough rows are in flight): dZ4[i][j] = bf16(dy[i] * w5[j] * G4[i][j]) with G4 = gelu'(Z4),
+// and part[.][.][j] = sum over the slice of dy[i] H4[i][j] (j < 256) and of dy[i] (j = 256),
+// four independent partial sums (rows i mod 4) added at the end.
+__global__ void head_bwd(const float* __restrict__ dy, const float* __restrict__ master,
+                         const __half* __restrict__ G4, const __nv_bfloat16* __restrict__ H4, __nv_bfloat16* dZ,
+                         float* part, int rows, int batch, int slices, int srows)
 {
-    const int mem = blockIdx.y, sl = blockIdx.x, j = threadIdx.x;
+    const int mem = blockIdx.y, sl = blockIdx.x, j = 2 * threadIdx.x;
     const float* d = dy + (long long)mem * batch;
-    const __nv_bfloat16* h = H4 + (long long)mem * batch * WID;
-    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    const int i0 = sl * kRowSlice, i1 = min(rows, i0 + kRowSlice);
+    const long long base = (long long)mem * batch * WID + j;
+    const float2 w = *reinterpret_cast<const float2*>(master + mem * P + OFF_W5 + j);
+    float s0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, s1[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int i0 = sl * srows, i1 = min(rows, i0 + srows);
+    auto row = [&](int i, int q) {
+        const float di = d[i];
+        const long long o = base + (long long)i * WID;
+        const float2 g = __half22float2(*reinterpret_cast<const __half2*>(G4 + o));
+        const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(H4 + o));
+        *reinterpret_cast<__nv_bfloat162*>(dZ + o) = __floats2bfloat162_rn(di * w.x * g.x, di * w.y * g.y);
+        s0[q] = fmaf(di, h.x, s0[q]);
+        s1[q] = fmaf(di, h.y, s1[q]);
+        sb[q] += di;
+    };
     int i = i0;
     for (; i + 4 <= i1; i += 4) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            s[q] = fmaf(d[i + q], __bfloat162float(h[(long long)(i + q) * WID + j]), s[q]);
-            sb[q] += d[i + q];
-        }
+        for (int q = 0; q < 4; ++q) row(i + q, q);
     }
-    for (; i < i1; ++i) {
-        s[0] = fmaf(d[i], __bfloat162float(h[(long long)i * WID + j]), s[0]);
-        sb[0] += d[i];
-    }
+    for (; i < i1; ++i) row(i, 0);
     float* o = part + ((long long)mem * slices + sl) * (WID + 1);
-    o[j] = (s[0] + s[1]) + (s[2] + s[3]);
+    o[j] = (s0[0] + s0[1]) + (s0[2] + s0[3]);
+    o[j + 1] = (s1[0] + s1[1]) + (s1[2] + s1[3]);
     if (j == 0) o[WID] = (sb[0] + sb[1]) + (sb[2] + sb[3]);
 }
 
@@ -221,18 +206,20 @@ __global__ void bias_partial(const __nv_bfloat16* __restrict__ dZ, float* part, 
 // partial sums are added in warp order (deterministic).
 __global__ void slices_reduce(const float* __restrict__ part, float* grad, long long off, int cols, int slices)
 {
+    // block = 32 columns x kRedWarps warps; warp w adds slices w, w + kRedWarps, ..., then
+    // the warps' sums are added in warp order
     const int mem = blockIdx.y, w = threadIdx.x >> 5;
     const int j = blockIdx.x * 32 + (threadIdx.x & 31);
-    __shared__ float red[8][32];
+    __shared__ float red[kRedWarps][32];
     float s = 0.0f;
     if (j < cols)
-        for (int q = w; q < slices; q += 8) s += part[((long long)mem * slices + q) * (WID + 1) + j];
+        for (int q = w; q < slices; q += kRedWarps) s += part[((long long)mem * slices + q) * (WID + 1) + j];
     red[w][threadIdx.x & 31] = s;
     __syncthreads();
     if (w == 0 && j < cols) {
         float t = red[0][threadIdx.x];
 #pragma unroll
-        for (int q = 1; q < 8; ++q) t += red[q][threadIdx.x];
+        for (int q = 1; q < kRedWarps; ++q) t += red[q][threadIdx.x];
         grad[mem * P + off + j] = t;
     }
 }
@@ -269,25 +256,41 @@ __global__ void split_reduce(const float* __restrict__ part, float* grad, long l
     *reinterpret_cast<float4*>(grad + mem * P + off_w + e) = s;
 }
 
-// Adam on FP32 master weights, then the BF16 copies of W1..W4.
+// Adam on FP32 master weights, then the BF16 copies of W1..W4; four consecutive
+// parameters per thread (every parameter segment starts at a multiple of 4, so a group
+// lies in one segment; padding past the last parameter is left alone).
 __global__ void adam_update(float* master, const float* grad, float* m, float* v, __nv_bfloat16* wbf, int members,
                             float lr, float b1, float b2, float eps, float c1, float c2)
 {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long e = 4 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
     if (e >= (long long)members * P) return;
     const long long p = e % P;
     if (p >= P_REAL) return;
-    const float g = grad[e];
-    const float mm = b1 * m[e] + (1.0f - b1) * g;
-    const float vv = b2 * v[e] + (1.0f - b2) * g * g;
-    m[e] = mm;
-    v[e] = vv;
-    const float w = master[e] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
-    master[e] = w;
+    float4 g4 = *reinterpret_cast<const float4*>(grad + e);
+    float4 m4 = *reinterpret_cast<const float4*>(m + e), v4 = *reinterpret_cast<const float4*>(v + e);
+    float4 w4 = *reinterpret_cast<const float4*>(master + e);
+    const float* gg = &g4.x;
+    float* mm = &m4.x;
+    float* vv = &v4.x;
+    float* ww = &w4.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (p + k >= P_REAL) break;
+        mm[k] = b1 * mm[k] + (1.0f - b1) * gg[k];
+        vv[k] = b2 * vv[k] + (1.0f - b2) * gg[k] * gg[k];
+        ww[k] = ww[k] - lr * (mm[k] / c1) / (sqrtf(vv[k] / c2) + eps);
+    }
+    *reinterpret_cast<float4*>(m + e) = m4;
+    *reinterpret_cast<float4*>(v + e) = v4;
+    *reinterpret_cast<float4*>(master + e) = w4;
     const long long mem = e / P;
     for (int l = 0; l < NL; ++l) {
         const long long len = WID * fan_in(l);
-        if (p >= OFF_W(l) && p < OFF_W(l) + len) wbf[mem * PB + BOFF_W(l) + (p - OFF_W(l))] = __float2bfloat16_rn(w);
+        if (p >= OFF_W(l) && p < OFF_W(l) + len) {
+            __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(wbf + mem * PB + BOFF_W(l) + (p - OFF_W(l)));
+            dst[0] = __floats2bfloat162_rn(ww[0], ww[1]);
+            dst[1] = __floats2bfloat162_rn(ww[2], ww[3]);
+        }
     }
 }
 
@@ -777,15 +780,21 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
     loss_grad<<<dim3(lblocks, h->members), 256, 0, s>>>(h->y, h->lbl, h->dy, h->part, n, B);
     loss_reduce<<<h->members, 32, 0, s>>>(h->part, h->loss, lblocks, n);
     const int slices = (n_pad + kRowSlice - 1) / kRowSlice;
-    head_bwd_partial<<<dim3(slices, h->members), WID, 0, s>>>(h->dy, h->H[NL - 1], h->part, n_pad, B, slices);
-    slices_reduce<<<dim3((WID + 1 + 31) / 32, h->members), 256, 0, s>>>(h->part, h->grad, OFF_W5, WID + 1, slices);
     // dZ of layer l: a buffer per layer when the input-gradient chain runs fused, else two
     // buffers in turn (each is consumed by its weight gradient before it is overwritten)
     const bool fused = h->use_tc && h->bwd_mode == 1;
     __nv_bfloat16* dzl[NL];
     for (int l = 0; l < NL; ++l) dzl[l] = h->dZ[fused ? l : (l & 1)];
-    head_bwd_act<<<dim3((unsigned)(((long long)B * WID / 8 + 255) / 256), h->members), 256, 0, s>>>(
-        h->dy, h->master, h->G[NL - 1], dzl[NL - 1], B);
+    // the head's weight and bias gradients (slices, then their sum) and dZ4 in one pass
+    // (16-row slices, longer where their partials would not fit the partial buffer)
+    int hrows = 16;
+    while ((long long)h->members * ((n_pad + hrows - 1) / hrows) * (WID + 1) > (long long)h->part_slices * WID * WID)
+        hrows *= 2;
+    const int hslices = (n_pad + hrows - 1) / hrows;
+    head_bwd<<<dim3(hslices, h->members), WID / 2, 0, s>>>(h->dy, h->master, h->G[NL - 1], h->H[NL - 1],
+                                                         dzl[NL - 1], h->part, n_pad, B, hslices, hrows);
+    slices_reduce<<<dim3((WID + 1 + 31) / 32, h->members), 32 * kRedWarps, 0, s>>>(h->part, h->grad, OFF_W5,
+                                                                                  WID + 1, hslices);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: head backward launch");
     if (fused) {
         int rc = fused_backward(h, n_pad, dzl, s);
@@ -804,7 +813,8 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
         }
         if (!fused) {  // the tcgen05 weight-gradient pass forms the bias gradient too
             bias_partial<<<dim3(slices, h->members), WID, 0, s>>>(dz, h->part, n_pad, B, slices);
-            slices_reduce<<<dim3(WID / 32, h->members), 256, 0, s>>>(h->part, h->grad, OFF_B(l), WID, slices);
+            slices_reduce<<<dim3(WID / 32, h->members), 32 * kRedWarps, 0, s>>>(h->part, h->grad, OFF_B(l), WID,
+                                                                                slices);
             TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: reduce launch");
         }
         if (l == 0 || fused) continue;
@@ -835,8 +845,8 @@ int adam(tune_surrogate* h, cudaStream_t s)
     h->step += 1;
     const float c1 = 1.0f - powf(h->b1, (float)h->step), c2 = 1.0f - powf(h->b2, (float)h->step);
     const long long total = (long long)h->members * P;
-    adam_update<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(h->master, h->grad, h->m, h->v, h->wbf, h->members,
-                                                                 h->lr, h->b1, h->b2, h->eps, c1, c2);
+    adam_update<<<(unsigned)((total / 4 + 255) / 256), 256, 0, s>>>(h->master, h->grad, h->m, h->v, h->wbf,
+                                                                     h->members, h->lr, h->b1, h->b2, h->eps, c1, c2);
     h->fp8_stale = true;
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: adam launch");
     return TUNE_OK;

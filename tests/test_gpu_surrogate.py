@@ -157,6 +157,53 @@ def test_training_backward_paths_agree(dev):
                 assert rel <= 1e-2, (n, m, name, rel)
 
 
+def test_weight_gradient_splits_agree(dev):
+    """The tcgen05 weight and bias gradients split the batch into ranges of 64-row chunks
+    (uneven when the split count does not divide the chunk count) and add the partials in
+    split order: 1, 7 and the default split count give the same gradients up to FP32
+    summation order."""
+    import torch
+
+    n = 2000
+    X = to_dev(feats(n, 17), dev)
+    t = torch.tensor(np.random.default_rng(8).standard_normal(n), dtype=torch.float32, device=dev)
+    grads = []
+    for splits in (1, 7, 0):
+        s, _ = make(2, 2048, seed0=31)
+        s.set_wgrad_splits(splits)
+        s.train_step(X, t, apply_update=False)
+        s.check()
+        grads.append(s.get(s.GET_GRADS).astype(np.float64))
+    for g in grads[1:]:
+        rel = np.linalg.norm(g - grads[0]) / np.linalg.norm(grads[0])
+        assert rel <= 1e-5, rel
+
+
+def test_training_backward_paths_agree_wide_ensemble(dev):
+    """16 members on a 256-row batch: the fused input-gradient chain runs 32 units, the weight
+    gradients 4 splits of one chunk each per member; the gradients agree with the mma.sync
+    backward."""
+    import torch
+
+    n = 200
+    X = to_dev(feats(n, 19), dev)
+    t = torch.tensor(np.random.default_rng(9).standard_normal(n), dtype=torch.float32, device=dev)
+    grads = []
+    for mode in ("fused", "layered"):
+        s, _ = make(16, 256, seed0=41)
+        if mode == "layered":
+            s.set_backward_mode(s.BWD_LAYERED)
+        s.train_step(X, t, apply_update=False)
+        s.check()
+        grads.append(s.get(s.GET_GRADS).reshape(16, L.P))
+    for m in range(16):
+        a, b = L.unpack(grads[0][m], 1)[0], L.unpack(grads[1][m], 1)[0]
+        for name in a:
+            x, y = np.asarray(a[name], np.float64), np.asarray(b[name], np.float64)
+            rel = np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-30)
+            assert rel <= 1e-2, (m, name, rel)
+
+
 def test_adam_steps_match_oracle(dev):
     import torch
 
