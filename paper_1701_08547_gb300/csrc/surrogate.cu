@@ -245,13 +245,20 @@ __global__ void split_reduce(const float* __restrict__ part, float* grad, long l
     if (e >= WID * cols) return;
     const float* p = part + (long long)mem * mstride + e;
     float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-#pragma unroll 8
-    for (int q = 0; q < splits; ++q) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(p + (long long)q * qstride));
-        s.x += t.x;
-        s.y += t.y;
-        s.z += t.z;
-        s.w += t.w;
+    for (int q0 = 0; q0 < splits; q0 += 16) {
+        // up to 16 partials requested together, then added in split order
+        float4 t[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (q0 + q < splits) t[q] = __ldg(reinterpret_cast<const float4*>(p + (long long)(q0 + q) * qstride));
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (q0 + q < splits) {
+                s.x += t[q].x;
+                s.y += t[q].y;
+                s.z += t[q].z;
+                s.w += t[q].w;
+            }
     }
     *reinterpret_cast<float4*>(grad + mem * P + off_w + e) = s;
 }
