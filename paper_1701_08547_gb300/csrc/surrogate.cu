@@ -635,7 +635,6 @@ int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaS
     rc = make_map_nd(&twt, u64, 4, h->wbfT, dw, sw, bw);
     if (rc) return rc;
     tcm::BwdArgs g;
-    g.rows = n_pad;
     g.members = h->members;
     g.units = (long long)(n_pad / tcm::kRows) * h->members;
     for (int j = 0; j < tcm::kBwdStages; ++j) {

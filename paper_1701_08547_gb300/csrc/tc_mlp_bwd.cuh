@@ -27,9 +27,8 @@ namespace tcm {
 constexpr int kBwdStages = kLayers - 1;  // products with W4, W3, W2
 
 struct BwdArgs {
-    int rows;                         // rows per member (a multiple of 128: every unit's rows exist)
     int members;
-    long long units;                  // rows / 128 * members
+    long long units;                  // rows / 128 * members (rows a multiple of 128: every unit's rows exist)
     const __half* g[kBwdStages];      // stage j: gelu'(Z_{3-j}), [members][act_stride]
     __nv_bfloat16* dz[kBwdStages];    // stage j: dZ_{3-j}, same layout
     long long act_stride;             // member stride of z and dz (elements); rows of 256
