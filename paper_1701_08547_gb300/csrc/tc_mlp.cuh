@@ -166,6 +166,40 @@ __device__ __forceinline__ void ld16(const float* p, float (&x)[16])
     }
 }
 
+// Packed FP32 pairs (two IEEE single-precision operations, round to nearest, per
+// instruction): the same result in each lane as the scalar fmaf / multiply / add.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n .reg .b64 a, b, c, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n mov.b64 c, {%6, %7};\n"
+        " fma.rn.f32x2 d, a, b, c;\n mov.b64 {%0, %1}, d;\n}\n"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n .reg .b64 a, b, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n mul.rn.f32x2 d, a, b;\n"
+        " mov.b64 {%0, %1}, d;\n}\n"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n .reg .b64 a, b, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n add.rn.f32x2 d, a, b;\n"
+        " mov.b64 {%0, %1}, d;\n}\n"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
 // 256-bit global store of eight 32-bit words (address 32-byte aligned).
 __device__ __forceinline__ void st_global_v8(void* p, const uint32_t (&w)[8])
 {
@@ -384,25 +418,41 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                         if (head) ld16(w5 + n0, ww);
                         float v[16];
                         tmem_ld16(taddr + (uint32_t)n0, v);
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] = fmaf(v[i], f8 ? ss[i] : acc_mul, bb[i]);
                         const long long arow = (long long)mem * g.act_stride + (long long)(tile * kRows + r) * kWid + n0;
-                        // 2 gelu(z) = z (1 + tanh u) in FP32: one multi-function-unit tanh per element;
-                        // training also keeps gelu'(z), from the same tanh, in FP16 for the backward pass
+                        // z = acc * s + b, then 2 gelu(z) = z (1 + tanh u), u = z (K C z^2 + K), in FP32:
+                        // one multi-function-unit tanh per element. Inference works on column pairs
+                        // (packed FP32x2: the scalar operations' results, half the instructions);
+                        // training, at the register limit with gelu'(z) (from the same tanh, kept in
+                        // FP16 for the backward pass) also live, is faster in scalar form.
                         uint32_t gd[8];
+                        if (TRAIN) {
 #pragma unroll
-                        for (int i = 0; i < 16; i += 2) {
-                            float dd[2];
+                            for (int i = 0; i < 16; ++i) v[i] = fmaf(v[i], acc_mul, bb[i]);
 #pragma unroll
-                            for (int k2 = 0; k2 < 2; ++k2) {
-                                const float z = v[i + k2], z2 = z * z;
-                                const float t = mlp::tanh_hw(mlp::gelu_u(z, z2));
-                                if (TRAIN) dd[k2] = mlp::gelu_grad_t(z, z2, t);
-                                v[i + k2] = fmaf(z, t, z);
-                            }
-                            if (TRAIN) {
+                            for (int i = 0; i < 16; i += 2) {
+                                float dd[2];
+#pragma unroll
+                                for (int k2 = 0; k2 < 2; ++k2) {
+                                    const float z = v[i + k2], z2 = z * z;
+                                    const float t = mlp::tanh_hw(mlp::gelu_u(z, z2));
+                                    dd[k2] = mlp::gelu_grad_t(z, z2, t);
+                                    v[i + k2] = fmaf(z, t, z);
+                                }
                                 const __half2 d2 = __floats2half2_rn(dd[0], dd[1]);
                                 gd[i / 2] = *reinterpret_cast<const uint32_t*>(&d2);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; i += 2) {
+                                const float2 z = fma2(make_float2(v[i], v[i + 1]),
+                                                      f8 ? make_float2(ss[i], ss[i + 1]) : f2(acc_mul),
+                                                      make_float2(bb[i], bb[i + 1]));
+                                const float2 uu =
+                                    mul2(z, fma2(f2(mlp::kGeluK * mlp::kGeluC), mul2(z, z), f2(mlp::kGeluK)));
+                                const float2 t = make_float2(mlp::tanh_hw(uu.x), mlp::tanh_hw(uu.y));
+                                const float2 h2 = fma2(z, t, z);
+                                v[i] = h2.x;
+                                v[i + 1] = h2.y;
                             }
                         }
                         if (TRAIN && !FP8 && g.g_out[l]) st_global_v8(g.g_out[l] + arow, gd);
