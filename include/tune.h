@@ -111,6 +111,7 @@ typedef struct tune_kernel_desc {
 #define TUNE_EMIT_POINTS 0x1u   /* also write per-point B*, W*, cost (pt_* arrays) */
 #define TUNE_SCHED_WARP 0x10u   /* schedule: one warp per descriptor (the default) */
 #define TUNE_SCHED_THREAD 0x20u /* schedule: one thread per descriptor (not with EMIT) */
+#define TUNE_HOST_DIRECT 0x40u  /* tune_eval_host: evaluate in place in mapped host memory */
 /* Warp schedule knobs (tune_autotune picks them): a work queue handing each warp
  * 2^c consecutive descriptors per grab (c in 0..14; default: a static stride),
  * and at most m resident CTAs per SM (m in 1..15; default: as many as fit). */
@@ -436,11 +437,17 @@ int tune_real_measure(int32_t kernel, int32_t n, const int32_t* T, const int32_t
  * library stream while chunk i + 1 is copied in and evaluated, so that the transfers
  * overlap the evaluation (two staging buffers in dev_scratch). Host buffers should be
  * pinned for the copies to run asynchronously. Results equal tune_eval's bit for bit.
+ * With TUNE_HOST_DIRECT the three host buffers must be pinned and mapped into the
+ * device's address space (cudaHostAlloc / cudaMallocHost, or cudaHostRegister with
+ * mapping; checked with cudaPointerGetAttributes, TUNE_EINVAL otherwise): one launch
+ * then reads the descriptors from and writes the top-k into host memory over the
+ * host link while it evaluates (no staging copies; chunk and dev_scratch's staging
+ * buffers are not used, the status header is).
  *   host_descs      host tune_kernel_desc[n_kernels]
  *   host_topk_idx   host int32[n_kernels * k];  host_topk_cost  host float[n_kernels * k]
  *   dev_scratch     device memory, 256-byte aligned, of tune_eval_host_scratch_bytes(chunk, k)
  *                   bytes; its first 256 bytes are the status header (read with tune_check)
- *   flags           TUNE_SCHED_WARP with its chunk / CTA fields
+ *   flags           TUNE_SCHED_WARP with its chunk / CTA fields, TUNE_HOST_DIRECT
  * Enqueues the work and returns; `stream` completes once the last result is in host
  * memory. Calls on one device use the same two library streams and must not run
  * concurrently from several host threads.

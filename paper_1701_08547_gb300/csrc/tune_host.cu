@@ -1,6 +1,9 @@
 // tune_eval_host: tune_eval with the descriptors and results in host memory; chunk i is
 // copied in on one library stream, evaluated on the caller's stream and copied out on
 // another while chunk i + 1 is copied in and evaluated (two device staging buffers).
+// With TUNE_HOST_DIRECT and mapped pinned buffers, one launch reads and writes host
+// memory in place over the host link (on Grace-Blackwell, NVLink-C2C), overlapping the
+// transfers with the evaluation without staging copies or extra launches.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -70,12 +73,32 @@ extern "C" int tune_eval_host(const tune_arch* arch, const tune_axes* axes, cons
         return tune::fail(TUNE_EINVAL, "dev_scratch must be 256-byte aligned");
     if (n_kernels > 0 && (!host_descs || !host_topk_idx || !host_topk_cost))
         return tune::fail(TUNE_EINVAL, "host_descs and outputs must be non-NULL");
-    if (flags & ~(TUNE_SCHED_WARP | 0xff00u))
-        return tune::fail(TUNE_EINVAL, "flags 0x%x: only TUNE_SCHED_WARP and its chunk/CTA fields", flags);
+    if (flags & ~(TUNE_SCHED_WARP | TUNE_HOST_DIRECT | 0xff00u))
+        return tune::fail(TUNE_EINVAL, "flags 0x%x: only TUNE_SCHED_WARP with its chunk/CTA fields and TUNE_HOST_DIRECT",
+                          flags);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (flags & TUNE_HOST_DIRECT) {
+        // in place: every buffer must be pinned host memory the device can address
+        const void* host[3] = {host_descs, host_topk_idx, host_topk_cost};
+        void* dev[3] = {nullptr, nullptr, nullptr};
+        for (int i = 0; i < 3 && n_kernels > 0; ++i) {
+            cudaPointerAttributes at;
+            TUNE_CUDA_TRY(cudaPointerGetAttributes(&at, host[i]), "tune_eval_host: cudaPointerGetAttributes");
+            if (at.type != cudaMemoryTypeHost || !at.devicePointer)
+                return tune::fail(TUNE_EINVAL, "TUNE_HOST_DIRECT: host buffer %d is not pinned, mapped memory", i);
+            dev[i] = at.devicePointer;
+        }
+        int* status = static_cast<int*>(dev_scratch);
+        unsigned long long* queue = reinterpret_cast<unsigned long long*>(dev_scratch) + 1;
+        TUNE_CUDA_TRY(cudaMemsetAsync(dev_scratch, 0, tune::kWorkspaceHeader, s), "tune_eval_host: status reset");
+        if (n_kernels == 0) return TUNE_OK;
+        return tune::eval_launch(arch, axes, static_cast<const tune_kernel_desc*>(dev[0]), n_kernels, k,
+                                 flags & ~TUNE_HOST_DIRECT, static_cast<int32_t*>(dev[1]), static_cast<float*>(dev[2]),
+                                 status, queue, s);
+    }
     HostPipe* hp = nullptr;
     int rc = host_pipe(&hp);
     if (rc) return rc;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // scratch: header (status word, one queue counter per buffer), then per buffer the
     // descriptors, indices and costs of one chunk
     char* base = static_cast<char*>(dev_scratch);

@@ -16,6 +16,7 @@ TUNE_OK, TUNE_EINVAL, TUNE_ENOMEM, TUNE_ECUDA, TUNE_ETIMEOUT, TUNE_ECOMPILE, TUN
     0, -1, -2, -3, -4, -5, -6)
 TUNE_EMIT_POINTS = 0x1
 TUNE_SCHED_WARP, TUNE_SCHED_THREAD = 0x10, 0x20
+TUNE_HOST_DIRECT = 0x40
 
 
 def TUNE_SCHED_CHUNK(c):
