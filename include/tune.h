@@ -441,8 +441,8 @@ int tune_real_measure(int32_t kernel, int32_t n, const int32_t* T, const int32_t
  * device's address space (cudaHostAlloc / cudaMallocHost, or cudaHostRegister with
  * mapping; checked with cudaPointerGetAttributes, TUNE_EINVAL otherwise): one launch
  * then reads the descriptors from and writes the top-k into host memory over the
- * host link while it evaluates (no staging copies; chunk and dev_scratch's staging
- * buffers are not used, the status header is).
+ * host link while it evaluates (no staging copies; chunk is not used, and dev_scratch
+ * needs only the 256-byte status header).
  *   host_descs      host tune_kernel_desc[n_kernels]
  *   host_topk_idx   host int32[n_kernels * k];  host_topk_cost  host float[n_kernels * k]
  *   dev_scratch     device memory, 256-byte aligned, of tune_eval_host_scratch_bytes(chunk, k)

@@ -208,15 +208,16 @@ def tune_search(arch, axes, descs, method, budget, seed, t_keep=None, workspace_
 
 
 def tune_eval_host(arch, axes, host_descs, k, chunk, topk_idx, topk_cost, scratch=None, flags=0, stream=None):
-    """tune_eval from and to host memory with the copies overlapping the evaluation.
-    host_descs: host uint8 tensor [n, 64] (pinned for overlap); topk_idx / topk_cost: host
-    int32 / float32 tensors [n, k] (pinned); scratch: device uint8 tensor of
-    tune_eval_host_scratch_bytes(chunk, k) bytes (allocated here if None). Enqueues on
-    `stream`; returns the scratch (its header holds the status word)."""
+    """tune_eval from and to host memory with the copies overlapping the evaluation, or,
+    with flags | TUNE_HOST_DIRECT and pinned buffers, in place over the host link in one
+    launch. host_descs: host uint8 tensor [n, 64] (pinned for overlap); topk_idx /
+    topk_cost: host int32 / float32 tensors [n, k] (pinned); scratch: device uint8 tensor of
+    tune_eval_host_scratch_bytes(chunk, k) bytes, 256 in the direct mode (allocated here if
+    None). Enqueues on `stream`; returns the scratch (its header holds the status word)."""
     torch = _torch()
     L = native.load()
     n = host_descs.numel() // 64
-    nbytes = L.tune_eval_host_scratch_bytes(int(chunk), int(k))
+    nbytes = 256 if flags & native.TUNE_HOST_DIRECT else L.tune_eval_host_scratch_bytes(int(chunk), int(k))
     if scratch is None:
         scratch = torch.empty(nbytes, dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
     a = native.make_arch(arch)

@@ -67,8 +67,11 @@ extern "C" int tune_eval_host(const tune_arch* arch, const tune_axes* axes, cons
     if (k < 1 || k > 16) return tune::fail(TUNE_EINVAL, "k = %d outside [1, 16]", k);
     if (n_kernels < 0) return tune::fail(TUNE_EINVAL, "n_kernels < 0");
     if (chunk < 1 || chunk > (1LL << 26)) return tune::fail(TUNE_EINVAL, "chunk %lld outside [1, 2^26]", (long long)chunk);
-    if (!dev_scratch || scratch_bytes < tune_eval_host_scratch_bytes(chunk, k))
-        return tune::fail(TUNE_ENOMEM, "scratch smaller than tune_eval_host_scratch_bytes(chunk, k)");
+    // the direct mode uses only the status header of the scratch
+    const size_t need = (flags & TUNE_HOST_DIRECT) ? tune::kWorkspaceHeader : tune_eval_host_scratch_bytes(chunk, k);
+    if (!dev_scratch || scratch_bytes < need)
+        return tune::fail(TUNE_ENOMEM, "scratch smaller than %zu bytes (tune_eval_host_scratch_bytes(chunk, k), or "
+                                       "256 with TUNE_HOST_DIRECT)", need);
     if ((reinterpret_cast<uintptr_t>(dev_scratch) & 255) != 0)
         return tune::fail(TUNE_EINVAL, "dev_scratch must be 256-byte aligned");
     if (n_kernels > 0 && (!host_descs || !host_topk_idx || !host_topk_cost))
