@@ -167,7 +167,7 @@ __device__ __forceinline__ void ld16(const float* p, float (&x)[16])
 }
 
 // Packed FP32 pairs (two IEEE single-precision operations, round to nearest, per
-// instruction): the same result in each lane as the scalar fmaf / multiply / add.
+// instruction): the same result in each lane as the scalar fmaf / multiply.
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
 {
     float2 d;
@@ -182,16 +182,6 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b)
 {
     float2 d;
     asm("{\n .reg .b64 a, b, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n mul.rn.f32x2 d, a, b;\n"
-        " mov.b64 {%0, %1}, d;\n}\n"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-
-__device__ __forceinline__ float2 add2(float2 a, float2 b)
-{
-    float2 d;
-    asm("{\n .reg .b64 a, b, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n add.rn.f32x2 d, a, b;\n"
         " mov.b64 {%0, %1}, d;\n}\n"
         : "=f"(d.x), "=f"(d.y)
         : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
