@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include <cuda_fp8.h>
@@ -78,6 +79,20 @@ T* carve(char*& p, size_t count)
     T* r = reinterpret_cast<T*>(p);
     p += (count * sizeof(T) + 255) & ~size_t(255);
     return r;
+}
+
+// A kernel's dynamic shared-memory limit, set once per device (the attribute belongs to the
+// device's context; `done` keeps one bit per device ordinal below 64).
+template <typename Kernel>
+int smem_attr(Kernel kernel, int bytes, std::atomic<uint64_t>& done, const char* what)
+{
+    int dev = 0;
+    TUNE_CUDA_TRY(cudaGetDevice(&dev), what);
+    const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return TUNE_OK;
+    TUNE_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes), what);
+    done.fetch_or(bit, std::memory_order_release);
+    return TUNE_OK;
 }
 
 // ---- small kernels ------------------------------------------------------------
@@ -463,12 +478,9 @@ int tc_layer(tune_surrogate* h, int l, int n_pad, cudaStream_t s, const __nv_bfl
     g.sH = (long long)h->batch * WID;
     g.status = h->status;
     const int smem = tc::smem_bytes(WID);
-    static bool attr = false;
-    if (!attr) {
-        TUNE_CUDA_TRY(cudaFuncSetAttribute(tc::gemm_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
-                      "surrogate: tc smem attribute");
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    rc = smem_attr(tc::gemm_fwd_kernel, smem, attr, "surrogate: tc smem attribute");
+    if (rc) return rc;
     tc::gemm_fwd_kernel<<<dim3(n_pad / tc::BM, h->members), tc::kThreads, smem, s>>>(ta, tb, g);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: tc gemm launch");
     return TUNE_OK;
@@ -502,13 +514,9 @@ int launch_fused(const CUtensorMap& tx, const CUtensorMap& tw1, const CUtensorMa
                  unsigned grid, cudaStream_t s)
 {
     constexpr int smem = tcm::Cfg<FP8>::smem;
-    static bool attr = false;
-    if (!attr) {
-        TUNE_CUDA_TRY(cudaFuncSetAttribute(tcm::mlp_infer_kernel<FP8, TRAIN>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
-                      "surrogate: fused smem attribute");
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    const int rc = smem_attr(tcm::mlp_infer_kernel<FP8, TRAIN>, smem, attr, "surrogate: fused smem attribute");
+    if (rc) return rc;
     tcm::mlp_infer_kernel<FP8, TRAIN><<<grid, tcm::kThreads, smem, s>>>(tx, tw1, tw, g);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: fused launch");
     return TUNE_OK;
@@ -644,12 +652,9 @@ int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaS
     g.act_stride = (long long)h->batch * WID;
     g.status = h->status;
     constexpr int smem = tcm::Cfg<false>::smem;
-    static bool attr = false;
-    if (!attr) {
-        TUNE_CUDA_TRY(cudaFuncSetAttribute(tcm::mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
-                      "surrogate: fused backward smem attribute");
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    rc = smem_attr(tcm::mlp_bwd_kernel, smem, attr, "surrogate: fused backward smem attribute");
+    if (rc) return rc;
     const long long sms = tune::device_sm_count();
     const unsigned grid = (unsigned)(g.units < sms ? g.units : sms);
     tcm::mlp_bwd_kernel<<<grid, tcm::kThreads, smem, s>>>(tdz, twt, g);
@@ -691,12 +696,9 @@ int wgrad_tc(tune_surrogate* h, int l, int n_pad, const __nv_bfloat16* dz, cudaS
     g.part = h->part;
     g.bpart = h->part + (long long)M * splits * WID * kin;
     g.status = h->status;
-    static bool attr = false;
-    if (!attr) {
-        TUNE_CUDA_TRY(cudaFuncSetAttribute(tcw::wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcw::kSmem),
-                      "surrogate: weight-gradient smem attribute");
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    rc = smem_attr(tcw::wgrad_kernel, tcw::kSmem, attr, "surrogate: weight-gradient smem attribute");
+    if (rc) return rc;
     tcw::wgrad_kernel<<<dim3(2 * splits, M), tcw::kThreads, tcw::kSmem, s>>>(ta, tb, g, l != 0);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: weight-gradient launch");
     split_reduce<<<dim3((WID * kin / 4 + 255) / 256 + 1, M), 256, 0, s>>>(
