@@ -53,7 +53,11 @@ enum { TUNE_NCLASS = 7 }; /* FP32, FP64, INT, GLDST, SLDST, BRANCH, SFU */
  * throughput per number of cycles" (Section III-B), plus the allocation
  * details the occupancy calculation needs on current GPUs. Host memory.
  * Limits: warp_size = 32, max_warps_sm <= 64, max_blocks_sm <= 32,
- * 1 <= n_smem_caps <= 16 with smem_caps ascending, ipc[c] > 0.
+ * 1 <= n_smem_caps <= 16 with smem_caps ascending, ipc[c] finite and
+ * >= 2^-16, 1 <= w_sat <= 2^20, 1 <= work_scale <= 2^24. (With the
+ * descriptor ranges below these bounds keep every cost of a valid point
+ * under 2^114, so an FP32 cost never overflows: +inf always means "no
+ * valid configuration".) A row outside them is refused with TUNE_EINVAL.
  */
 typedef struct tune_arch {
     int32_t cc;                  /* compute capability x 10 */
@@ -96,13 +100,15 @@ typedef struct tune_axes {
  * paper's front end extracts (Section III, "Static Analysis": registers and
  * shared memory from ptxas, instruction counts from the binary).
  * space_mask bits 0..31 select t[], 32..47 g[], 48..55 u[], 56..59 c[];
- * bits 60..63 and bits beyond each axis length must be zero.
+ * bits 60..63 and bits beyond each axis length must be zero. A record
+ * outside the field ranges below, or whose mask breaks these rules, is
+ * malformed (see tune_eval).
  */
 typedef struct tune_kernel_desc {
-    float n[TUNE_NCLASS]; /* static instruction counts per class, >= 0 */
-    int32_t r0;           /* registers per thread at unroll 1 */
-    int32_t s0;           /* shared memory per block, bytes */
-    float d;              /* branch-divergence fraction, >= 0 */
+    float n[TUNE_NCLASS]; /* static instruction counts per class, in [0, 2^40] */
+    int32_t r0;           /* registers per thread at unroll 1, in [0, 2^24) */
+    int32_t s0;           /* shared memory per block, bytes, in [0, 2^30) */
+    float d;              /* branch-divergence fraction, in [0, 1] */
     uint64_t space_mask;
     int32_t reserved[4];
 } tune_kernel_desc;
@@ -147,8 +153,10 @@ enum { TUNE_CALL_EVAL = 0, TUNE_CALL_TOPK = 1 };
  * n_kernels records); 1 <= k <= 16; workspace (device) of at least
  * tune_workspace_bytes(TUNE_CALL_EVAL, n_kernels, k) bytes.
  * n_kernels = 0 is valid and enqueues only the status reset.
- * A descriptor whose mask selects values outside the axes gets padding
- * outputs and sets TUNE_EINVAL in the status word.
+ * A malformed descriptor (mask selecting values outside the axes, or a
+ * field outside its range: a count above 2^40, negative or not a number,
+ * d outside [0, 1], r0 or s0 out of range) gets padding outputs and sets
+ * TUNE_EINVAL in the status word; the other descriptors are unaffected.
  */
 int tune_eval(const tune_arch* arch, const tune_axes* axes, const tune_kernel_desc* descs,
               int64_t n_kernels, int32_t k, uint32_t flags, int32_t* topk_idx, float* topk_cost,
@@ -168,10 +176,15 @@ int tune_eval(const tune_arch* arch, const tune_axes* axes, const tune_kernel_de
  * loads the library holds until the process exits. It calls no cudaMalloc,
  * cudaFree or other allocating routine.
  *  - A call whose scratch need, tune_workspace_bytes(TUNE_CALL_EVAL, n, k),
- *    exceeds 4096 bytes is rejected with TUNE_ENOMEM.
+ *    exceeds 4096 bytes is rejected with TUNE_ENOMEM. (Every call of this
+ *    version needs the 256-byte header only, so the limit is not reached.)
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before starting any stream capture.
+ *  - That address is kept for the life of the process. It belongs to the
+ *    device's primary context: after cudaDeviceReset (or anything else that
+ *    destroys and recreates that context) it is stale, so do not use this
+ *    entry point across a device reset.
  *  - Every call shares the array and clears the part it uses at the start;
  *    calls that overlap on the GPU (for example on two streams) race on it.
  *  - The call waits for `stream` before returning, so that it can return
@@ -200,7 +213,10 @@ int tune_autotune(const tune_arch* arch, const tune_axes* axes, const tune_kerne
                   tune_stream_t stream);
 
 /*
- * tune_topk — segmented top-k over an external score array (device).
+ * tune_topk — segmented top-k over an external score array (device): the
+ * ranking step of the paper's autotuning (Section IV-A: the variants of a
+ * kernel are sorted by time, ascending, and the best ranks are kept), here
+ * over any per-point score, e.g. a surrogate's predicted runtimes.
  * For segment s = [seg_offsets[s], seg_offsets[s+1]) of `scores`, the k
  * smallest scores that are not +inf or NaN, equal scores -> lower index;
  * topk_idx holds indices within the segment (-1 for padding), topk_score

@@ -272,6 +272,20 @@ static int cmp_pair(const void* pa, const void* pb)
     return (a->idx > b->idx) - (a->idx < b->idx);
 }
 
+/*
+ * Field ranges of a well-formed descriptor (the library's record format): every
+ * instruction count a number in [0, 2^40], the divergence fraction d in [0, 1],
+ * r0 in [0, 2^24), s0 in [0, 2^30). With these bounds no cost of a valid point
+ * can overflow; a descriptor outside them is malformed and gets no points.
+ */
+static int fields_ok(const or_kernel* k)
+{
+    for (int c = 0; c < OR_NCLASS; ++c)
+        if (!(k->n32[c] >= 0.0f && k->n32[c] <= 1099511627776.0f)) return 0; /* 2^40; false for NaN */
+    if (!(k->d >= 0.0f && k->d <= 1.0f)) return 0;
+    return k->r0 >= 0 && k->r0 < (1 << 24) && k->s0 >= 0 && k->s0 < (1 << 30);
+}
+
 /* Space size of one descriptor, or -1 if its mask selects values beyond the axes. */
 int64_t or_space_size(const or_axes* ax, const void* rec)
 {
@@ -293,7 +307,9 @@ int64_t or_space_size(const or_axes* ax, const void* rec)
  * than k valid points -> pad with index -1, cost +inf).
  * Optional per-point outputs (any may be NULL) are written at
  * pt_off[kernel] + canonical index.
- * Returns 0, or -1 if a descriptor's mask is outside the axes.
+ * A malformed descriptor (mask outside the axes, or a field outside the
+ * ranges of fields_ok) gets padding only and no per-point outputs.
+ * Returns 0, or -1 if any descriptor was malformed.
  */
 int or_eval(const or_arch* a, const or_axes* ax, const void* descs, int64_t n_kernels, int64_t k,
             int32_t* topk_idx, float* topk_cost, int32_t* pt_B, int32_t* pt_W, float* pt_c32,
@@ -317,8 +333,12 @@ int or_eval(const or_arch* a, const or_axes* ax, const void* descs, int64_t n_ke
             int64_t ng = set_positions(kd.mask, 32, 16, ax->n_g, gp);
             int64_t nu = set_positions(kd.mask, 48, 8, ax->n_u, up);
             int64_t nc = set_positions(kd.mask, 56, 4, ax->n_c, cp);
-            if ((kd.mask >> 60) || nt < 0 || ng < 0 || nu < 0 || nc < 0) {
+            if ((kd.mask >> 60) || nt < 0 || ng < 0 || nu < 0 || nc < 0 || !fields_ok(&kd)) {
                 err = -1;
+                for (int64_t r = 0; r < k; ++r) {
+                    topk_idx[i * k + r] = -1;
+                    topk_cost[i * k + r] = INFINITY;
+                }
                 continue;
             }
             int64_t nvalid = 0, idx = 0;

@@ -137,12 +137,15 @@ def space_size(axes, desc):
     return lib().or_space_size(C.byref(a), rec.ctypes.data)
 
 
-def evaluate(row, axes, descs, k, emit=False, offsets=None, nthreads=0):
+def evaluate(row, axes, descs, k, emit=False, offsets=None, nthreads=0, strict=True):
     """Evaluate all points and select each kernel's top-k.
 
     Returns dict(idx=int32[n,k], cost=float32[n,k]) and, with emit=True,
     per-point arrays B, W (int32), cost32 (float32), cost64 (float64) laid
     out at offsets[kernel] + canonical index (offsets: int64[n+1]).
+    Malformed descriptors (mask outside the axes, counts outside [0, 2^40],
+    d outside [0, 1], r0 or s0 out of range) get padding; with strict=True
+    they raise ValueError, otherwise out["malformed"] is True.
     """
     descs = np.ascontiguousarray(descs)
     n = len(descs)
@@ -163,8 +166,9 @@ def evaluate(row, axes, descs, k, emit=False, offsets=None, nthreads=0):
     rc = lib().or_eval(C.byref(a), C.byref(ax), descs.ctypes.data, n, int(k), idx.ctypes.data,
                        cost.ctypes.data, _ptr(pB), _ptr(pW), _ptr(p32), _ptr(p64),
                        _ptr(offsets) if emit else None, int(nthreads))
-    if rc != 0:
-        raise ValueError("oracle: descriptor mask selects values outside the axes")
+    if rc != 0 and strict:
+        raise ValueError("oracle: malformed descriptor (mask outside the axes or a field out of range)")
+    out["malformed"] = rc != 0
     return out
 
 

@@ -111,15 +111,23 @@ __device__ __forceinline__ void unpack(const int4 (&v)[4], Desc& k)
     k.top = mhi >> 28;
 }
 
-// Malformed descriptor: mask outside the axes, or a field out of range.
+// Largest instruction count a descriptor may carry (2^40). With the architecture
+// row's bounds (IPC >= 2^-16, W_sat <= 2^20, K <= 2^24) and d <= 1, every cost of
+// a valid point stays below 2^114, so no FP32 cost overflows or turns into NaN.
+constexpr float kMaxCount = 0x1p40f;
+
+// Malformed descriptor: mask outside the axes, or a field out of range (counts
+// outside [0, 2^40] or not a number, d outside [0, 1], r0 outside [0, 2^24),
+// s0 outside [0, 2^30)).
 __device__ __forceinline__ bool desc_bad(const Desc& k, const tune_axes& x)
 {
     const uint32_t t_ok = x.n_t == 32 ? 0xffffffffu : ((1u << x.n_t) - 1u);
     const uint32_t g_ok = (1u << x.n_g) - 1u, u_ok = (1u << x.n_u) - 1u, c_ok = (1u << x.n_c) - 1u;
     bool bad = k.top != 0 || (k.tm & ~t_ok) || (k.gm & ~g_ok) || (k.um & ~u_ok) || (k.cm & ~c_ok) ||
-               k.r0 < 0 || k.r0 >= (1 << 24) || k.s0 < 0 || k.s0 >= (1 << 30) || !(k.d >= 0.0f);
+               k.r0 < 0 || k.r0 >= (1 << 24) || k.s0 < 0 || k.s0 >= (1 << 30) ||
+               !(k.d >= 0.0f && k.d <= 1.0f);
 #pragma unroll
-    for (int c = 0; c < 7; ++c) bad = bad || !(k.n[c] >= 0.0f);
+    for (int c = 0; c < 7; ++c) bad = bad || !(k.n[c] >= 0.0f && k.n[c] <= kMaxCount);
     return bad;
 }
 

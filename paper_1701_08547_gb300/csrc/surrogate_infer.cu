@@ -154,6 +154,8 @@ int tune_features(const tune_arch* arch, const tune_axes* axes, const tune_kerne
         return tune::fail(TUNE_EINVAL, "tune_features: bad arguments");
     if (n > 0 && (!descs || !sample_kernel || !sample_point || !feats))
         return tune::fail(TUNE_EINVAL, "tune_features: NULL array");
+    int rc = tune::validate_inputs(arch, axes);
+    if (rc) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     TUNE_CUDA_TRY(cudaMemsetAsync(workspace, 0, tune::kWorkspaceHeader, s), "tune_features: status reset");
     if (n == 0) return TUNE_OK;

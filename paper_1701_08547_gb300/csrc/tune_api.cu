@@ -27,15 +27,30 @@ void clear_error() { g_msg[0] = 0; }
 
 int device_sm_count()
 {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[kMaxDevices];
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    if (cached[dev] == 0) {
-        int n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+    int n = cached[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-        cached[dev] = n;
+        cached[dev].store(n, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return n;
+}
+
+int blocks_per_sm(std::atomic<int> (&cache)[kMaxDevices], const void* kern, int threads, int* out)
+{
+    int dev = 0;
+    TUNE_CUDA_TRY(cudaGetDevice(&dev), "occupancy query: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(TUNE_EUNSUPPORTED, "device ordinal %d too large", dev);
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
+        TUNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, 0), "occupancy query");
+        if (n < 1) n = 1;
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    *out = n;
+    return TUNE_OK;
 }
 
 }  // namespace tune

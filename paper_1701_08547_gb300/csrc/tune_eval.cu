@@ -973,12 +973,10 @@ int launch_thread(const EvalParams& p, const tune_kernel_desc* descs, int32_t* t
                   cudaStream_t s)
 {
     auto kern = tune_eval_thread_kernel<KMAX>;
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        TUNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsT, 0),
-                      "tune_eval: occupancy query");
-        if (per_sm < 1) per_sm = 1;
-    }
+    static std::atomic<int> per_sm_cache[tune::kMaxDevices];
+    int per_sm = 0;
+    int rc = tune::blocks_per_sm(per_sm_cache, reinterpret_cast<const void*>(kern), kThreadsT, &per_sm);
+    if (rc) return rc;
     const int sms = tune::device_sm_count();
     if (sms <= 0) return tune::fail(TUNE_ECUDA, "tune_eval: cannot query the SM count");
     const int64_t need = (p.n_kernels + kThreadsT - 1) / kThreadsT;
@@ -995,12 +993,10 @@ int launch_rows(const EvalParams& p, const tune_kernel_desc* descs, int32_t* ti,
                 unsigned long long* queue)
 {
     auto kern = tune_eval_kernel<EMIT, MULTI>;
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        TUNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0),
-                      "tune_eval: occupancy query");
-        if (per_sm < 1) per_sm = 1;
-    }
+    static std::atomic<int> per_sm_cache[tune::kMaxDevices];
+    int per_sm = 0;
+    int rc = tune::blocks_per_sm(per_sm_cache, reinterpret_cast<const void*>(kern), kThreads, &per_sm);
+    if (rc) return rc;
     const int sms = tune::device_sm_count();
     if (sms <= 0) return tune::fail(TUNE_ECUDA, "tune_eval: cannot query the SM count");
     const int64_t need = (p.n_kernels + kWarps - 1) / kWarps;
@@ -1028,9 +1024,17 @@ int launch(const EvalParams& p, const tune_kernel_desc* descs, int32_t* ti, floa
 
 int validate(const tune_arch* a, const tune_axes* x, int32_t k)
 {
-    using tune::fail;
+    if (k < 1 || k > 16) return tune::fail(TUNE_EINVAL, "k = %d outside [1, 16]", k);
+    return tune::validate_inputs(a, x);
+}
+
+}  // namespace
+
+namespace tune {
+
+int validate_inputs(const tune_arch* a, const tune_axes* x)
+{
     if (!a || !x) return fail(TUNE_EINVAL, "arch and axes must be non-NULL host pointers");
-    if (k < 1 || k > 16) return fail(TUNE_EINVAL, "k = %d outside [1, 16]", k);
     if (a->warp_size != 32) return fail(TUNE_EINVAL, "warp_size must be 32");
     if (a->n_sm < 1 || a->max_threads_block < 1 || a->max_warps_sm < 1 || a->max_warps_sm > kMaxW ||
         a->max_blocks_sm < 1 || a->max_blocks_sm > kMaxB)
@@ -1049,7 +1053,8 @@ int validate(const tune_arch* a, const tune_axes* x, int32_t k)
             a->smem_caps[i] > (1 << 24))
             return fail(TUNE_EINVAL, "arch: smem_caps must be ascending, in [0, 16 MB]");
     for (int c = 0; c < TUNE_NCLASS; ++c)
-        if (!(a->ipc[c] > 0.0f) || !isfinite(a->ipc[c])) return fail(TUNE_EINVAL, "arch: ipc[%d] must be > 0", c);
+        if (!(a->ipc[c] >= 0x1p-16f) || !isfinite(a->ipc[c]))
+            return fail(TUNE_EINVAL, "arch: ipc[%d] must be finite and >= 2^-16", c);
     if (a->w_sat < 1 || a->w_sat > (1 << 20) || a->work_scale < 1 || a->work_scale > (1 << 24))
         return fail(TUNE_EINVAL, "arch: w_sat or work_scale out of range");
     if (x->n_t < 1 || x->n_t > 32 || x->n_g < 1 || x->n_g > 16 || x->n_u < 1 || x->n_u > 8 ||
@@ -1069,7 +1074,7 @@ int validate(const tune_arch* a, const tune_axes* x, int32_t k)
     return TUNE_OK;
 }
 
-}  // namespace
+}  // namespace tune
 
 extern "C" int tune_eval(const tune_arch* arch, const tune_axes* axes, const tune_kernel_desc* descs,
                          int64_t n_kernels, int32_t k, uint32_t flags, int32_t* topk_idx,
@@ -1143,9 +1148,8 @@ constexpr size_t kNoallocScratchBytes = 4096;  // stated maximum scratch for one
 // call on a device: calls that overlap on the GPU race on it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+void* g_noalloc_ptr[tune::kMaxDevices] = {nullptr};
 
 // Device address of the scratch array for the current device, looked up once
 // per device (host code must not use the symbol itself: on the host it names a
@@ -1154,7 +1158,7 @@ int noalloc_scratch(void** out)
 {
     int dev = 0;
     TUNE_CUDA_TRY(cudaGetDevice(&dev), "tune_eval_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return tune::fail(TUNE_EUNSUPPORTED, "device ordinal %d too large", dev);
+    if (dev < 0 || dev >= tune::kMaxDevices) return tune::fail(TUNE_EUNSUPPORTED, "device ordinal %d too large", dev);
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
         void* p = nullptr;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "tune.h"
 
 namespace tune {
@@ -23,6 +25,18 @@ constexpr size_t kWorkspaceHeader = 256;
 
 // Number of SMs of the current device (cached per device).
 int device_sm_count();
+
+// Device ordinals the per-device caches cover.
+constexpr int kMaxDevices = 64;
+
+// Resident blocks per SM of `kern` launched with `threads` threads and no dynamic shared
+// memory on the current device (at least 1): the occupancy query runs once per device and
+// its answer is kept in cache[device] (one cache per kernel, shared by host threads).
+int blocks_per_sm(std::atomic<int> (&cache)[kMaxDevices], const void* kern, int threads, int* out);
+
+// Host-side checks of an architecture row and tuning axes against the limits stated
+// in tune.h (TUNE_EINVAL with a message, or TUNE_OK).
+int validate_inputs(const tune_arch* arch, const tune_axes* axes);
 
 // tune_eval's warp-schedule launch for one architecture row (flags: TUNE_SCHED_WARP
 // with its chunk / CTA fields), with a caller-chosen status word and queue counter.

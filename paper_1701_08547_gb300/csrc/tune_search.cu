@@ -273,9 +273,8 @@ extern "C" int tune_search(const tune_arch* arch, const tune_axes* axes, const t
     if (n_kernels > 0 && (!descs || !best_idx || !best_cost || !evals))
         return tune::fail(TUNE_EINVAL, "descs and outputs must be non-NULL");
     if ((reinterpret_cast<uintptr_t>(descs) & 15) != 0) return tune::fail(TUNE_EINVAL, "descs must be 16-byte aligned");
-    if (axes->n_t < 1 || axes->n_t > 32 || axes->n_g < 1 || axes->n_g > 16 || axes->n_u < 1 || axes->n_u > 8 ||
-        axes->n_c < 1 || axes->n_c > 4)
-        return tune::fail(TUNE_EINVAL, "axes: lengths out of range");
+    int rc = tune::validate_inputs(arch, axes);
+    if (rc) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     TUNE_CUDA_TRY(cudaMemsetAsync(workspace, 0, tune::kWorkspaceHeader, s), "tune_search: status reset");
     if (n_kernels == 0) return TUNE_OK;

@@ -132,9 +132,8 @@ extern "C" int tune_suggest(const tune_arch* arch, const tune_axes* axes, const 
         return tune::fail(TUNE_EINVAL, "tune_suggest: bad arguments");
     if (n_kernels > 0 && (!descs || !t_star || !occ_star || !r_headroom || !s_star || !t_rule))
         return tune::fail(TUNE_EINVAL, "tune_suggest: NULL array");
-    if (arch->warp_size != 32 || arch->max_warps_sm > 64 || arch->max_blocks_sm > 32 || arch->n_smem_caps < 1 ||
-        arch->n_smem_caps > 16 || axes->n_t < 1 || axes->n_t > 32)
-        return tune::fail(TUNE_EINVAL, "tune_suggest: arch or axes out of range");
+    int rc = tune::validate_inputs(arch, axes);
+    if (rc) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     TUNE_CUDA_TRY(cudaMemsetAsync(workspace, 0, tune::kWorkspaceHeader, s), "tune_suggest: status reset");
     if (n_kernels == 0) return TUNE_OK;

@@ -207,12 +207,10 @@ __global__ void __launch_bounds__(kThreads)
 int launch(const float* scores, const int64_t* off, int64_t n_seg, int k, int32_t* oi, float* os, cudaStream_t st)
 {
     auto kern = topk_segmented_kernel;
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        TUNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0),
-                      "tune_topk: occupancy query");
-        if (per_sm < 1) per_sm = 1;
-    }
+    static std::atomic<int> per_sm_cache[tune::kMaxDevices];
+    int per_sm = 0;
+    int rc = tune::blocks_per_sm(per_sm_cache, reinterpret_cast<const void*>(kern), kThreads, &per_sm);
+    if (rc) return rc;
     const int sms = tune::device_sm_count();
     if (sms <= 0) return tune::fail(TUNE_ECUDA, "tune_topk: cannot query the SM count");
     const int64_t need = (n_seg + kWarps - 1) / kWarps;

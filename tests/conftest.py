@@ -12,6 +12,14 @@ GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the compiled library")
+    config.addinivalue_line("markers", "run_last: run after every other collected test")
+
+
+def pytest_collection_modifyitems(session, config, items):
+    """Tests marked run_last go to the end of the run (stable otherwise), so that a run that
+    stops at the first failure has already run everything else when one of them fails."""
+    items[:] = [i for i in items if i.get_closest_marker("run_last") is None] + \
+               [i for i in items if i.get_closest_marker("run_last") is not None]
 
 
 def read_golden(name):

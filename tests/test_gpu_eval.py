@@ -257,3 +257,112 @@ def test_equal_cost_walks(dev, oracle, k):
     # per point bit for bit (costs of zero or subnormal size have no meaningful FP64 ratio)
     assert np.array_equal(g["B"], o["B"]) and np.array_equal(g["W"], o["W"])
     assert np.array_equal(g["cost32"].view(np.uint32), o["cost32"].view(np.uint32))
+
+
+# Grid sizes near 2^24 / 5 for a 5-SM row: many ipar(B*, G) = waves slots / (n_SM G) values
+# are distinct but closer than 2^-21 relative, so the kernel's order check fails and its
+# selection walks equal costs to the end ("relaxed"). With ipar near 0.2 (mantissa 1.6)
+# distinct values can round to one product X ipar, and the oracle's top-k then holds equal
+# costs whose ipar values (and grid positions) are out of order; the GPU must still give
+# the full sort's order (cost, then canonical index).
+NEAR_G = [2963331, 2980211, 3002178, 3009017, 3036783, 3060326, 3067565, 3108723, 3116643, 3136795,
+          3149478, 3154700, 3156302, 3255545, 3316942, 3346151]
+
+
+def _ipar_rows(n_sm, gs):
+    rows = []
+    for b in range(1, 33):
+        slots = n_sm * b
+        rows.append([np.float32((-(-g // slots)) * slots) / np.float32(n_sm * g) for g in gs])
+    return np.array(rows, dtype=np.float32)
+
+
+def _inverted_ties(oracle, d, ax, o, off, rows):
+    """Adjacent equal costs in the oracle's top-k whose ipar values are distinct and out of order."""
+    n = 0
+    for i in range(len(d)):
+        c = o["cost"][i]
+        for r in range(len(c) - 1):
+            if c[r] == c[r + 1] and np.isfinite(c[r]):
+                v = []
+                for p in o["idx"][i, r:r + 2]:
+                    G = oracle.decode_point(d[i], ax, p)[1]
+                    v.append(rows[o["B"][off[i] + p] - 1][ax["g"].index(G)])
+                n += v[0] > v[1]
+    return n
+
+
+@pytest.mark.parametrize("n_sm,gs", [(5, NEAR_G), (4, [2_200_000 + j for j in range(0, 48, 3)])])
+def test_near_equal_grid_factors(dev, oracle, n_sm, gs):
+    """Caller-supplied row and grid axis with nearly equal ipar values (the relaxed walk):
+    dense and uneven masks, k = 10 and 16, every schedule and the emitting pass, bit for bit."""
+    a = archs.arch("sm_103")
+    a["n_sm"] = n_sm
+    ax = gen.axes()
+    ax["g"] = list(gs)
+    rows = _ipar_rows(n_sm, gs)
+    gaps = []
+    for r in rows:
+        v = np.unique(r)
+        gaps.append(np.min(np.diff(v) / v[:-1]) if len(v) > 1 else 1.0)
+    assert min(gaps) <= 2.0 ** -21  # the premise: the kernel cannot rely on strict order
+    inverted = 0
+    for space, n in (("dense", 96), ("uneven", 256)):
+        d = gen.descriptors(n, 77, space)
+        off = gen.point_offsets(d)
+        for k in (10, 16):
+            g = gpu_eval(dev, a, ax, d, k, emit=True)
+            o = oracle.evaluate(a, ax, d, k, emit=True, offsets=off)
+            assert_same_topk(g, o)
+            assert_same_points(g, o)
+            inverted += _inverted_ties(oracle, d, ax, o, off, rows)
+    if n_sm == 5:
+        assert inverted > 0  # equal costs out of ipar order were met and ranked by index
+
+
+def test_field_bounds(dev, oracle):
+    """Counts at 2^40, d = 1 and an architecture row at its limits (IPC 2^-16, W_sat 2^20,
+    K 2^24), T = 1 and G = 1: finite costs up to about 2^107 equal the oracle bit for bit."""
+    from tests.test_oracle_bounds import extreme_arch, extreme_axes, extreme_descs
+
+    a, ax, d = extreme_arch(), extreme_axes(), extreme_descs()
+    g = gpu_eval(dev, a, ax, d, 5, emit=True)
+    o = oracle.evaluate(a, ax, d, 5, emit=True, offsets=gen.point_offsets(d))
+    assert_same_topk(g, o)
+    assert_same_points(g, o)
+    assert np.all(np.isfinite(g["cost32"][g["B"] > 0]))
+
+
+def test_out_of_range_fields(dev, oracle):
+    """Counts above 2^40 (1e36, +inf, NaN, negative), d outside [0, 1], r0 or s0 out of range:
+    each such descriptor gets padding and the status word reports TUNE_EINVAL; the others
+    equal the oracle; an architecture row with an IPC below 2^-16 is refused on the host."""
+    import paper_1701_08547_gb300 as T
+
+    a, ax = archs.arch("sm_103"), gen.axes()
+    d = gen.descriptors(12, 43, "uneven")
+    bad = [1, 4, 5, 7, 8, 10]
+    d["n"][1, 0] = np.float32(1e36)
+    d["n"][4, 6] = np.float32(np.inf)
+    d["n"][5, 2] = np.float32(np.nan)
+    d["d"][7] = np.float32(1.5)
+    d["n"][8, 3] = np.nextafter(np.float32(2.0 ** 40), np.float32(np.inf))
+    d["s0"][10] = 1 << 30
+    d["n"][0, 0] = np.float32(2.0 ** 40)  # at the bound: fine
+    dd = T.descs_to_device(d, dev)
+    for flags in (0, SCHED_THREAD):
+        ws = T.workspace(0, len(d), 6, dev)
+        idx, cost = T.tune_eval(a, ax, dd, 6, flags=flags, workspace_buf=ws)
+        with pytest.raises(T.TuneError) as e:
+            T.tune_check(ws)
+        assert e.value.code == -1
+        o = oracle.evaluate(a, ax, d, 6, strict=False)
+        assert o["malformed"]
+        assert np.array_equal(idx.cpu().numpy(), o["idx"])
+        assert np.array_equal(cost.cpu().numpy().view(np.uint32), o["cost"].view(np.uint32))
+        assert np.all(o["idx"][bad] == -1)
+    low = archs.arch("sm_103")
+    low["ipc"][1] = 2.0 ** -17
+    with pytest.raises(T.TuneError) as e:
+        T.tune_eval(low, ax, dd, 6)
+    assert e.value.code == -1

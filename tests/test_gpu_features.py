@@ -127,3 +127,47 @@ def test_infer_several_chunks_and_empty_spaces(dev, oracle):
         chosen = gi[kk]
         assert len(set(chosen.tolist())) == k and np.all(chosen >= 0)
         assert np.all(score[chosen] <= kth * 1.05 + 1e-12), (kk, score[chosen], kth)
+
+
+def test_fallback_decision_at_configured_threshold(dev, oracle):
+    """The per-kernel fallback at the configured std/mean threshold 0.1: for each kernel the
+    oracle's spread (FP64 forward on the same BF16 weights and features) of the points the
+    GPU's ensemble picked decides whether the kernel falls back; kernels whose largest spread
+    lies within 0.015 of the threshold are not compared (the GPU's FP32 forward moves a
+    member's prediction by up to about 1e-2, and a spread by about twice that at worst).
+    Kernels kept by the ensemble return its picks; kernels that fall back return the analytic
+    top-k, bit for bit."""
+    from paper_1701_08547_gb300.surrogate import Surrogate
+    import paper_1701_08547_gb300 as T
+
+    a, ax = archs.arch("sm_103"), gen.axes()
+    d = gen.descriptors(64, 51, "dense128")
+    off = gen.point_offsets(d)
+    members, k, thresh, band = 3, 5, 0.1, 0.015
+    flat = L.init_params(members, [61, 62, 63]).reshape(members, L.P)
+    flat[:, L.OFF_W5:L.OFF_W5 + L.WID] *= 2.5  # members disagree by about the threshold
+    flat = flat.ravel()
+    s = Surrogate(members=members, batch=1024)
+    s.set_params(flat)
+    dd = T.descs_to_device(d, dev)
+    picks, _, fb_none = s.infer(a, ax, dd, off, k, thresh=1e30)
+    idx, val, fb = s.infer(a, ax, dd, off, k, thresh=thresh)
+    picks, fb_none = picks.cpu().numpy(), fb_none.cpu().numpy()
+    idx, val, fb = idx.cpu().numpy(), val.cpu().numpy(), fb.cpu().numpy()
+    assert np.all(fb_none == 0)
+    analytic = oracle.evaluate(a, ax, d, k)
+    compared = {0: 0, 1: 0}
+    for kk in range(len(d)):
+        _, spread = _oracle_scores(oracle, a, ax, d[kk], flat, members)
+        m = spread[picks[kk]].max()
+        if fb[kk]:
+            assert np.array_equal(idx[kk], analytic["idx"][kk])
+            assert np.array_equal(val[kk].view(np.uint32), analytic["cost"][kk].view(np.uint32))
+        else:
+            assert np.array_equal(idx[kk], picks[kk])
+        if abs(m - thresh) <= band:
+            continue
+        want = int(m > thresh)
+        assert fb[kk] == want, (kk, m, fb[kk])
+        compared[want] += 1
+    assert compared[0] >= 8 and compared[1] >= 8, compared

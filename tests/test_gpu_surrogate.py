@@ -6,8 +6,9 @@ approximation (about 2^-11 relative) where
 the oracle uses FP64, so a stored BF16 value can land one BF16 step (2^-8
 relative) away from the oracle's; such flips pass through at most four
 layers. Forward outputs are compared with |dy| <= 2e-2 (1 + |y|), gradients
-by relative Frobenius error per tensor <= 3e-2; Adam, given the same
-gradients, to within FP32 rounding.
+by relative Frobenius error per tensor <= 3e-2 and element by element within
+6e-2 (|g| + rms(g)) of the oracle's entry g (rms over the tensor); Adam, given
+the same gradients, to within FP32 rounding.
 """
 
 import numpy as np
@@ -104,6 +105,19 @@ def test_gradients_match_oracle(dev):
             got = np.asarray(gm[name], np.float64).reshape(want.shape)
             rel = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30)
             assert rel <= 3e-2, (m, name, rel)
+            # element by element: an entry is a sum over the batch of products of BF16-rounded
+            # factors; the hardware tanh (about 2^-11 relative) moves about a quarter of the
+            # stored BF16 activations by one step (2^-8), and those flips spread through the
+            # layers below, so an entry may move by a small multiple of the tensor's typical
+            # entry even where the entry itself is near zero. A CPU model of exactly that
+            # rounding (FP32 sums, a 2^-11 tanh error, BF16 and FP16 storage) reaches
+            # 3.4e-2 (|g| + rms) on this batch; the bound leaves a factor 1.8. A wrong tile or
+            # a dropped term moves entries by the order of |g| + rms.
+            rms = np.sqrt(np.mean(want * want))
+            err = np.abs(got - want)
+            lim = 6e-2 * (np.abs(want) + rms)
+            assert np.all(err <= lim), (m, name, np.unravel_index(np.argmax(err - lim), err.shape),
+                                        float(np.max(err / (np.abs(want) + rms))))
 
 
 def test_training_forward_paths_agree(dev):

@@ -125,3 +125,39 @@ def test_flat_layout_round_trip():
     back = L.unpack(flat, 1)[0]
     for k in g:
         assert np.array_equal(np.asarray(back[k]).ravel(), np.asarray(g[k]).ravel())
+
+
+def test_fp8_forward_worked_example():
+    """A single path through the network, worked by hand: W1[0][0] = 1, W2[0][0] = 1/2,
+    W3[0][0] = -1/4, W4[0][0] = 2, w5[0] = 1, b5 = 1/2, every other weight and bias zero.
+    Each one-entry row quantises to the code +-448 with scale |w| / 448, so layer l gives
+    z = (s / 2) E4M3(2 h) (+-448) = (w / 2) E4M3(2 h). Rows of zeros keep scale 1 and code 0.
+    Input x = 1:
+      h1 = gelu(1) = 0.84119..., 2 h1 = 1.68238 = 13.46 steps of 1/8 -> 13/8 = 1.625,
+      z2 = 1.625 / 4 = 0.40625; h2 = gelu(z2) = 0.26719, 2 h2 = 0.53440 = 8.55 steps of
+      1/16 -> 9/16 = 0.5625, z3 = -0.5625 / 8 = -0.0703125; h3 = gelu(z3) = -0.033186,
+      2 h3 = -0.066371 = -8.4955 steps of 2^-7 -> -8/128 = -0.0625, z4 = -0.0625,
+      y = gelu(-0.0625) + 1/2.
+    Input x = 2:
+      2 gelu(2) = 3.9092 = 15.64 steps of 1/4 -> 4.0, z2 = 1; 2 gelu(1) -> 1.625 as above,
+      z3 = -0.203125; 2 gelu(z3) = -0.17043 = -10.91 steps of 2^-6 -> -11/64, z4 = -11/64,
+      y = gelu(-11/64) + 1/2.
+    The scale |w| / 448 is rounded to FP32 (as the kernel takes it), so these hold to about
+    2^-24 relative. The FP64 forward without quantisation differs (z2 = gelu(1) / 2 etc.) by
+    far more, so the example fixes where E4M3 rounding happens and the 2h scaling."""
+    def g(z):
+        return 0.5 * z * (1.0 + math.tanh(math.sqrt(2.0 / math.pi) * (z + 0.044715 * z ** 3)))
+
+    flat = np.zeros(L.P, dtype=np.float32)
+    p = L.unpack(flat, 1)[0]
+    p["W1"][0, 0], p["W2"][0, 0], p["W3"][0, 0], p["W4"][0, 0] = 1.0, 0.5, -0.25, 2.0
+    p["w5"][0], p["b5"][0] = 1.0, 0.5
+    X = np.zeros((2, L.IN))
+    X[0, 0], X[1, 0] = 1.0, 2.0
+    y = S.forward_fp8(p, X)
+    assert abs(y[0] - (g(-0.0625) + 0.5)) < 1e-8
+    assert abs(y[1] - (g(-11.0 / 64.0) + 0.5)) < 1e-8
+    # the intermediate values stated above
+    assert abs(g(1.0) - 0.8411919906) < 1e-9 and abs(g(0.40625) - 0.2671909895) < 1e-9
+    y_bf, _ = S.forward(p, X, bf=False)
+    assert abs(y_bf[0] - y[0]) > 1e-4 and abs(y_bf[1] - y[1]) > 1e-4

@@ -4,8 +4,9 @@ memory, or a budget fixed at start-up). Its scratch is a static array inside
 the library, so its results must equal tune_eval's, bit for bit, call after
 call: the array keeps the previous call's contents, which each call clears.
 
-Collected last on purpose (file name), so a failure here cannot hide
-failures elsewhere in a run that stops at the first one.
+Marked run_last (tests/conftest.py moves such tests to the end of the run; the
+file name also sorts last), so a failure here cannot hide failures elsewhere in
+a run that stops at the first one.
 """
 
 import ctypes as C
@@ -15,7 +16,7 @@ import pytest
 
 from workloads import archs, gen
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.run_last]
 
 
 @pytest.fixture(scope="module")
@@ -91,3 +92,45 @@ def test_noalloc_rejects_bad_arguments(lib):
     rc = lib.tune_eval_noalloc(C.byref(a), C.byref(x), fake, 1, 17, 0, fake, fake, None, None, None,
                                None, None)
     assert rc == -1
+
+
+def test_noalloc_emit_points_match_tune_eval(lib):
+    """TUNE_EMIT_POINTS through the static scratch: per-point B*, W* and cost equal
+    tune_eval's bit for bit, with one of the three per-point arrays NULL (left untouched),
+    on two calls in a row."""
+    import torch
+
+    import paper_1701_08547_gb300 as T
+    from paper_1701_08547_gb300 import native
+
+    stream = torch.cuda.current_stream()
+    a, ax = archs.arch("sm_103"), gen.axes()
+    d = gen.descriptors(90, 9, "uneven")
+    off = gen.point_offsets(d)
+    total, k = int(off[-1]), 4
+    dd = T.descs_to_device(d)
+    po = torch.from_numpy(off).cuda()
+    ref = [torch.empty(total, dtype=dt, device="cuda") for dt in (torch.int32, torch.int32, torch.float32)]
+    ref_i, ref_c = T.tune_eval(a, ax, dd, k, flags=T.TUNE_EMIT_POINTS, pt_blocks=ref[0], pt_warps=ref[1],
+                               pt_cost=ref[2], pt_offsets=po, stream=stream)
+    ref_np = [r.cpu().numpy() for r in ref]
+    for null in (1, 2):  # pt_warps NULL, then pt_cost NULL
+        pts = [torch.full((total,), 7, dtype=dt, device="cuda") for dt in (torch.int32, torch.int32, torch.float32)]
+        ptr = [C.c_void_p(t.data_ptr()) for t in pts]
+        ptr[null] = None
+        idx = torch.empty((90, k), dtype=torch.int32, device="cuda")
+        cost = torch.empty((90, k), dtype=torch.float32, device="cuda")
+        ax_, a_ = native.make_axes(ax), native.make_arch(a)
+        rc = lib.tune_eval_noalloc(C.byref(a_), C.byref(ax_), C.c_void_p(dd.data_ptr()), 90, k,
+                                   native.TUNE_EMIT_POINTS, C.c_void_p(idx.data_ptr()),
+                                   C.c_void_p(cost.data_ptr()), ptr[0], ptr[1], ptr[2],
+                                   C.c_void_p(po.data_ptr()), C.c_void_p(stream.cuda_stream))
+        assert rc == 0, lib.tune_last_error()
+        assert np.array_equal(idx.cpu().numpy(), ref_i.cpu().numpy())
+        assert np.array_equal(cost.cpu().numpy().view(np.uint32), ref_c.cpu().numpy().view(np.uint32))
+        got = [t.cpu().numpy() for t in pts]
+        for j in range(3):
+            if j == null:
+                assert np.all(got[j] == 7)
+            else:
+                assert np.array_equal(got[j].view(np.uint32), ref_np[j].view(np.uint32)), j
