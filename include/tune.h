@@ -289,7 +289,8 @@ int surrogate_members(const tune_surrogate* h);
  * operands MN-major), split over the batch and reduced in split order;
  * 3 = batch splits per member of those weight gradients (0, the default: SMs / (2 members)). */
 int surrogate_set_option(tune_surrogate* h, int option, int value);
-/* Synchronous: TUNE_ETIMEOUT if a bounded wait inside a surrogate kernel gave up. */
+/* Synchronous: TUNE_ETIMEOUT if a bounded wait inside a surrogate kernel gave up since the
+ * last check; the check clears the handle's status word. */
 int surrogate_status(tune_surrogate* h);
 
 /*
@@ -327,14 +328,21 @@ size_t surrogate_infer_workspace_bytes(int members, int64_t n_kernels, int32_t k
  * Section IV-A; these variants are the library's own, not Orio's.)
  * For sample i, descriptor descs[sample_kernel[i]] at point sample_point[i]
  * (canonical index) becomes a kernel compiled at run time (NVRTC, sm_103a)
- * that executes `items` work items; per item and instruction class it runs a
- * dependent loop of round(n_c * count_scale) operations, unrolled U times,
- * keeps registers live according to r0, uses s0 bytes of dynamic shared
- * memory, and repeats its FP32 loop on round(32 d) lanes of each warp. It is
- * launched with G blocks of T threads at carveout C: one untimed launch, then
- * `reps` launches timed with CUDA events. us[i] = median time in
- * microseconds (NaN where the launch is not possible, e.g. too many
- * registers for T); regs[i] = the variant's registers per thread.
+ * in which every thread executes `items` work items; per item and
+ * instruction class it runs a dependent loop of round(n_c * count_scale)
+ * operations, unrolled U times, keeps registers live according to r0, uses
+ * s0 bytes of dynamic shared memory, and repeats its FP32 loop on round(32 d)
+ * lanes of each warp. The per-thread work is therefore the same at every
+ * (T, G): the descriptor's counts are per thread, as in Eq. 6, and a launch of
+ * G blocks does G T items of work (time / (G T items) is what the model's
+ * cost ranks). It is launched with G blocks of T threads at carveout C: one
+ * untimed launch, then `reps` launches timed with CUDA events.
+ *   us[i]       median time of the launch in microseconds (NaN where the
+ *               launch is not possible, e.g. too many registers for T)
+ *   regs[i]     the variant's registers per thread
+ *   launched    NULL or int32[4 * n_samples]: the (T, G, U, C) the sample's
+ *               canonical index decoded to (row-major over T, G, U, C
+ *               restricted to the mask, C fastest), written before the launch
  * descs, sample arrays and outputs are host memory; the call allocates two
  * 4 MB device buffers for its duration and is synchronous. Returns
  * TUNE_ECOMPILE if a variant fails to compile.
@@ -342,7 +350,7 @@ size_t surrogate_infer_workspace_bytes(int members, int64_t n_kernels, int32_t k
 int tune_emit_measure(const tune_axes* axes, const tune_kernel_desc* descs, int64_t n_kernels,
                       const int32_t* sample_kernel, const int32_t* sample_point, int64_t n_samples,
                       int32_t items, float count_scale, int32_t reps, float* us, int32_t* regs,
-                      tune_stream_t stream);
+                      int32_t* launched, tune_stream_t stream);
 
 /*
  * tune_eval_archs — tune_eval of the same descriptors against n_arch
@@ -487,6 +495,34 @@ const char* tune_last_error(void);
 
 /* Library version, e.g. 100 for 0.1.0. */
 int tune_version(void);
+
+/*
+ * tune_inject_fault — make the library's failure paths run on purpose, for
+ * testing a caller's error handling (library tooling; the paper has no
+ * counterpart). Sets the number of pending faults of one kind (0 clears);
+ * each fault is used up once. Nothing here faults or hangs the GPU: the
+ * failures are made on the host, or by a kernel that leaves a copy unissued
+ * and gives up its bounded wait on it early.
+ *   TUNE_FAULT_COMPILE   the next `count` variant modules that tune_emit_measure
+ *                        or tune_real_measure request fail as if run-time
+ *                        compilation had rejected them (TUNE_ECOMPILE; nothing
+ *                        is cached)
+ *   TUNE_FAULT_SLOW_REP  the next `count` timed repetitions of those calls
+ *                        read one second longer, as if the GPU had been taken
+ *                        away meanwhile (the median of reps >= 3 discards a
+ *                        single such repetition)
+ *   TUNE_FAULT_WAIT      the next `count` launches of the surrogate's per-layer
+ *                        tcgen05 forward GEMM (option 1 = 0, option 0 = 1)
+ *                        leave their first operand copy unissued, so its wait
+ *                        gives up after a short bound: every CTA records the
+ *                        timeout, waits for the copies it did issue, frees its
+ *                        tensor memory and returns without writing its output;
+ *                        surrogate_status then returns TUNE_ETIMEOUT
+ */
+#define TUNE_FAULT_COMPILE 1
+#define TUNE_FAULT_SLOW_REP 2
+#define TUNE_FAULT_WAIT 3
+int tune_inject_fault(int kind, int count);
 
 #ifdef __cplusplus
 }

@@ -2,7 +2,9 @@
 // at run time (NVRTC, sm_103a), run each sampled tuning point on this GPU and
 // time it — the labels of the learned surrogate.
 //
-// A variant executes `items` work items in a grid-stride loop; per item it
+// Every thread of a variant executes `items` work items (the same per-thread
+// work at every launch configuration, as the static model assumes: its counts
+// are per thread, and its cost is the time per unit of that work); per item it
 // runs, for each instruction class, a dependent loop of round(n_c * scale)
 // operations (FP32 FMA, FP64 FMA, integer LCG step, global load, shared
 // load + store, data-dependent branch, SFU sine), unrolled U times; lanes
@@ -44,8 +46,7 @@ extern "C" __global__ void variant(const float* __restrict__ src, float* __restr
         for (int i = threadIdx.x; i <= smem_mask; i += blockDim.x) sm[i] = (float)i;
         __syncthreads();
     }
-    const int stride = gridDim.x * blockDim.x;
-    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < items; item += stride) {
+    for (int item = 0; item < items; ++item) {
 #pragma unroll
         for (int i = 0; i < NACC; ++i) asm volatile("" : "+f"(keep[i]));
 #pragma unroll UNROLL
@@ -100,6 +101,8 @@ int nacc_bucket(int r0)
 int get_module(int dev, int unroll, int nacc, Module** out)
 {
     std::lock_guard<std::mutex> lock(g_mu);
+    if (tune::take_fault(TUNE_FAULT_COMPILE))
+        return tune::fail(TUNE_ECOMPILE, "variant compile failed (injected fault)");
     auto key = std::make_tuple(dev, unroll, nacc);
     auto it = g_mods.find(key);
     if (it != g_mods.end()) {
@@ -164,7 +167,7 @@ struct DevBuf {
 extern "C" int tune_emit_measure(const tune_axes* axes, const tune_kernel_desc* descs, int64_t n_kernels,
                                  const int32_t* sample_kernel, const int32_t* sample_point, int64_t n_samples,
                                  int32_t items, float count_scale, int32_t reps, float* us, int32_t* regs,
-                                 tune_stream_t stream)
+                                 int32_t* launched, tune_stream_t stream)
 {
     tune::clear_error();
     if (!axes || !descs || !sample_kernel || !sample_point || !us || !regs || n_samples < 0 || items < 1 ||
@@ -212,6 +215,12 @@ extern "C" int tune_emit_measure(const tune_axes* axes, const tune_kernel_desc* 
         const int g_r = p % nG, t_r = p / nG;
         const int T = axes->t[nth(tm, t_r)], G = axes->g[nth(gm, g_r)], U = axes->u[nth(um, u_r)],
                   C = axes->c[nth(cm, c_r)];
+        if (launched) {
+            launched[4 * i] = T;
+            launched[4 * i + 1] = G;
+            launched[4 * i + 2] = U;
+            launched[4 * i + 3] = C;
+        }
         Module* mod = nullptr;
         int rc = get_module(dev, U, nacc_bucket(d.r0), &mod);
         if (rc) return rc;
@@ -250,8 +259,10 @@ extern "C" int tune_emit_measure(const tune_axes* axes, const tune_kernel_desc* 
             TUNE_CUDA_TRY(cudaEventRecord(ev.e[2 * r + 1], s), "tune_emit_measure: event");
         }
         TUNE_CUDA_TRY(cudaStreamSynchronize(s), "tune_emit_measure: sync");
-        for (int r = 0; r < reps; ++r)
+        for (int r = 0; r < reps; ++r) {
             TUNE_CUDA_TRY(cudaEventElapsedTime(&t[r], ev.e[2 * r], ev.e[2 * r + 1]), "tune_emit_measure: elapsed");
+            if (tune::take_fault(TUNE_FAULT_SLOW_REP)) t[r] += 1000.0f;  // injected: one second more
+        }
         std::sort(t.begin(), t.end());
         us[i] = 1000.0f * t[reps / 2];
     }

@@ -55,6 +55,8 @@ std::map<std::pair<int, int>, RealModule> g_real_mods;  // (device, unroll)
 int real_module(int dev, int unroll, RealModule** out)
 {
     std::lock_guard<std::mutex> lock(g_real_mu);
+    if (tune::take_fault(TUNE_FAULT_COMPILE))
+        return tune::fail(TUNE_ECOMPILE, "real kernel compile failed (injected fault)");
     auto key = std::make_pair(dev, unroll);
     auto it = g_real_mods.find(key);
     if (it != g_real_mods.end()) {
@@ -197,8 +199,10 @@ extern "C" int tune_real_measure(int32_t kernel, int32_t n, const int32_t* T, co
             TUNE_CUDA_TRY(cudaEventRecord(ev[2 * q + 1], s), "tune_real_measure: event");
         }
         TUNE_CUDA_TRY(cudaStreamSynchronize(s), "tune_real_measure: sync");
-        for (int q = 0; q < reps; ++q)
+        for (int q = 0; q < reps; ++q) {
             TUNE_CUDA_TRY(cudaEventElapsedTime(&t[q], ev[2 * q], ev[2 * q + 1]), "tune_real_measure: elapsed");
+            if (tune::take_fault(TUNE_FAULT_SLOW_REP)) t[q] += 1000.0f;  // injected: one second more
+        }
         std::sort(t.begin(), t.end());
         us[v] = 1000.0f * t[reps / 2];
         if (v == 0 && result) {

@@ -477,6 +477,7 @@ int tc_layer(tune_surrogate* h, int l, int n_pad, cudaStream_t s, const __nv_bfl
     g.H = h->H[l];
     g.sH = (long long)h->batch * WID;
     g.status = h->status;
+    g.fault_skip_first = tune::take_fault(TUNE_FAULT_WAIT) ? 1 : 0;
     const int smem = tc::smem_bytes(WID);
     static std::atomic<uint64_t> attr{0};
     rc = smem_attr(tc::gemm_fwd_kernel, smem, attr, "surrogate: tc smem attribute");
@@ -911,6 +912,7 @@ int surrogate_status(tune_surrogate* h)
     if (!h) return tune::fail(TUNE_EINVAL, "surrogate_status: NULL handle");
     int st = 0;
     TUNE_CUDA_TRY(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost), "surrogate_status: copy");
+    if (st) TUNE_CUDA_TRY(cudaMemset(h->status, 0, sizeof(int)), "surrogate_status: clear");
     if (st & 2) return tune::fail(TUNE_ETIMEOUT, "a bounded wait in a surrogate kernel gave up");
     return TUNE_OK;
 }

@@ -26,6 +26,7 @@ constexpr int kThreads = 256;  // eight warps: two per TMEM lane quarter (column
 constexpr int BM = 128;        // rows per CTA (UMMA M)
 constexpr int BK = 64;         // K elements per chunk (one 128-byte swizzle span)
 constexpr long long kSpin = 1LL << 22;  // try_wait iterations before giving up
+constexpr long long kSpinShort = 1LL << 10;  // the first wait of a launch with an injected fault
 
 struct Args {
     int M, N, K;
@@ -37,6 +38,7 @@ struct Args {
     __nv_bfloat16* H;       // [members][M][N]
     long long sH;
     int* status;            // bit 2 (timeout) set on a wait that gives up
+    int fault_skip_first;   // injected fault: chunk 0 is never loaded; its wait gives up after kSpinShort
 };
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -59,10 +61,10 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Bounded wait; false (and the status bit) after kSpin unsuccessful polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* status)
+// Bounded wait; false (and the status bit) after `limit` unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* status, long long limit = kSpin)
 {
-    for (long long i = 0; i < kSpin; ++i)
+    for (long long i = 0; i < limit; ++i)
         if (mbar_try(b, parity)) return true;
     atomicOr(status, 2);
     return false;
@@ -175,13 +177,17 @@ __global__ void __launch_bounds__(kThreads) gemm_fwd_kernel(const __grid_constan
             tma_load_3d(sA + st * a_bytes, &ta, c * BK, m0, g.batched_a ? member : 0, &bar_full[st]);
             tma_load_3d(sB + st * b_bytes, &tb, c * BK, 0, member, &bar_full[st]);
         };
-        for (int c = 0; c < n_chunks && c < kStages; ++c) load(c);
+        // with an injected fault chunk 0 is never requested (nothing is in flight for it), so
+        // its wait below runs out after kSpinShort polls and the CTA takes the timeout path
+        const bool skip0 = g.fault_skip_first != 0;
+        for (int c = 0; c < n_chunks && c < kStages; ++c)
+            if (!(skip0 && c == 0)) load(c);
         const uint32_t idesc = idesc_bf16(BM, g.N);
-        int loaded = n_chunks < kStages ? n_chunks : kStages;
+        int loaded = n_chunks < kStages ? n_chunks : kStages;  // chunks 0 .. loaded-1 requested
         bool ok = true;
         for (int c = 0; c < n_chunks; ++c) {
             const int st = c % kStages;
-            ok = mbar_wait(&bar_full[st], (c / kStages) & 1, g.status);
+            ok = mbar_wait(&bar_full[st], (c / kStages) & 1, g.status, skip0 && c == 0 ? kSpinShort : kSpin);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
@@ -201,7 +207,8 @@ __global__ void __launch_bounds__(kThreads) gemm_fwd_kernel(const __grid_constan
         if (!ok) {
             ok_flag = 0;
             // let the copies already issued finish before the CTA exits
-            for (int c = 0; c < loaded; ++c) mbar_wait(&bar_full[c % kStages], (c / kStages) & 1, g.status);
+            for (int c = skip0 ? 1 : 0; c < loaded; ++c)
+                mbar_wait(&bar_full[c % kStages], (c / kStages) & 1, g.status);
         }
         mma_commit(&bar_mma);  // arrives when the issued MMAs (if any) complete
     }

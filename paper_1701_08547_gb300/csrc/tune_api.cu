@@ -38,6 +38,18 @@ int device_sm_count()
     return n;
 }
 
+// Pending injected faults per kind (index = TUNE_FAULT_* value).
+static std::atomic<int> g_faults[4];
+
+bool take_fault(int kind)
+{
+    if (kind < 1 || kind > 3) return false;
+    int n = g_faults[kind].load();
+    while (n > 0)
+        if (g_faults[kind].compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
+
 int blocks_per_sm(std::atomic<int> (&cache)[kMaxDevices], const void* kern, int threads, int* out)
 {
     int dev = 0;
@@ -60,6 +72,16 @@ extern "C" {
 const char* tune_last_error(void) { return tune::g_msg; }
 
 int tune_version(void) { return 100; }
+
+int tune_inject_fault(int kind, int count)
+{
+    tune::clear_error();
+    if (kind < TUNE_FAULT_COMPILE || kind > TUNE_FAULT_WAIT)
+        return tune::fail(TUNE_EINVAL, "tune_inject_fault: unknown kind %d", kind);
+    if (count < 0 || count > 1000000) return tune::fail(TUNE_EINVAL, "tune_inject_fault: count outside [0, 10^6]");
+    tune::g_faults[kind].store(count);
+    return TUNE_OK;
+}
 
 size_t tune_workspace_bytes(int call, int64_t n, int32_t k)
 {

@@ -34,6 +34,10 @@ constexpr int kMaxDevices = 64;
 // its answer is kept in cache[device] (one cache per kernel, shared by host threads).
 int blocks_per_sm(std::atomic<int> (&cache)[kMaxDevices], const void* kern, int threads, int* out);
 
+// Injected faults (tune_inject_fault): true, and one fewer pending, if a fault of this
+// kind is pending.
+bool take_fault(int kind);
+
 // Host-side checks of an architecture row and tuning axes against the limits stated
 // in tune.h (TUNE_EINVAL with a message, or TUNE_OK).
 int validate_inputs(const tune_arch* arch, const tune_axes* axes);
