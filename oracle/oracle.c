@@ -418,6 +418,17 @@ int or_topk(const float* scores, const int64_t* off, int64_t n_seg, int64_t k, i
     return 0;
 }
 
+/* Round to bfloat16 through float32 (round to nearest, ties to even), as a double. */
+static double bf16_round(double x)
+{
+    float f = (float)x;
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    b = (b + 0x7fffu + ((b >> 16) & 1u)) & 0xffff0000u;
+    memcpy(&f, &b, 4);
+    return (double)f;
+}
+
 /*
  * The surrogate's 48 input features of one point (T, G, U, C) of a kernel,
  * in FP64: fixed scalings of the descriptor, the launch parameters and the
@@ -485,6 +496,7 @@ int or_features(const or_arch* a, const void* rec, int64_t T, int64_t G, int64_t
     f[42] = (double)o.cap / 233472.0;
     f[43] = (double)s_alloc / 65536.0;
     f[44] = log2(k.n[C_BRANCH] / (double)U + 1.0) / 20.0;
-    f[45] = f[46] = f[47] = 0.0;
+    /* what BF16 storage of the three cost features drops, scaled by 256 */
+    for (int j = 0; j < 3; ++j) f[45 + j] = (f[38 + j] - bf16_round(f[38 + j])) * 256.0;
     return 0;
 }

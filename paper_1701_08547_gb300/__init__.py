@@ -12,7 +12,7 @@ from . import native
 from .native import (TUNE_EMIT_POINTS, TUNE_SCHED_CHUNK, TUNE_SCHED_CTAS,  # noqa: F401
                      TUNE_SCHED_THREAD, TUNE_SCHED_WARP, TuneError)
 
-__all__ = ["tune_eval", "tune_eval_archs", "tune_topk", "tune_autotune", "tune_features", "tune_suggest", "tune_search", "tune_eval_host", "tune_workspace_bytes", "tune_check",
+__all__ = ["tune_eval", "tune_eval_archs", "tune_topk", "tune_autotune", "tune_features", "tune_suggest", "tune_search", "tune_eval_host", "tune_workspace_bytes", "tune_check", "tune_inject_fault",
            "descs_to_device", "TUNE_EMIT_POINTS", "TUNE_SCHED_WARP", "TUNE_SCHED_THREAD",
            "TUNE_SCHED_CHUNK", "TUNE_SCHED_CTAS", "TuneError"]
 
@@ -226,6 +226,12 @@ def tune_eval_host(arch, axes, host_descs, k, chunk, topk_idx, topk_cost, scratc
                           _ptr(topk_cost), int(chunk), _ptr(scratch), scratch.numel(), _stream(stream))
     native.check(rc)
     return scratch
+
+
+def tune_inject_fault(kind, count=1):
+    """Set `count` pending injected faults of one kind (native.TUNE_FAULT_COMPILE,
+    TUNE_FAULT_SLOW_REP or TUNE_FAULT_WAIT; 0 clears), to exercise failure paths."""
+    native.check(native.load().tune_inject_fault(int(kind), int(count)))
 
 
 def tune_check(workspace_buf, stream=None):

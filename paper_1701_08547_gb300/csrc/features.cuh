@@ -13,8 +13,13 @@
 //  35    log2 waves / 10   36  par / n_SM   37  hide / 32
 //  38-40 log2(cost + 1), log2(C_nm + 1), log2(C_m + 1), each / 40
 //  41    log2(G T) / 26   42  capacity / 233472   43  block allocation / 65536
-//  44    log2(n_BRANCH / U + 1) / 20       45-47 zero
+//  44    log2(n_BRANCH / U + 1) / 20
+//  45-47 256 (f - bf16(f)) for f = features 38, 39, 40: what BF16 storage drops of the
+//        three cost terms, so that f + f_45..47 / 256 carries them to about 2^-16 (the
+//        cost feature alone resolves costs to only 5-11 % once stored in BF16)
 #pragma once
+
+#include <cuda_bf16.h>
 
 #include "eval_common.cuh"
 
@@ -113,7 +118,8 @@ __device__ __forceinline__ void point_features(const tune_arch& a, const Desc& k
     f[42] = (float)cap / 233472.0f;
     f[43] = (float)s_alloc / 65536.0f;
     f[44] = log2f(__fdiv_rn(kd.n[CL_BRANCH], (float)U) + 1.0f) / 20.0f;
-    f[45] = f[46] = f[47] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) f[45 + j] = (f[38 + j] - __bfloat162float(__float2bfloat16_rn(f[38 + j]))) * 256.0f;
 }
 
 // Canonical index -> axis positions of (T, G, U, C) for a descriptor's masks (carveout fastest).

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtune.so")
 TUNE_OK, TUNE_EINVAL, TUNE_ENOMEM, TUNE_ECUDA, TUNE_ETIMEOUT, TUNE_ECOMPILE, TUNE_EUNSUPPORTED = (
     0, -1, -2, -3, -4, -5, -6)
 TUNE_EMIT_POINTS = 0x1
+TUNE_FAULT_COMPILE, TUNE_FAULT_SLOW_REP, TUNE_FAULT_WAIT = 1, 2, 3
 TUNE_SCHED_WARP, TUNE_SCHED_THREAD = 0x10, 0x20
 TUNE_HOST_DIRECT = 0x40
 
@@ -98,6 +99,8 @@ def load():
     L.tune_eval_host_scratch_bytes.restype = sz
     L.tune_eval_host.argtypes = [C.POINTER(TuneArch), C.POINTER(TuneAxes), vp, i64, i32, u32, vp, vp, i64, vp, sz, vp]
     L.tune_eval_host.restype = C.c_int
+    L.tune_inject_fault.argtypes = [C.c_int, C.c_int]
+    L.tune_inject_fault.restype = C.c_int
     _lib = L
     return L
 

@@ -1,12 +1,19 @@
 """Surrogate data generation, training and evaluation on the GPU (driver code).
 
 * label generation: tune_emit_measure times synthetic variants of sampled
-  (descriptor, point) pairs on this GPU; the label is ln(median microseconds);
+  (descriptor, point) pairs on this GPU. Every thread of a variant runs the
+  descriptor's per-thread work, so a launch of G blocks of T threads does
+  G T units of it; the label is ln(nanoseconds per unit of work) =
+  ln(1000 us / (G T ITEMS)), the quantity the static model's cost ranks (its
+  counts are per thread; its launch-shape terms spread G T units of work over
+  the busy SMs);
 * features: tune_features (the analyzer's internals for each sample);
 * training: surrogate_train (the library's BF16 kernels) over seeded epochs;
 * evaluation: held-out descriptors whose small spaces are timed completely;
-  hit@5 = the measured-best point is among the 5 a ranking picks, for the
-  ensemble (with its analytic fallback) and for the analytic model alone.
+  hit@5 = the measured-best point (least time per unit of work) is among the
+  5 a ranking picks, for the ensemble (with its analytic fallback), for the
+  analytic model alone, and for 5 uniform random picks (the chance floor),
+  each with a 95 % Wilson interval over the kernels.
 
 All random choices (descriptors, sampled points, epoch orders, initial
 weights) are seeded; the seeds are arguments.
@@ -20,11 +27,11 @@ from . import native
 from . import descs_to_device, tune_eval, tune_features, tune_suggest
 from .surrogate import Surrogate
 
-ITEMS = 65536
+ITEMS = 1                 # work items per thread
 COUNT_SCALE = 1.0 / 1024.0
-# Sub-space sampled for labels: threads >= 64, grid >= 64 blocks (axis positions), so
-# that every variant finishes in tens of microseconds.
-T_MIN_POS, G_MIN_POS = 1, 6
+# Sub-space sampled for labels: threads >= 64, grid 64 .. 4096 blocks (axis positions), so
+# that every variant finishes within a few milliseconds.
+T_MIN_POS, G_MIN_POS, G_MAX_POS = 1, 6, 12
 # Held-out spaces, fully timed: 5 thread counts x 4 grids x unroll {1, 4} x carveout {0, 100}
 EVAL_T, EVAL_G, EVAL_U, EVAL_C = [1, 3, 7, 15, 31], [7, 9, 11, 13], [0, 3], [0, 3]
 # Pruning spaces, fully timed: all 32 thread counts x grids {512, 2048} x unroll 1 x carveout 100
@@ -36,14 +43,15 @@ def _emit_lib():
     if not getattr(L, "_emit_declared", False):
         vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
         L.tune_emit_measure.argtypes = [C.POINTER(native.TuneAxes), vp, i64, vp, vp, i64, i32, C.c_float, i32,
-                                        vp, vp, vp]
+                                        vp, vp, vp, vp]
         L.tune_emit_measure.restype = C.c_int
         L._emit_declared = True
     return L
 
 
-def measure(axes, descs, skern, spoint, items=ITEMS, scale=COUNT_SCALE, reps=3, stream=None):
-    """Median runtime (us; NaN where not launchable) and registers of each sample's variant."""
+def measure(axes, descs, skern, spoint, items=ITEMS, scale=COUNT_SCALE, reps=3, stream=None, launched=False):
+    """Median launch time (us; NaN where not launchable) and registers of each sample's variant;
+    with launched=True also the (T, G, U, C) each sample decoded to (int32 [n, 4])."""
     import torch
 
     L = _emit_lib()
@@ -52,22 +60,29 @@ def measure(axes, descs, skern, spoint, items=ITEMS, scale=COUNT_SCALE, reps=3, 
     sp = np.ascontiguousarray(spoint, dtype=np.int32)
     us = np.empty(len(sk), dtype=np.float32)
     regs = np.empty(len(sk), dtype=np.int32)
+    cfg = np.zeros((len(sk), 4), dtype=np.int32)
     s = torch.cuda.current_stream() if stream is None else stream
     x = native.make_axes(axes)
     native.check(L.tune_emit_measure(C.byref(x), d.ctypes.data, len(d), sk.ctypes.data, sp.ctypes.data, len(sk),
                                      int(items), float(scale), int(reps), us.ctypes.data, regs.ctypes.data,
-                                     C.c_void_p(s.cuda_stream)))
-    return us, regs
+                                     cfg.ctypes.data, C.c_void_p(s.cuda_stream)))
+    return (us, regs, cfg) if launched else (us, regs)
+
+
+def per_unit_ns(us, cfg, items=ITEMS):
+    """Nanoseconds per unit of per-thread work: 1000 us / (G T items) (NaN stays NaN)."""
+    return 1000.0 * np.asarray(us, np.float64) / (cfg[:, 1].astype(np.float64) * cfg[:, 0] * items)
 
 
 def sample_points(descs, per_desc, seed):
-    """per_desc random canonical point indices per descriptor, restricted to T and G >= 64."""
+    """per_desc random canonical point indices per descriptor, restricted to T >= 64 and
+    64 <= G <= 4096."""
     rng = np.random.default_rng(seed)
     skern, spoint = [], []
     for i, d in enumerate(descs):
         m = int(d["space_mask"])
         tp = [b for b in range(32) if (m >> b) & 1 and b >= T_MIN_POS]
-        gp = [b for b in range(16) if (m >> (32 + b)) & 1 and b >= G_MIN_POS]
+        gp = [b for b in range(16) if (m >> (32 + b)) & 1 and G_MIN_POS <= b <= G_MAX_POS]
         up = [b for b in range(8) if (m >> (48 + b)) & 1]
         cp = [b for b in range(4) if (m >> (56 + b)) & 1]
         if not (tp and gp and up and cp):
@@ -83,19 +98,48 @@ def sample_points(descs, per_desc, seed):
 
 
 def build_set(arch, axes, descs, per_desc, seed, dev):
-    """Measured training set: features (device bf16), labels ln(us) (device), kept samples."""
+    """Measured training set: features (device bf16), labels ln(ns per unit of work) (device),
+    kept samples."""
     import torch
 
     skern, spoint = sample_points(descs, per_desc, seed)
-    us, _ = measure(axes, descs, skern, spoint)
+    us, _, cfg = measure(axes, descs, skern, spoint, launched=True)
+    ns = per_unit_ns(us, cfg)
     feats = tune_features(arch, axes, descs_to_device(descs, dev), torch.from_numpy(skern).to(dev),
                           torch.from_numpy(spoint).to(dev))
     valid = feats[:, 29].float().cpu().numpy() > 0  # B* > 0 under the model
-    keep = np.isfinite(us) & (us > 0) & valid
+    keep = np.isfinite(ns) & (ns > 0) & valid
     idx = torch.from_numpy(np.nonzero(keep)[0]).to(dev)
     return {"feats": feats[idx].contiguous(),
-            "labels": torch.from_numpy(np.log(us[keep]).astype(np.float32)).to(dev),
+            "labels": torch.from_numpy(np.log(ns[keep]).astype(np.float32)).to(dev),
             "n": int(keep.sum()), "measured": len(us), "us": us}
+
+
+def analytic_set(arch, axes, descs, per_desc, seed, dev):
+    """Training set labelled by the analytic model itself (the surrogate's sanity case): the
+    same sampled points and features as build_set, label ln(cost) - (its median) from
+    tune_eval's per-point costs (a constant shift changes neither the ranking nor the members'
+    std / mean); points without a valid configuration are dropped."""
+    import torch
+
+    from workloads import gen
+
+    skern, spoint = sample_points(descs, per_desc, seed)
+    dd = descs_to_device(descs, dev)
+    off = gen.point_offsets(descs)
+    total = int(off[-1])
+    pc = torch.empty(total, dtype=torch.float32, device=dev)
+    tune_eval(arch, axes, dd, 1, flags=native.TUNE_EMIT_POINTS, pt_cost=pc,
+              pt_offsets=torch.from_numpy(off).to(dev))
+    cost = pc.cpu().numpy()[off[skern] + spoint].astype(np.float64)
+    feats = tune_features(arch, axes, dd, torch.from_numpy(skern).to(dev), torch.from_numpy(spoint).to(dev))
+    keep = np.isfinite(cost) & (cost > 0)
+    idx = torch.from_numpy(np.nonzero(keep)[0]).to(dev)
+    lab = np.log(cost[keep])
+    shift = float(np.median(lab))
+    return {"feats": feats[idx].contiguous(),
+            "labels": torch.from_numpy((lab - shift).astype(np.float32)).to(dev),
+            "n": int(keep.sum()), "measured": len(cost), "label_shift": shift}
 
 
 def train(data, members=5, epochs=20, batch=8192, lr=1e-3, seed=5, dev="cuda"):
@@ -125,18 +169,39 @@ def eval_spaces(descs):
     return out
 
 
-def evaluate(sur, arch, axes, descs, dev, k=5, thresh=0.1):
-    """Against the measured best of fully timed held-out spaces: hit@k (best among the k picks),
-    overlap of the k picks with the measured k best, and the median slowdown of the first pick,
-    for the ensemble (with its analytic fallback at `thresh`) and for the analytic model."""
+def wilson(hits, n, z=1.96):
+    """95 % Wilson score interval of a binomial proportion hits / n."""
+    if n == 0:
+        return [0.0, 1.0]
+    p = hits / n
+    c = (p + z * z / (2 * n)) / (1 + z * z / n)
+    h = z * np.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / (1 + z * z / n)
+    return [float(max(0.0, c - h)), float(min(1.0, c + h))]
+
+
+def timed_spaces(axes, descs):
+    """Time every point of each descriptor's held-out space: (descriptors with those spaces,
+    ns per unit of work [n, size], NaN where not launchable)."""
     from workloads import gen
 
     d = eval_spaces(descs)
     size = int(gen.space_sizes(d[:1])[0])
     skern = np.repeat(np.arange(len(d)), size)
     spoint = np.tile(np.arange(size), len(d)).astype(np.int32)
-    us, _ = measure(axes, d, skern, spoint)
-    us = us.reshape(len(d), size)
+    us, _, cfg = measure(axes, d, skern, spoint, launched=True)
+    return d, per_unit_ns(us, cfg).reshape(len(d), size)
+
+
+def evaluate(sur, arch, axes, descs, dev, k=5, thresh=0.1, timed=None):
+    """Against the measured best (least time per unit of work) of fully timed held-out spaces:
+    hit@k (best among the k picks), overlap of the k picks with the measured k best, and the
+    median slowdown of the first pick, for the ensemble (with its analytic fallback at
+    `thresh`) and for the analytic model; the chance floor of k uniform picks among the
+    launchable points; 95 % Wilson intervals of the hit rates. `timed` reuses timed_spaces()."""
+    from workloads import gen
+
+    d, us = timed if timed is not None else timed_spaces(axes, descs)
+    size = us.shape[1]
     dd = descs_to_device(d, dev)
     a_idx, _ = tune_eval(arch, axes, dd, k)
     s_idx, _, fb = sur.infer(arch, axes, dd, gen.point_offsets(d), k, thresh)
@@ -151,11 +216,15 @@ def evaluate(sur, arch, axes, descs, dev, k=5, thresh=0.1):
         ov = np.array([len(set(idx[i]) & set(meas_top[i])) / k for i in range(len(d))])[ok]
         first = np.array([t[i, idx[i, 0]] / t[i, best[i]] if idx[i, 0] >= 0 else np.inf
                           for i in range(len(d))])[ok]
-        return float(hit.mean()), float(ov.mean()), float(np.median(first))
+        return float(hit.mean()), int(hit.sum()), float(ov.mean()), float(np.median(first))
 
-    hs, os_, rs = stats(s_idx)
-    ha, oa, ra = stats(a_idx)
-    return {"kernels": int(ok.sum()), "k": k, "thresh": thresh, "hit_surrogate": hs, "hit_analytic": ha,
+    n_ok = int(ok.sum())
+    hs, ns_, os_, rs = stats(s_idx)
+    ha, na, oa, ra = stats(a_idx)
+    launchable = np.sum(np.isfinite(us), axis=1)[ok]
+    floor = float(np.mean(np.minimum(1.0, k / launchable)))
+    return {"kernels": n_ok, "k": k, "thresh": thresh, "hit_surrogate": hs, "hit_analytic": ha,
+            "hit_random": floor, "hit_surrogate_ci95": wilson(ns_, n_ok), "hit_analytic_ci95": wilson(na, n_ok),
             "overlap_surrogate": os_, "overlap_analytic": oa, "first_pick_slowdown_surrogate": rs,
             "first_pick_slowdown_analytic": ra, "fallback_rate": float(fb[ok].mean())}
 
@@ -170,8 +239,10 @@ def evaluate_pruning(arch, axes, descs, dev):
     d["space_mask"] = np.uint64(gen.mask_bits(PRUNE_T, PRUNE_G, PRUNE_U, PRUNE_C))
     size = int(gen.space_sizes(d[:1])[0])
     n_g = len(PRUNE_G)
-    us, _ = measure(axes, d, np.repeat(np.arange(len(d)), size), np.tile(np.arange(size), len(d)).astype(np.int32))
-    t = np.where(np.isfinite(us), us, np.inf).reshape(len(d), len(PRUNE_T), n_g)  # canonical order: T, then G
+    us, _, cfg = measure(axes, d, np.repeat(np.arange(len(d)), size), np.tile(np.arange(size), len(d)).astype(np.int32),
+                         launched=True)
+    ns = per_unit_ns(us, cfg)
+    t = np.where(np.isfinite(ns), ns, np.inf).reshape(len(d), len(PRUNE_T), n_g)  # canonical order: T, then G
     sug = tune_suggest(arch, axes, descs_to_device(d, dev))
     star = sug["t_star"].cpu().numpy().astype(np.int64) & 0xFFFFFFFF
     rule = sug["t_rule"].cpu().numpy().astype(np.int64) & 0xFFFFFFFF

@@ -104,6 +104,10 @@ def test_host_validation_rejects_bad_arguments(lib):
     assert _call_eval(lib, bad, ax, 5) == native.TUNE_EINVAL
     big = dict(ax, g=[1 << 20])
     assert _call_eval(lib, a, big, 5) == native.TUNE_EINVAL
+    low = dict(a, ipc=[2.0 ** -17] + a["ipc"][1:])  # below 2^-16: costs could overflow
+    assert _call_eval(lib, low, ax, 5) == native.TUNE_EINVAL
+    at = dict(a, ipc=[2.0 ** -16] + a["ipc"][1:])
+    assert _call_eval(lib, at, ax, 5) != native.TUNE_EINVAL or "ipc" not in lib.tune_last_error().decode()
     assert "k = 0" in (lib.tune_last_error().decode() if _call_eval(lib, a, ax, 0) else "")
 
 
@@ -123,3 +127,16 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(native, "LIB_PATH", "/nonexistent/libtune.so")
     with pytest.raises(RuntimeError, match="missing"):
         native.load()
+
+
+def test_fault_injection_arguments(lib):
+    """tune_inject_fault takes a known kind and a count in [0, 10^6]; setting and clearing
+    pending faults involves no GPU."""
+    from paper_1701_08547_gb300 import native
+
+    assert lib.tune_inject_fault(0, 1) == native.TUNE_EINVAL
+    assert lib.tune_inject_fault(4, 1) == native.TUNE_EINVAL
+    assert lib.tune_inject_fault(native.TUNE_FAULT_COMPILE, -1) == native.TUNE_EINVAL
+    for kind in (native.TUNE_FAULT_COMPILE, native.TUNE_FAULT_SLOW_REP, native.TUNE_FAULT_WAIT):
+        assert lib.tune_inject_fault(kind, 3) == 0
+        assert lib.tune_inject_fault(kind, 0) == 0

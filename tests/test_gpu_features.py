@@ -46,9 +46,16 @@ def test_features_match_oracle(dev, oracle):
     assert np.all(g[:, 48:] == 0)
     for i in range(len(kern)):
         T_, G_, U_, C_ = oracle.decode_point(d[kern[i]], ax, pt[i])
-        want = S.bf16(oracle.features(a, d[kern[i]], T_, G_, U_, C_))
-        err = np.abs(g[i, :48] - want)
-        assert np.all(err <= 2.0 ** -7 * np.abs(want) + 1e-30), (i, np.argmax(err), g[i, :48], want)
+        raw = oracle.features(a, d[kern[i]], T_, G_, U_, C_)
+        want = S.bf16(raw)
+        err = np.abs(g[i, :45] - want[:45])
+        assert np.all(err <= 2.0 ** -7 * np.abs(want[:45]) + 1e-30), (i, np.argmax(err), g[i, :48], want)
+        # 45-47 hold what BF16 storage drops of 38-40 (scaled by 256): whether the GPU's FP32
+        # value and the oracle's FP64 value round to the same BF16 may differ, so compare what
+        # they carry together, the cost features to about 2^-15
+        for hi, lo in ((38, 45), (39, 46), (40, 47)):
+            rec = g[i, hi] + g[i, lo] / 256
+            assert abs(rec - raw[hi]) <= 2.0 ** -15 * abs(raw[hi]) + 1e-30, (i, hi, rec, raw[hi])
 
 
 def _oracle_scores(oracle, a, ax, desc, flat, members):

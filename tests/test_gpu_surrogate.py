@@ -255,3 +255,30 @@ def test_training_reduces_loss(dev):
     tr = trace.cpu().numpy().reshape(epochs, steps, members)
     assert np.all(np.isfinite(tr))
     assert tr[-1].mean() < 0.1 * tr[0, 0].mean(), (tr[0, 0], tr[-1].mean())
+
+
+def test_timed_out_wait_is_reported_and_the_next_call_is_clean(dev):
+    """Failure detection without a fault: with TUNE_FAULT_WAIT pending, the next per-layer
+    tcgen05 forward launch leaves its first operand copy unissued, so that copy's wait gives
+    up after a short bound; every CTA records the timeout, waits for the copies it did
+    issue, frees its tensor memory and returns. surrogate_status reports TUNE_ETIMEOUT
+    once, and the next forward (no fault pending) is correct."""
+    import paper_1701_08547_gb300 as T
+    from paper_1701_08547_gb300 import native
+
+    s, flat = make(2, 512)
+    s.set_forward_mode(s.FWD_LAYERED)
+    s.use_tcgen05(True)
+    X = feats(300, 14)
+    Xd = to_dev(X, dev)
+    T.tune_inject_fault(native.TUNE_FAULT_WAIT, 1)
+    s.forward(Xd)
+    with pytest.raises(T.TuneError) as e:
+        s.check()
+    assert e.value.code == native.TUNE_ETIMEOUT
+    s.check()  # the status was cleared by the check
+    pred = s.forward(Xd).cpu().numpy()
+    s.check()
+    for m, p in enumerate(L.unpack(flat, 2)):
+        y, _ = S.forward(p, X, bf=True)
+        assert np.all(np.abs(pred[m] - y) <= 2e-2 * (1 + np.abs(y)))

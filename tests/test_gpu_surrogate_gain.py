@@ -1,11 +1,17 @@
-"""What the learned surrogate gains over the analytic model alone.
+"""What the learned surrogate gains over the analytic model alone, and the sanity case.
 
-Labels are this GPU's measured runtimes of the library's synthetic variants
-(tune_emit_measure); the ensemble is trained by the library's kernels; on
-held-out kernels whose small spaces are timed completely, the ensemble's
-top-5 (with the analytic fallback at a std/mean threshold of 0.1, and
-without fallback) must contain the measured-best point at least as often as
-the analytic model's top-5.
+Measured labels: this GPU's times of the library's synthetic variants
+(tune_emit_measure), per unit of per-thread work (every thread runs the
+descriptor's counts, so time / (G T) is what the static cost ranks). The ensemble
+is trained by the library's kernels; on held-out kernels whose small spaces
+(80 points) are timed completely, hit@5 = the measured-best point is among a
+ranking's 5 picks. The analytic model must beat 5 uniform random picks among the
+launchable points, and the ensemble (with its analytic fallback at std/mean 0.1,
+and without fallback) must hit at least as often as the analytic model.
+
+Sanity case: trained on the analytic model's own costs as labels, the ensemble
+must reproduce the analytic choice: on held-out kernels, a point of least
+analytic cost is among its top 5 for at least 95 % of them.
 """
 
 import numpy as np
@@ -16,25 +22,55 @@ from workloads import archs, gen
 pytestmark = pytest.mark.gpu
 
 
-def test_surrogate_beats_analytic_on_measured_best():
+@pytest.fixture(scope="module")
+def dev():
     import torch
 
     from paper_1701_08547_gb300 import build
-    from paper_1701_08547_gb300 import surrogate_data as SD
 
     build.build()
-    dev = torch.device("cuda:0")
+    return torch.device("cuda:0")
+
+
+def test_surrogate_beats_analytic_on_measured_best(dev):
+    from paper_1701_08547_gb300 import surrogate_data as SD
+
     a, ax = archs.arch("sm_103"), gen.axes()
     data = SD.build_set(a, ax, gen.descriptors(600, 4, "dense"), 64, 4, dev)
     assert data["n"] > 0.6 * data["measured"]
     sur, trace = SD.train(data, members=5, epochs=30, dev=dev)
     assert trace[-1].mean() < 0.1 * trace[0, 0].mean()
-    held_out = gen.descriptors(120, 40, "dense")
-    with_fb = SD.evaluate(sur, a, ax, held_out, dev, k=5, thresh=0.1)
-    no_fb = SD.evaluate(sur, a, ax, held_out, dev, k=5, thresh=1e30)
+    timed = SD.timed_spaces(ax, gen.descriptors(120, 40, "dense"))
+    with_fb = SD.evaluate(sur, a, ax, None, dev, k=5, thresh=0.1, timed=timed)
+    no_fb = SD.evaluate(sur, a, ax, None, dev, k=5, thresh=1e30, timed=timed)
     print(with_fb, no_fb)
     assert with_fb["kernels"] >= 60
+    assert with_fb["hit_analytic"] > with_fb["hit_random"]
     assert with_fb["hit_surrogate"] >= with_fb["hit_analytic"]
     assert no_fb["hit_surrogate"] >= no_fb["hit_analytic"]
-    assert no_fb["hit_surrogate"] > 0.2
     assert no_fb["first_pick_slowdown_surrogate"] <= no_fb["first_pick_slowdown_analytic"]
+
+
+def test_surrogate_trained_on_analytic_labels_reproduces_the_analytic_choice(dev):
+    import torch
+
+    import paper_1701_08547_gb300 as T
+    from paper_1701_08547_gb300 import surrogate_data as SD
+
+    a, ax = archs.arch("sm_103"), gen.axes()
+    data = SD.analytic_set(a, ax, gen.descriptors(2000, 44, "dense"), 64, 44, dev)
+    sur, trace = SD.train(data, members=5, epochs=100, dev=dev)
+    held = SD.eval_spaces(gen.descriptors(200, 45, "dense"))
+    off = gen.point_offsets(held)
+    dd = T.descs_to_device(held, dev)
+    s_idx, _, _ = sur.infer(a, ax, dd, off, 5, thresh=1e30)
+    pc = torch.empty(int(off[-1]), dtype=torch.float32, device=dev)
+    T.tune_eval(a, ax, dd, 1, flags=T.TUNE_EMIT_POINTS, pt_cost=pc, pt_offsets=torch.from_numpy(off).to(dev))
+    cost = pc.cpu().numpy().reshape(len(held), -1)
+    s_idx = s_idx.cpu().numpy()
+    ok = np.isfinite(cost).any(axis=1)
+    # a hit: one of the 5 picks has the least analytic cost (equal costs are equally best)
+    hit = np.array([np.isin(cost[i, s_idx[i][s_idx[i] >= 0]], cost[i].min()).any() for i in range(len(held))])
+    print("sanity hit@5", hit[ok].mean(), "kernels", ok.sum(), "final loss", trace[-1].mean())
+    assert ok.sum() >= 150
+    assert hit[ok].mean() >= 0.95
