@@ -82,9 +82,11 @@ def triple_instructions(descs):
 
 
 def kernel_source_hash():
+    """Hash of the evaluation kernel's sources (tune_eval.cu and the arithmetic it includes)."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1701_08547_gb300", "csrc", "tune_eval.cu"), "rb") as f:
-        h.update(f.read())
+    for name in ("tune_eval.cu", "eval_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1701_08547_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -216,37 +218,44 @@ def measured_peaks():
     return {"sm_max_mhz": 2070.0}, "fallback"
 
 
-def run_ours(args):
+def _uuid(dev):
     import torch
-    import torch.distributed as dist
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    return f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+
+
+def issue_peak(dev):
+    """(Tinstr/s, description): SMs x 4 schedulers x 32 lanes x the measured maximum SM clock."""
+    import torch
+
+    peaks, kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return (sms * ISSUE_LANES_PER_SM_CLK * peaks["sm_max_mhz"] * 1e6 / 1e12,
+            f"{sms} SMs x 128 lanes x {peaks['sm_max_mhz']} MHz ({kind})")
+
+
+def eval_workload(args, name, dev, stream, flush, rank, world, local, n=None, with_e2e=True, with_clocks=False):
+    """One tune_eval workload timed the way the headline is: schedule from the library's
+    autotuner (untimed), one step captured in a CUDA graph, W warm-up replays, K timed
+    replays with an L2 flush before each (outside the events), max over ranks; then the
+    end-to-end call from and to pinned host buffers (transfers inside the timed region).
+    Returns the measurement dict and the device results of the last step."""
+    import torch
 
     import paper_1701_08547_gb300 as T
-    from paper_1701_08547_gb300 import build as B
 
-    rank, world, local = dist_env()
-    B.build()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
-
-    n, space, k, seed = WORKLOADS[args.workload]
-    n = args.kernels or n
+    n0, space, k, seed = WORKLOADS[name]
+    n = n or n0
     a, ax = archs.arch("sm_103"), gen.axes()
     descs = shard(n, seed, space, rank)
     points = int(gen.space_sizes(descs).sum())
-    algo_instr = algorithmic_instructions(descs, ax)
-    triple_instr = triple_instructions(descs)
-
     d_dev = T.descs_to_device(descs, dev)
     ws = T.workspace(0, n, k, dev)
     topi = torch.empty((n, k), dtype=torch.int32, device=dev)
     topc = torch.empty((n, k), dtype=torch.float32, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.Stream(dev)
-    torch.cuda.set_stream(stream)
 
-    # Schedule: chosen by the library's autotuner on this workload (untimed), or forced.
     if args.flags:
         sched, tuned_ms = int(args.flags, 16), None
     elif args.sched == "auto":
@@ -256,8 +265,7 @@ def run_ours(args):
         sched, tuned_ms = {"warp": 0x10, "thread": 0x20}[args.sched], None
 
     def step():
-        T.tune_eval(a, ax, d_dev, k, flags=sched, topk_idx=topi, topk_cost=topc, workspace_buf=ws,
-                    stream=stream)
+        T.tune_eval(a, ax, d_dev, k, flags=sched, topk_idx=topi, topk_cost=topc, workspace_buf=ws, stream=stream)
 
     step()  # first call outside capture (occupancy queries are cached here)
     torch.cuda.synchronize()
@@ -267,22 +275,19 @@ def run_ours(args):
         with torch.cuda.graph(graph, stream=stream):
             step()
     run_step = graph.replay if graph is not None else step
-
     for _ in range(args.warmup):
         flush.zero_()
         run_step()
     torch.cuda.synchronize()
     T.tune_check(ws, stream)
-
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:
+        import torch.distributed as dist
+
         dist.barrier()
     torch.cuda.synchronize()
-    props = torch.cuda.get_device_properties(dev)
-    uuid = getattr(props, "uuid", None)
-    uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else uuid
-    with ClockSampler(uuid, local) as clk:
+    with ClockSampler(_uuid(dev), local) as clk:
         for i in range(args.steps):
             flush.zero_()  # L2 flush between timed steps (outside the event pair)
             starts[i].record(stream)
@@ -292,21 +297,33 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     T.tune_check(ws, stream)
-    step_ms = [s_.elapsed_time(e) for s_, e in zip(starts, ends)]
-    ms = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
+    ms = max_over_ranks(sum(s_.elapsed_time(e) for s_, e in zip(starts, ends)) / args.steps, world, dev)
+    out = {"descs": descs, "n": n, "k": k, "points": points, "ms": ms, "sched": sched, "tuned_ms": tuned_ms,
+           "graph": graph is not None, "clocks": clk.summary(), "topi": topi, "topc": topc}
+    if with_e2e:
+        out["e2e"] = e2e_eval(args, descs, n, k, points, sched, dev, stream, flush, world, topi, topc)
+    return out
 
-    # ---- end to end through the public API with host buffers (pinned), transfers timed.
-    # Direct: one launch reads the descriptors from and writes the top-k into the pinned
-    # (mapped) host buffers over the host link while it evaluates. Staged: tune_eval_host
-    # copies chunks in and out on library streams while it evaluates (reported beside).
+
+def e2e_eval(args, descs, n, k, points, sched, dev, stream, flush, world, topi, topc):
+    """End to end through the public API with host buffers (pinned), transfers timed. Direct:
+    one launch reads the descriptors from and writes the top-k into the pinned (mapped) host
+    buffers over the host link while it evaluates. Staged: tune_eval_host copies chunks in and
+    out on library streams while it evaluates (reported beside). Results are checked equal to
+    the device run's."""
+    import torch
+
+    import paper_1701_08547_gb300 as T
+
+    a, ax = archs.arch("sm_103"), gen.axes()
     host_d = torch.from_numpy(np.ascontiguousarray(descs).view(np.uint8).reshape(-1, 64)).pin_memory()
     host_i = torch.empty((n, k), dtype=torch.int32).pin_memory()
     host_c = torch.empty((n, k), dtype=torch.float32).pin_memory()
     # staged: one chunk per 250,000 kernels at least (a launch needs enough kernels per warp
     # to pay for its set-up), four chunks for larger inputs
-    e2e_chunk = args.e2e_chunk or max(1, min(n, max(250_000, (n + 3) // 4)))
+    chunk = args.e2e_chunk or max(1, min(n, max(250_000, (n + 3) // 4)))
 
-    def e2e_time(extra_flags):
+    def timed(extra_flags):
         e_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         e_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         scratch = None
@@ -314,151 +331,440 @@ def run_ours(args):
             flush.zero_()
             if i >= args.warmup:
                 e_start[i - args.warmup].record(stream)
-            scratch = T.tune_eval_host(a, ax, host_d, k, e2e_chunk, host_i, host_c, scratch=scratch,
+            scratch = T.tune_eval_host(a, ax, host_d, k, chunk, host_i, host_c, scratch=scratch,
                                        flags=sched | extra_flags, stream=stream)
             if i >= args.warmup:
                 e_end[i - args.warmup].record(stream)
         torch.cuda.synchronize()
         T.tune_check(scratch, stream)
-        # the host results are the device run's, bit for bit
         if not (torch.equal(host_i, topi.cpu()) and torch.equal(host_c, topc.cpu())):
             raise RuntimeError("tune_eval_host results differ from tune_eval")
         return max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(e_start, e_end)) / args.steps, world, dev)
 
-    e2e_staged_ms = e2e_time(0)
-    e2e_call = ("tune_eval_host with TUNE_HOST_DIRECT (one launch reads and writes the pinned host buffers "
-                "over NVLink-C2C while it evaluates)")
+    staged_ms = timed(0)
+    call = ("tune_eval_host with TUNE_HOST_DIRECT (one launch reads and writes the pinned host buffers "
+            "over NVLink-C2C while it evaluates)")
     try:
-        e2e_ms = e2e_time(T.native.TUNE_HOST_DIRECT)
+        ms = timed(T.native.TUNE_HOST_DIRECT)
     except T.native.TuneError as err:  # pinned memory not mapped on this system: staged copies only
-        e2e_ms, e2e_call = e2e_staged_ms, f"tune_eval_host, staged ({err})"
-    if world > 1:
-        dist.destroy_process_group()
-    if rank != 0:
-        return None
+        ms, call = staged_ms, f"tune_eval_host, staged ({err})"
+    return {"value": world * points / (ms * 1e-3), "unit": "points/s", "h2d_bytes_per_step": n * 64,
+            "d2h_bytes_per_step": n * k * 8, "ms_per_step": ms, "call": call, "staged_ms_per_step": staged_ms,
+            "staged_call": f"tune_eval_host, {chunk} kernels per chunk copied in and out on library streams"}
 
-    peaks, peak_kind = measured_peaks()
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sms * ISSUE_LANES_PER_SM_CLK * peaks["sm_max_mhz"] * 1e6 / 1e12  # Tinstr/s
-    achieved = algo_instr / (ms * 1e-3) / 1e12
+
+def eval_roofline(r, dev, workload):
+    """Issue roofline of one tune_eval measurement. Algorithmic figure: the scope table's 12
+    thread-instructions per point of a per-point evaluation after the per-kernel hoists. The
+    kernel ranks exactly without pricing most points (a (T,U,C) triple's cheapest point bounds
+    all of its grid sizes; only candidate triples are walked), so it can exceed that figure's
+    issue bound; the executed instructions per point (ncu) and the issue-slot use are given
+    beside it."""
+    peak, peak_source = issue_peak(dev)
+    ms, points = r["ms"], r["points"]
     achieved_12 = PER_POINT_EVAL_INSTR * points / (ms * 1e-3) / 1e12
-    achieved_triple = triple_instr / (ms * 1e-3) / 1e12
+    prof = recorded_profile(workload)
+    out = {"bound": "alu", "achieved": achieved_12, "peak": peak, "unit": "Tinstr/s", "frac": achieved_12 / peak,
+           "traffic": prof.get("bytes_per_launch"), "peak_source": peak_source,
+           "instr_per_point": PER_POINT_EVAL_INSTR,
+           "instr_definition": ("12 thread-instructions per point of a per-point evaluation (scope table); the "
+                                "kernel is an exact top-k by (T,U,C)-triple bounds that prices only candidate "
+                                "triples' points, so frac > 1 means it beats per-point evaluation"),
+           "executed_instr_per_point_ncu": prof.get("thread_instr_per_point"),
+           "issue_active_ncu": prof.get("issue_active"),
+           "frac_2_per_point_5_per_triple": algorithmic_instructions(r["descs"], None) / (ms * 1e-3) / 1e12 / peak}
+    return out
+
+
+def eval_line(args, name, r, dev, world, cpu=True):
+    """The JSON object of one tune_eval workload (headline or sub-object)."""
+    n, k, points = r["n"], r["k"], r["points"]
     line = {
         "metric": METRIC,
-        "value": world * points / (ms * 1e-3),
+        "value": world * points / (r["ms"] * 1e-3),
         "unit": "points/s",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": ms,
+        "ms_per_step": r["ms"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "int32+f32",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {n} kernels x {points // n} points, top-{k}, sm_103 row",
+        "config": {"workload": f"{name}: {n} kernels x {points / n:.0f} points (mean), top-{k}, sm_103 row",
                    "kernels_per_gpu": n, "points_per_gpu": points, "k": k,
                    "l2": "flushed between timed steps (256 MB write outside the timed events)",
                    "parallelism": f"replicas x{world} (kernel ranges)",
-                   "schedule_flags": hex(sched),
+                   "schedule_flags": hex(r["sched"]),
                    "schedule": "forced" if args.flags else ("autotuned" if args.sched == "auto" else args.sched),
-                   "cuda_graph": graph is not None},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
-                     "peak_source": f"{sms} SMs x 128 lanes x {peaks['sm_max_mhz']} MHz ({peak_kind})",
-                     "instr_per_point": algo_instr / points,
-                     "instr_definition": "2 per point (cost multiply, compare) + 5 per (T,U,C) triple",
-                     "frac_12_per_point": achieved_12 / peak,
-                     "issue_active_ncu": recorded_profile(args.workload).get("issue_active"),
-                     "frac_8_per_triple": achieved_triple / peak},
-        "e2e": {"value": world * points / (e2e_ms * 1e-3), "unit": "points/s",
-                "h2d_bytes_per_step": n * 64, "d2h_bytes_per_step": n * k * 8,
-                "ms_per_step": e2e_ms,
-                "call": e2e_call,
-                "staged_ms_per_step": e2e_staged_ms,
-                "staged_call": f"tune_eval_host, {e2e_chunk} kernels per chunk copied in and out on library streams"},
-        "clocks": clk.summary(),
+                   "cuda_graph": r["graph"]},
+        "roofline": eval_roofline(r, dev, name),
+        "clocks": r["clocks"],
         "gpu_launches": args.steps,
     }
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample)
-    if not args.no_surrogate:
-        line["surrogate"] = surrogate_section(args, dev, a, ax, peaks)
+    if "e2e" in r:
+        line["e2e"] = r["e2e"]
+    if cpu and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(name, CPU_SAMPLE.get(name, args.cpu_sample))
     return line
 
 
-# FLOPs per sample and member of the surrogate MLP (128 -> 256 x 4 -> 1): forward
-# 2 (128*256 + 3*256*256 + 256); training = forward + backward (2x forward).
-MLP_FWD_FLOP = 2 * (128 * 256 + 3 * 256 * 256 + 256)
+def emit_points(args, dev, stream, flush, world):
+    """Every point priced and written (TUNE_EMIT_POINTS): B*, W* (int32) and the FP32 cost of
+    each of the dense workload's points, 12 bytes per point, plus the top-k. HBM-bound:
+    algorithmic bytes = 12 per point written + the 64-byte descriptor and the 8-byte offset
+    read + 8 k bytes of top-k written per kernel."""
+    import torch
+
+    import paper_1701_08547_gb300 as T
+
+    n0, space, k, seed = WORKLOADS["dense"]
+    n = args.emit_kernels or n0
+    a, ax = archs.arch("sm_103"), gen.axes()
+    descs = gen.descriptors(n, seed, space)
+    off = gen.point_offsets(descs)
+    points = int(off[-1])
+    d_dev = T.descs_to_device(descs, dev)
+    po = torch.from_numpy(off).to(dev)
+    pb = torch.empty(points, dtype=torch.int32, device=dev)
+    pw = torch.empty(points, dtype=torch.int32, device=dev)
+    pc = torch.empty(points, dtype=torch.float32, device=dev)
+    ws = T.workspace(0, n, k, dev)
+    topi = torch.empty((n, k), dtype=torch.int32, device=dev)
+    topc = torch.empty((n, k), dtype=torch.float32, device=dev)
+
+    def step():
+        T.tune_eval(a, ax, d_dev, k, flags=T.TUNE_EMIT_POINTS, topk_idx=topi, topk_cost=topc, pt_blocks=pb,
+                    pt_warps=pw, pt_cost=pc, pt_offsets=po, workspace_buf=ws, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    T.tune_check(ws, stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev[2 * i].record(stream)
+        step()
+        ev[2 * i + 1].record(stream)
+    torch.cuda.synchronize()
+    T.tune_check(ws, stream)
+    ms = max_over_ranks(sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)) / args.steps,
+                        world, dev)
+    # the emitted points agree with the oracle on sampled kernels (bit for bit)
+    from oracle import oracle as O
+
+    pick = np.random.default_rng(7).choice(n, 16, replace=False)
+    o = O.evaluate(a, ax, descs[pick], k, emit=True, offsets=gen.point_offsets(descs[pick]))
+    for j, i in enumerate(pick):
+        got = pc[int(off[i]):int(off[i + 1])].cpu().numpy()
+        want = o["cost32"][j * 16384:(j + 1) * 16384]
+        if not np.array_equal(got.view(np.uint32), want.view(np.uint32)):
+            raise RuntimeError("emitted per-point costs differ from the oracle")
+    peaks, kind = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    nbytes = 12 * points + 72 * n + 8 + 8 * k * n
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    prof = recorded_profile("emit")
+    line = {"metric": "tuning points priced and written/sec (B*, W*, cost of every point)",
+            "value": world * points / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms, "steps": args.steps,
+            "warmup": args.warmup,
+            "config": {"workload": f"emit: dense {n} kernels x 16384 points, every point's B*, W* and FP32 cost "
+                                   f"written ({12 * points / 1e9:.1f} GB), top-{k}",
+                       "l2": "outputs far larger than L2; 256 MB flush between timed steps"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "traffic": prof.get("bytes_per_launch_scaled"), "algorithmic_bytes": nbytes,
+                         "peak_source": kind},
+            "gpu_launches": args.steps, "check": "16 sampled kernels' per-point costs equal the oracle's bit for bit"}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline("dense", 4000, emit=True)
+    return line
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1701_08547_gb300 import build as B
+
+    rank, world, local = dist_env()
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+
+    head = eval_workload(args, args.workload, dev, stream, flush, rank, world, local, n=args.kernels or None)
+    subs = {}
+    if not args.headline_only and args.workload == "dense":
+        for name in ("dense128", "uneven"):
+            subs[name] = eval_workload(args, name, dev, stream, flush, rank, world, local)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    line = eval_line(args, args.workload, head, dev, world)
+    if not args.headline_only and args.workload == "dense":
+        line["configs"] = {"C1_dense128": eval_line(args, "dense128", subs["dense128"], dev, world),
+                           "C3_uneven": eval_line(args, "uneven", subs["uneven"], dev, world)}
+        line["configs"]["C2_emit_every_point"] = emit_points(args, dev, stream, flush, world)
+    if not args.no_surrogate:
+        peaks, _ = measured_peaks()
+        line["surrogate"] = surrogate_section(args, dev, archs.arch("sm_103"), gen.axes(), peaks, stream)
+    if not args.headline_only and args.workload == "dense":
+        line["other_kernels"] = other_workloads(args)
+    return line
+
+
+# Algorithmic FLOPs per sample and member of the surrogate MLP (48 features -> 256 x 4 -> 1):
+# forward 2 (48*256 + 3*256*256 + 256) = 418,304 (the zero padding of the inputs is not
+# counted); training = forward + backward (2x forward).
+MLP_FWD_FLOP = 2 * (48 * 256 + 3 * 256 * 256 + 256)
 MLP_TRAIN_FLOP = 3 * MLP_FWD_FLOP
 
 
-def surrogate_section(args, dev, a, ax, peaks):
-    """Learned surrogate at bounded size: measured labels, training and inference
-    throughput against the BF16 tensor peak, top-5 agreement with the measured best
-    (held-out, fully timed spaces) and with the analytic model (dense points)."""
+def surrogate_section(args, dev, a, ax, peaks, stream):
+    """The learned path at the scope table's configurations 4 and 5: labels measured on this
+    GPU (s1), training throughput (C4), inference over every point of the dense workload in
+    BF16 and FP8 with the analytic fallback (C5), and the top-5 agreement with the measured
+    best (held-out, fully timed spaces) and with the analytic model."""
     import torch
 
     import paper_1701_08547_gb300 as T
     from paper_1701_08547_gb300 import surrogate_data as SD
+    from workloads import mlp as L
 
     members = 5
     t0 = time.perf_counter()
     data = SD.build_set(a, ax, gen.descriptors(args.sur_descs, 4, "dense"), 64, 4, dev)
     gen_s = time.perf_counter() - t0
-    epochs = 20
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sur, trace = SD.train(data, members=members, epochs=epochs, dev=dev)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    samples = data["n"] * epochs
-    train_tflops = samples * members * MLP_TRAIN_FLOP / train_s / 1e12
-    # inference over every point of dense kernels (features, ensemble, ranking, fallback)
+    out = {"members": members,
+           "labels": {"samples_measured": data["measured"], "samples_kept": data["n"], "seconds": gen_s,
+                      "kind": "this GPU's median-of-3 times of emitted variants, per unit of per-thread work"}}
+    out["C4_train"], sur = train_section(args, dev, data, members, peaks, stream)
+
+    # ---- C5: every point of the dense workload scored by the ensemble, BF16 and FP8
     nk = args.sur_infer_kernels
     d = gen.descriptors(nk, 2, "dense")
     off = gen.point_offsets(d)
-    dd = T.descs_to_device(d, dev)
+    pts = int(off[-1])
     inf_sur = SD.Surrogate(members=members, batch=65536)
     inf_sur.set_params(sur.get(sur.GET_PARAMS))
-    inf_sur.infer(a, ax, dd, off, 5, 0.1)  # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    s_idx, _, fb = inf_sur.infer(a, ax, dd, off, 5, 0.1)
-    torch.cuda.synchronize()
-    infer_s = time.perf_counter() - t0
-    pts = int(off[-1])
-    infer_tflops = pts * members * MLP_FWD_FLOP / infer_s / 1e12
-    a_idx, _ = T.tune_eval(a, ax, dd, 5)
-    si, ai = s_idx.cpu().numpy(), a_idx.cpu().numpy()
-    agree_overlap = float(np.mean([len(set(si[i]) & set(ai[i])) / 5 for i in range(nk)]))
-    agree_hit = float(np.mean([ai[i, 0] in si[i] for i in range(nk)]))
-    held_out = gen.descriptors(args.sur_eval, 40, "dense")
-    ev = SD.evaluate(sur, a, ax, held_out, dev, k=5, thresh=0.1)
-    ev_nofb = SD.evaluate(sur, a, ax, held_out, dev, k=5, thresh=1e30)
-    pruning = SD.evaluate_pruning(a, ax, held_out, dev)
+    host_d = torch.from_numpy(np.ascontiguousarray(d).view(np.uint8).reshape(-1, 64)).pin_memory()
+    dd = torch.empty_like(host_d, device=dev)
+    dd.copy_(host_d)
+    a_idx, _ = T.tune_eval(a, ax, dd, 5, stream=stream)
+    ai = a_idx.cpu().numpy()
+    warm = gen.descriptors(max(1, nk // 16), 2, "dense")
+    warm_d = T.descs_to_device(warm, dev)
+    timed = SD.timed_spaces(ax, gen.descriptors(args.sur_eval, 40, "dense"))
+    c5 = {}
+    sustained = peaks.get("bf16_tflops_sustained", 1700.0)
+    for name, mode in (("bf16", SD.Surrogate.FWD_FUSED_BF16), ("fp8", SD.Surrogate.FWD_FUSED_FP8)):
+        inf_sur.set_forward_mode(mode)
+        for _ in range(args.warmup):
+            inf_sur.infer(a, ax, warm_d, gen.point_offsets(warm), 5, 0.1, stream=stream)
+        torch.cuda.synchronize()
+        hi = torch.empty((nk, 5), dtype=torch.int32).pin_memory()
+        hf = torch.empty(nk, dtype=torch.uint8).pin_memory()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with ClockSampler(_uuid(dev), dev.index or 0) as clk:
+            ev[0].record(stream)
+            with torch.cuda.stream(stream):
+                dd.copy_(host_d, non_blocking=True)
+            ev[1].record(stream)
+            s_idx, _, fb = inf_sur.infer(a, ax, dd, off, 5, 0.1, stream=stream)
+            ev[2].record(stream)
+            with torch.cuda.stream(stream):
+                hi.copy_(s_idx, non_blocking=True)
+                hf.copy_(fb, non_blocking=True)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+        ms = ev[1].elapsed_time(ev[2])
+        e2e_ms = ev[0].elapsed_time(ev[3])
+        inf_sur.check()
+        si, fbn = hi.numpy(), hf.numpy()
+        tf = pts * members * MLP_FWD_FLOP / (ms * 1e-3) / 1e12
+        peak = sustained * (2 if name == "fp8" else 1)
+        ev_fb = SD.evaluate(inf_sur, a, ax, None, dev, k=5, thresh=0.1, timed=timed)
+        ev_nofb = SD.evaluate(inf_sur, a, ax, None, dev, k=5, thresh=1e30, timed=timed)
+        c5[name] = {
+            "metric": "tuning points scored by the surrogate ensemble/sec + top-k (fallback at std/mean 0.1)",
+            "value": pts / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms, "steps": 1,
+            "warmup": args.warmup, "dtype": "bf16" if name == "bf16" else "e4m3 layers 2-4, bf16 layer 1",
+            "config": {"workload": f"C5: dense {nk} kernels x 16384 points ({pts} points), 5 members, top-5, "
+                                   "fallback per kernel where a pick's std/mean > 0.1",
+                       "warmup": f"{args.warmup} passes over {len(warm)} kernels"},
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                         "traffic": None,
+                         "flop_definition": "418,304 FLOP per point and member (48 -> 256 x 4 -> 1 forward); "
+                                            "the whole call (features, ensemble, ranking, fallback) is timed",
+                         "peak_source": "measured sustained BF16 GEMM" + (" x 2 (nominal FP8/BF16)" if name == "fp8"
+                                                                           else "")},
+            "e2e": {"value": pts / (e2e_ms * 1e-3), "unit": "points/s", "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": nk * 64, "d2h_bytes_per_step": nk * (5 * 4 + 1),
+                    "call": "descriptors copied from pinned host memory, surrogate_infer, top-5 and fallback "
+                            "flags copied back, all inside the timed region"},
+            "fallback_rate": float(fbn.mean()),
+            "top5_vs_analytic": {"overlap": float(np.mean([len(set(si[i]) & set(ai[i])) / 5 for i in range(nk)])),
+                                 "analytic_best_in_top5": float(np.mean([ai[i, 0] in si[i] for i in range(nk)]))},
+            "top5_vs_measured_best": {"thresh_0.1": ev_fb, "no_fallback": ev_nofb},
+            "clocks": clk.summary(), "gpu_launches": None,
+        }
+        if not args.no_cpu_baseline and name == "bf16":
+            c5[name]["cpu_baseline"] = surrogate_cpu_baseline(a, ax, inf_sur, members)
+    out["C5_infer"] = c5
+    out["static_pruning_vs_measured_best"] = SD.evaluate_pruning(a, ax, gen.descriptors(args.sur_eval, 40, "dense"),
+                                                                 dev)
     from paper_1701_08547_gb300 import realkernels as RK
 
+    inf_sur.set_forward_mode(SD.Surrogate.FWD_FUSED_BF16)
     t0 = time.perf_counter()
     real = RK.evaluate(a, ax, dev, n=args.real_n, surrogate=inf_sur)
     real["seconds"] = time.perf_counter() - t0
     real["matrix_order"] = args.real_n
-    peak = peaks.get("bf16_tflops", 1900.0)
-    return {
-        "members": members,
-        "labels": {"samples_measured": data["measured"], "samples_kept": data["n"], "seconds": gen_s,
-                   "kind": "this GPU's median-of-3 times of emitted variants"},
-        "train": {"samples_per_s": samples / train_s, "epochs": epochs, "seconds": train_s,
-                  "tflops": train_tflops, "frac_bf16_peak": train_tflops / peak,
-                  "final_mse_ln_us": float(trace[-1].mean())},
-        "infer": {"points_per_s": pts / infer_s, "points": pts, "kernels": nk, "seconds": infer_s,
-                  "tflops": infer_tflops, "frac_bf16_peak": infer_tflops / peak,
-                  "fallback_rate": float(fb.float().mean().item())},
-        "top5_vs_analytic": {"overlap": agree_overlap, "analytic_best_in_surrogate_top5": agree_hit},
-        "top5_vs_measured_best": {"thresh_0.1": ev, "no_fallback": ev_nofb},
-        "static_pruning_vs_measured_best": pruning,
-        "real_kernels": real,
-    }
+    out["real_kernels"] = real
+    return out
+
+
+def train_section(args, dev, data, members, peaks, stream):
+    """C4: the library's training (surrogate_train: BF16 tcgen05 forward and backward, Adam) on
+    the measured labels, timed with CUDA events; and end to end with the features, labels and
+    epoch orders copied from pinned host memory and the loss trace copied back."""
+    import torch
+
+    from paper_1701_08547_gb300 import surrogate_data as SD
+    from workloads import mlp as L
+
+    epochs = args.sur_epochs
+    n = data["n"]
+    batch = 8192
+    rng = np.random.default_rng(5)
+    order_h = torch.from_numpy(np.concatenate([rng.permutation(n) for _ in range(epochs)]).astype(np.int32))
+    steps = (n + batch - 1) // batch
+    feats_h = data["feats"].cpu().pin_memory()
+    labels_h = data["labels"].cpu().pin_memory()
+    order_h = order_h.pin_memory()
+
+    def run(e2e):
+        sur = SD.Surrogate(members=members, batch=batch)
+        sur.set_params(L.init_params(members, [5 + m for m in range(members)]))
+        trace = torch.zeros(epochs * steps * members, dtype=torch.float32, device=dev)
+        trace_h = torch.empty(trace.numel(), dtype=torch.float32).pin_memory()
+        f, lab, o = data["feats"], data["labels"], order_h.to(dev)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        with torch.cuda.stream(stream):
+            if e2e:
+                f = feats_h.to(dev, non_blocking=True)
+                lab = labels_h.to(dev, non_blocking=True)
+                o = order_h.to(dev, non_blocking=True)
+            sur.train(f, lab, o, epochs, trace, stream=stream)
+            if e2e:
+                trace_h.copy_(trace, non_blocking=True)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        sur.check()
+        return sur, e[0].elapsed_time(e[1]), trace.cpu().numpy().reshape(epochs, steps, members)
+
+    run(False)  # warm-up (module load, first launches)
+    sur, ms, trace = run(False)
+    _, e2e_ms, _ = run(True)
+    samples = n * epochs
+    step_ms = ms / (epochs * steps)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    gbs = train_step_bytes(batch, members) / (step_ms * 1e-3) / 1e9
+    tf = samples * members * MLP_TRAIN_FLOP / (ms * 1e-3) / 1e12
+    line = {"metric": "surrogate training samples/sec (5 members)", "value": samples / (ms * 1e-3),
+            "unit": "samples/s", "ms_per_step": step_ms, "steps": epochs * steps, "warmup": 1,
+            "dtype": "bf16 (FP32 accumulation and master weights)",
+            "config": {"workload": f"C4: {n} measured labels x {epochs} epochs in {batch}-row steps, {members} "
+                                   "members, 48 -> 256 x 4 -> 1, Adam",
+                       "labels": "64 K measured here instead of 20 M (timing 20 M variants takes hours); the "
+                                 "step time does not depend on the label count"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "traffic": None, "algorithmic_bytes_per_step": train_step_bytes(batch, members),
+                         "tensor_tflops": tf, "tensor_frac_sustained": tf / peaks.get("bf16_tflops_sustained", 1700.0),
+                         "flop_definition": "3 x 418,304 FLOP per sample and member"},
+            "e2e": {"value": samples / (e2e_ms * 1e-3), "unit": "samples/s", "ms": e2e_ms,
+                    "h2d_bytes_per_step": (feats_h.numel() * 2 + labels_h.numel() * 4 + order_h.numel() * 4) /
+                    (epochs * steps),
+                    "d2h_bytes_per_step": 4 * members,
+                    "call": "features, labels and epoch orders copied from pinned host memory, surrogate_train, "
+                            "loss trace copied back, all inside the timed region"},
+            "final_mse": float(trace[-1].mean()), "gpu_launches": None}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = train_cpu_baseline(members)
+    return line, sur
+
+
+def train_cpu_baseline(members, rows=2048):
+    """The FP64 oracle's forward + backward (+ Adam) on one batch, per sample and member."""
+    from oracle import surrogate_oracle as S
+    from workloads import mlp as L
+
+    rng = np.random.default_rng(0)
+    X = np.zeros((rows, L.IN))
+    X[:, :L.FEATURES] = rng.standard_normal((rows, L.FEATURES))
+    X = S.bf16(X)
+    t = rng.standard_normal(rows)
+    flat = L.init_params(members)
+    t0 = time.perf_counter()
+    for p in L.unpack(flat, members):
+        S.loss_and_grads(p, X, t, bf=True)
+    dt = time.perf_counter() - t0
+    return {"value": rows / dt, "unit": "samples/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"one {rows}-row batch, {members} members, FP64 forward + backward (numpy), {dt:.2f} s"}
+
+
+def surrogate_cpu_baseline(a, ax, sur, members, kernels=8, per_kernel=1000):
+    """The oracle's inference (features in FP64, FP64 forward of every member on the BF16
+    weights, mean and spread) on `per_kernel` points of each of `kernels` dense kernels."""
+    from oracle import oracle as O
+    from oracle import surrogate_oracle as S
+    from workloads import mlp as L
+
+    d = gen.descriptors(kernels, 2, "dense")
+    flat = sur.get(sur.GET_PARAMS)
+    rng = np.random.default_rng(3)
+    t0 = time.perf_counter()
+    for i in range(kernels):
+        X = np.zeros((per_kernel, L.IN))
+        for r, p in enumerate(rng.integers(0, 16384, per_kernel)):
+            X[r, :48] = O.features(a, d[i], *O.decode_point(d[i], ax, p))
+        X = S.bf16(X)
+        preds = np.stack([S.forward(prm, X, bf=True)[0] for prm in L.unpack(flat, members)])
+        r = np.exp(preds)
+        _ = r.std(0) / r.mean(0)
+    dt = time.perf_counter() - t0
+    n = kernels * per_kernel
+    return {"value": n / dt, "unit": "points/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"{per_kernel} random points of each of {kernels} dense kernels ({n} points), {dt:.2f} s"}
+
+
+def other_workloads(args):
+    """The remaining kernels of the path, each timed alone (their own JSON objects): the
+    segmented top-k (a8), the fused ensemble forward (s3) in BF16 and FP8, one training step
+    (s4), and the search drivers."""
+    import copy
+
+    out = {}
+    for name, fn in (("topk", run_topk), ("surfwd", run_surfwd), ("surtrain", run_surtrain),
+                     ("search", run_search)):
+        a2 = copy.copy(args)
+        a2.kernels = 0
+        a2.workload = name
+        r = fn(a2)
+        for key in ("n_gpus", "higher_is_better", "scaling", "vs_baseline", "data"):
+            r.pop(key, None)
+        out[name] = r
+    return out
 
 
 def run_surfwd(args):
@@ -479,7 +785,9 @@ def run_surfwd(args):
     n = args.kernels or (1 << 20)
     g = torch.Generator(device=dev)
     g.manual_seed(12)
-    X = torch.randn(n, 128, generator=g, device=dev).to(torch.bfloat16)
+    X = torch.zeros(n, L.IN, device=dev)  # 48 standard-normal features, zero padding as tune_features writes
+    X[:, :L.FEATURES] = torch.randn(n, L.FEATURES, generator=g, device=dev)
+    X = X.to(torch.bfloat16)
     pred = torch.empty((5, n), device=dev)
     peaks, kind = measured_peaks()
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
@@ -712,7 +1020,16 @@ def run_topk(args):
             "clocks": clk.summary(), "gpu_launches": args.steps}
 
 
-def cpu_baseline(workload, sample):
+# Oracle samples per workload for the CPU baseline (about 1-2 s on 16 Grace cores each).
+CPU_SAMPLE = {"dense": 16000, "dense128": 64, "uneven": 10000}
+CPU_SAMPLE_1CORE = 1000  # kernels of the single-thread run, extrapolated per point
+
+
+def cpu_baseline(workload, sample, emit=False):
+    """The CPU oracle (plain C, FP64 cost + FP32 mirror, full sort per kernel, OpenMP over
+    kernels) timed on the host cores on the first `sample` kernels of the workload, and on one
+    core on the first 1,000 (points/s of each; the workload's points per kernel are the same
+    distribution, so the rates extrapolate to the whole workload)."""
     from oracle import oracle as O
 
     n, space, k, seed = WORKLOADS[workload]
@@ -720,14 +1037,27 @@ def cpu_baseline(workload, sample):
     descs = gen.descriptors(sample, seed, space)
     a, ax = archs.arch("sm_103"), gen.axes()
     threads = O.threads_available()
-    O.evaluate(a, ax, descs[:8], k, nthreads=threads)  # load + warm
-    t0 = time.perf_counter()
-    O.evaluate(a, ax, descs, k, nthreads=threads)
-    dt = time.perf_counter() - t0
+
+    def run(d, nt):
+        kw = dict(emit=True, offsets=gen.point_offsets(d)) if emit else {}
+        t0 = time.perf_counter()
+        O.evaluate(a, ax, d, k, nthreads=nt, **kw)
+        return time.perf_counter() - t0
+
+    run(descs[:8], threads)  # load + warm
+    dt = run(descs, threads)
     pts = int(gen.space_sizes(descs).sum())
+    one = descs[:min(CPU_SAMPLE_1CORE, sample)]
+    dt1 = run(one, 1)
+    pts1 = int(gen.space_sizes(one).sum())
+    what = "every point's B*, W*, FP32 and FP64 cost written, " if emit else ""
     return {"value": pts / dt, "unit": "points/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {sample} kernels of the {workload} workload ({pts} points), "
-                      f"{dt:.2f} s wall on {threads} threads"}
+            "sample": f"first {sample} kernels of the {workload} workload ({pts} points), {what}"
+                      f"{dt:.2f} s wall on {threads} threads",
+            "one_core": {"value": pts1 / dt1, "unit": "points/s", "cores": 1,
+                         "sample": f"first {len(one)} kernels ({pts1} points), {dt1:.2f} s on 1 thread; "
+                                   f"extrapolated to the whole workload: "
+                                   f"{n * (pts1 / len(one)) / (pts1 / dt1):.0f} s"}}
 
 
 def run_reference(args):
@@ -787,8 +1117,12 @@ def main():
     p.add_argument("--no-graph", action="store_true", help="plain launches instead of graph replays")
     p.add_argument("--flags", default="", help="tune_eval schedule flags in hex (skips the autotuner)")
     p.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate section")
+    p.add_argument("--headline-only", action="store_true",
+                   help="only the selected workload (no sub-configurations or other kernels)")
+    p.add_argument("--emit-kernels", type=int, default=0, help="kernels of the every-point run (0: 100,000)")
+    p.add_argument("--sur-epochs", type=int, default=20, help="training epochs over the measured labels")
     p.add_argument("--sur-descs", type=int, default=1000, help="descriptors for surrogate labels (x64 points)")
-    p.add_argument("--sur-infer-kernels", type=int, default=500, help="dense kernels scored by the ensemble")
+    p.add_argument("--sur-infer-kernels", type=int, default=100_000, help="dense kernels scored by the ensemble")
     p.add_argument("--sur-eval", type=int, default=150, help="held-out kernels with fully timed spaces")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--budget", type=int, default=128, help="search workload: evaluations per kernel")
