@@ -353,6 +353,21 @@ int tune_emit_measure(const tune_axes* axes, const tune_kernel_desc* descs, int6
                       int32_t* launched, tune_stream_t stream);
 
 /*
+ * tune_emit_count — the executed instruction mix of tune_emit_measure's variants (the
+ * dynamic side of Section IV's comparison of static and dynamic instruction mixes, Table
+ * "Error rates when estimating dynamic instruction mixes from static mixes"). Sample i's
+ * variant is built with per-class tallies (one per executed iteration of a class's loop:
+ * FP32 FMA, FP64 FMA, integer step, global load, shared load-store, branch, SFU sine) and
+ * launched once as tune_emit_measure launches it; counts[7 i + c] = the operations of class c
+ * executed by all its threads (UINT64_MAX where the launch is not possible). Arguments as
+ * for tune_emit_measure; counts is host memory; synchronous; allocates its buffers (two 4 MB,
+ * one 56 B) for the duration of the call.
+ */
+int tune_emit_count(const tune_axes* axes, const tune_kernel_desc* descs, int64_t n_kernels,
+                    const int32_t* sample_kernel, const int32_t* sample_point, int64_t n_samples,
+                    int32_t items, float count_scale, uint64_t* counts, tune_stream_t stream);
+
+/*
  * tune_eval_archs — tune_eval of the same descriptors against n_arch
  * architecture rows (1..8) in one launch (a sweep over GPU generations:
  * Eqs. 1-6 with each row's limits and throughputs). archs: host array

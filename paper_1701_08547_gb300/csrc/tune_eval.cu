@@ -72,7 +72,7 @@ struct CtaTables {
 };
 
 struct WarpTables {
-    float iparmin[kMaxB];    // min over the kernel's grid sizes of ipar(b, G)
+    float iparmin[kMaxB + 1];  // by B*: min over the kernel's grid sizes of ipar(B*, G); [0] = NaN
     unsigned char gwr[32][8];  // min(G_W, G_R) by (t rank, u rank)
     float cnm[8], cm[8];     // by u rank
     int regs[8];             // R by u rank
@@ -403,9 +403,10 @@ __global__ void __maxnreg__(64)
             // ---- waves/slots factor rows, compacted to this kernel's grid sizes, and
             // their minima.
             const bool g_dense = gm == g_ok;
+            if (lane == 0) w.iparmin[0] = __int_as_float(0x7fc00000);  // B* = 0: no valid configuration
             if (lane < kMaxB) {
                 if (g_dense) {
-                    w.iparmin[lane] = ct.iparmin[lane];
+                    w.iparmin[lane + 1] = ct.iparmin[lane];
                 } else {
                     float mn = kInf;
 #pragma unroll
@@ -414,7 +415,7 @@ __global__ void __maxnreg__(64)
                         if (EMIT) w.iparc[lane][j] = f;
                         mn = fminf(mn, f);
                     }
-                    w.iparmin[lane] = mn;
+                    w.iparmin[lane + 1] = mn;
                 }
             }
             __syncwarp();
@@ -488,11 +489,16 @@ __global__ void __maxnreg__(64)
                     int gs[NC];
 #pragma unroll
                     for (int c = 0; c < NC; ++c) gs[c] = w.gs[c];
-                    for (int j = 0; j < n_prow; ++j) {
+                    // pair pr = lane + 32 j = t_r nU + u_r, advanced by 32 pairs per step
+                    const int dq = small_div(32, rcp_u), dr = 32 - dq * nU;
+                    int t_r = small_div(lane, rcp_u), u_r = lane - t_r * nU;
+                    for (int j = 0; j < n_prow; ++j, t_r += dq, u_r += dr) {
                         const int pr = lane + (j << 5);
                         if (pr >= nP) break;
-                        const int t_r = small_div(pr, rcp_u);
-                        const int u_r = pr - t_r * nU;
+                        if (u_r >= nU) {
+                            u_r -= nU;
+                            ++t_r;
+                        }
                         const int4 ti = w.tinfo[t_r];
                         const int wb = ti.x;
                         const float ln = __int_as_float(ti.y);
@@ -501,17 +507,14 @@ __global__ void __maxnreg__(64)
                         float key[NC];
 #pragma unroll
                         for (int c = 0; c < NC; ++c) {
-                            // branch-free: a triple without a valid configuration (B* = 0) is
-                            // priced with B* = 1, then keyed NaN (never a candidate) and ranked
-                            // +inf (no effect on the bound)
+                            // branch-free: a triple without a valid configuration (B* = 0) reads
+                            // hide[0] and iparmin[0] = NaN, so it is keyed NaN (never a
+                            // candidate) and ranked +inf (no effect on the bound); W* = B* W_B
+                            // <= W_mp <= kMaxW for a valid triple. X is finite (counts <= 2^40).
                             const int B = min(gwr, gs[c]);
-                            const int Bv = max(B, 1);
-                            // (W* <= kMaxW for a valid triple; the clamp only keeps the B* = 0 lookup in range)
-                            const float X = __fmul_rn(__fmaf_rn(cmv, ct.hide[min(Bv * wb, kMaxW)], cnm), ln);
-                            // NaN (from infinite counts) is ranked as +inf
-                            float m = fminf(__fmul_rn(X, w.iparmin[Bv - 1]), kInf);
-                            key[c] = B > 0 ? m : __int_as_float(0x7fc00000);
-                            m = B > 0 ? m : kInf;
+                            const float X = __fmul_rn(__fmaf_rn(cmv, ct.hide[B * wb], cnm), ln);
+                            key[c] = __fmul_rn(X, w.iparmin[B]);
+                            float m = fminf(key[c], kInf);
                             {
                                 float lo;
                                 lo = fminf(m0, m); m = fmaxf(m0, m); m0 = lo;
@@ -710,7 +713,7 @@ __global__ void __maxnreg__(64)
                         base = t_r * g_stride + uc_r;
                         if (B > 0) {
                             const float* row = ipar_rows + (B - 1) * 16;
-                            any = __fmul_rn(X, w.iparmin[B - 1]) <= tau_c;
+                            any = __fmul_rn(X, w.iparmin[B]) <= tau_c;
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
                                 if (j < nG) {

@@ -45,6 +45,8 @@ def _emit_lib():
         L.tune_emit_measure.argtypes = [C.POINTER(native.TuneAxes), vp, i64, vp, vp, i64, i32, C.c_float, i32,
                                         vp, vp, vp, vp]
         L.tune_emit_measure.restype = C.c_int
+        L.tune_emit_count.argtypes = [C.POINTER(native.TuneAxes), vp, i64, vp, vp, i64, i32, C.c_float, vp, vp]
+        L.tune_emit_count.restype = C.c_int
         L._emit_declared = True
     return L
 
@@ -67,6 +69,42 @@ def measure(axes, descs, skern, spoint, items=ITEMS, scale=COUNT_SCALE, reps=3, 
                                      int(items), float(scale), int(reps), us.ctypes.data, regs.ctypes.data,
                                      cfg.ctypes.data, C.c_void_p(s.cuda_stream)))
     return (us, regs, cfg) if launched else (us, regs)
+
+
+def count_ops(axes, descs, skern, spoint, items=ITEMS, scale=COUNT_SCALE, stream=None):
+    """Operations executed per class (FP32, FP64, INT, GLDST, SLDST, BRANCH, SFU) by all threads
+    of each sample's variant, uint64 [n, 7] (all ones where the launch is not possible)."""
+    import torch
+
+    L = _emit_lib()
+    d = np.ascontiguousarray(descs)
+    sk = np.ascontiguousarray(skern, dtype=np.int32)
+    sp = np.ascontiguousarray(spoint, dtype=np.int32)
+    out = np.empty((len(sk), 7), dtype=np.uint64)
+    s = torch.cuda.current_stream() if stream is None else stream
+    x = native.make_axes(axes)
+    native.check(L.tune_emit_count(C.byref(x), d.ctypes.data, len(d), sk.ctypes.data, sp.ctypes.data, len(sk),
+                                   int(items), float(scale), out.ctypes.data, C.c_void_p(s.cuda_stream)))
+    return out
+
+
+CATEGORIES = {"FLOPS": (0, 1, 6), "MEM": (3, 4), "CTRL": (5,), "INT": (2,)}
+
+
+def mix_error(static, dynamic):
+    """Section IV's comparison of a static and a dynamic instruction mix, per category
+    (FLOPS = FP32 + FP64 + SFU, MEM = global + shared loads/stores, CTRL = branches, INT):
+    the squared difference of the two mixes' category shares in percent, (100 f_s - 100 f_d)^2,
+    and the intensity FLOPS / MEM of the static mix."""
+    st = np.asarray(static, np.float64)
+    dy = np.asarray(dynamic, np.float64)
+    out = {}
+    for name, cls in CATEGORIES.items():
+        fs = st[list(cls)].sum() / st.sum()
+        fd = dy[list(cls)].sum() / dy.sum()
+        out[name] = float((100 * fs - 100 * fd) ** 2)
+    out["intensity"] = float(st[[0, 1, 6]].sum() / max(st[[3, 4]].sum(), 1e-30))
+    return out
 
 
 def per_unit_ns(us, cfg, items=ITEMS):
@@ -117,9 +155,10 @@ def build_set(arch, axes, descs, per_desc, seed, dev):
 
 def analytic_set(arch, axes, descs, per_desc, seed, dev):
     """Training set labelled by the analytic model itself (the surrogate's sanity case): the
-    same sampled points and features as build_set, label ln(cost) - (its median) from
-    tune_eval's per-point costs (a constant shift changes neither the ranking nor the members'
-    std / mean); points without a valid configuration are dropped."""
+    same sampled points and features as build_set, label (ln(cost) - median) / std from
+    tune_eval's per-point costs (a positive affine map of the label keeps the ranking; the
+    members' std / mean is not used with these labels); points without a valid configuration
+    are dropped."""
     import torch
 
     from workloads import gen
@@ -136,10 +175,10 @@ def analytic_set(arch, axes, descs, per_desc, seed, dev):
     keep = np.isfinite(cost) & (cost > 0)
     idx = torch.from_numpy(np.nonzero(keep)[0]).to(dev)
     lab = np.log(cost[keep])
-    shift = float(np.median(lab))
+    shift, scale = float(np.median(lab)), float(np.std(lab)) or 1.0
     return {"feats": feats[idx].contiguous(),
-            "labels": torch.from_numpy((lab - shift).astype(np.float32)).to(dev),
-            "n": int(keep.sum()), "measured": len(cost), "label_shift": shift}
+            "labels": torch.from_numpy(((lab - shift) / scale).astype(np.float32)).to(dev),
+            "n": int(keep.sum()), "measured": len(cost), "label_shift": shift, "label_scale": scale}
 
 
 def train(data, members=5, epochs=20, batch=8192, lr=1e-3, seed=5, dev="cuda"):

@@ -6,6 +6,8 @@
 * Every thread runs the same per-thread work at every launch shape, so time per
   unit of work (time / (G T)) is what the static cost ranks: the analytic cost and
   the measured per-unit time must be rank-correlated on fully timed spaces.
+* Each class's executed operations (an instrumented build of the variants) equal
+  what the descriptor asks for at that launch.
 * Failure paths made on the host: an injected compile failure returns
   TUNE_ECOMPILE and the next call works; one repetition made a second slower is
   discarded by the median of three (and shows with a single repetition).
@@ -112,3 +114,53 @@ def test_injected_slow_repetition_is_discarded_by_the_median(dev):
     T.tune_inject_fault(native.TUNE_FAULT_SLOW_REP, 0)
     assert base[0] < 1e5 and med[0] < 1e5, (base, med)   # well under the injected second
     assert single[0] >= 1e6                             # the fault itself was live
+
+
+def _expected_counts(desc, T, G, items, scale):
+    """Operations per class a variant's threads must execute: each thread runs `items` items of
+    round(n_c scale) operations per class (computed in FP32 as the library does); shared
+    loads/stores only with at least 4 bytes of shared memory; lanes below round(32 d) of every
+    warp repeat the FP32 loop."""
+    n = np.floor(np.float32(desc["n"]) * np.float32(scale) + np.float32(0.5)).astype(np.int64)
+    if int(desc["s0"]) // 4 == 0:
+        n[4] = 0
+    div = int(np.floor(np.float32(desc["d"]) * np.float32(32.0) + np.float32(0.5)))
+    lanes_div = sum(1 for t in range(T) if (t & 31) < div)
+    e = n * G * T * items
+    e[0] += n[0] * G * lanes_div * items
+    return e
+
+
+def test_executed_instruction_counts_match_the_descriptors(dev, oracle):
+    """The dynamic side of the static-versus-dynamic instruction mix (Section IV): every class's
+    executed operations, tallied in an instrumented build of each variant, equal what its
+    descriptor asks for at that launch (so the labels time the work the features describe);
+    with divergence the dynamic mix departs from the static one only by the repeated FP32
+    loop, which the mix error shows."""
+    from paper_1701_08547_gb300 import surrogate_data as SD
+
+    ax = gen.axes()
+    d = gen.descriptors(30, 65, "dense")
+    d["space_mask"] = np.uint64(gen.mask_bits([0, 1, 4, 7, 31], [0, 3, 6], [0, 3], [3]))
+    d["s0"][:3] = [0, 3, 5]  # no shared memory, or less than one word
+    d["d"][3] = np.float32(0.0)
+    d["d"][4] = np.float32(1.0)
+    sizes = gen.space_sizes(d)
+    rng = np.random.default_rng(6)
+    kern = np.arange(len(d))
+    pt = np.array([rng.integers(0, sizes[k]) for k in kern], dtype=np.int32)
+    items, scale = 2, 1.0 / 2048
+    cnt = SD.count_ops(ax, d, kern, pt, items=items, scale=scale)
+    checked = 0
+    for i in range(len(kern)):
+        if np.all(cnt[i] == np.iinfo(np.uint64).max):
+            continue
+        T_, G_, U_, C_ = oracle.decode_point(d[kern[i]], ax, pt[i])
+        want = _expected_counts(d[kern[i]], T_, G_, items, scale)
+        assert np.array_equal(cnt[i].astype(np.int64), want), (i, cnt[i], want)
+        checked += 1
+    assert checked >= 25
+    # mix error: zero without divergence (up to the rounding of n scale), grows with d
+    e0 = SD.mix_error(d["n"][3] * scale, cnt[3])
+    e1 = SD.mix_error(d["n"][4] * scale, cnt[4])
+    assert e0["FLOPS"] < 1.0 and e1["FLOPS"] > e0["FLOPS"]
