@@ -40,6 +40,8 @@ WORKLOADS = {
     "surfwd": (1 << 20, None, 0, 12),
     "surtrain": (1 << 16, None, 0, 13),
     "search": (100_000, "dense", 1, 2),
+    "mix": (12, "dense", 0, 67),
+    "emit": (100_000, "dense", 10, 2),
 }
 ISSUE_LANES_PER_SM_CLK = 4 * 32  # 4 schedulers x 32 lanes per SM and clock
 # Thread-instructions of a per-point evaluation after the per-kernel hoists (decode ~3,
@@ -481,6 +483,24 @@ def emit_points(args, dev, stream, flush, world):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline("dense", 4000, emit=True)
     return line
+
+
+def run_emit(args):
+    """The every-point path alone (TUNE_EMIT_POINTS on the dense workload; --kernels sets a
+    smaller case for profiling)."""
+    import torch
+
+    from paper_1701_08547_gb300 import build as B
+
+    B.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    a2 = argparse.Namespace(**vars(args))
+    a2.emit_kernels = args.kernels or 0
+    return emit_points(a2, dev, stream, flush, 1)
 
 
 def run_ours(args):
@@ -966,6 +986,62 @@ def run_search(args):
             "methods": out, "gpu_launches": args.steps}
 
 
+MIX_POINT = (256, 64, 2, 100)  # (T, G, U, carveout %) at which the mix samples are launched
+
+
+def run_mix(args):
+    """Static versus dynamic instruction mix (Section IV, Table "Error rates when estimating
+    dynamic instruction mixes from static mixes"), the launches for an ncu capture: 12 dense
+    descriptors' variants at one point (one untimed and one timed launch each) and the three
+    real kernels at (T = 128, G = 1024, U = 4, C = 100 %) (one untimed and one timed run each).
+    Prints, per variant, the descriptor's counts (scaled as emitted), the executed operations per
+    class tallied by an instrumented build (tune_emit_count) and their mix error; per real
+    kernel, its descriptor. The SASS-level dynamic mix comes from ncu's per-class counters of
+    the same launches (`kernel name` variant / rows / cols, in this order)."""
+    import torch
+
+    from paper_1701_08547_gb300 import build as B
+    from paper_1701_08547_gb300 import realkernels as RK
+    from paper_1701_08547_gb300 import surrogate_data as SD
+
+    B.build()
+    torch.cuda.set_device(0)
+    ax = gen.axes()
+    d = gen.descriptors(12, 67, "dense")
+    d["d"][:6] = np.float32(0.0)  # half without divergence
+    T_, G_, U_, C_ = MIX_POINT
+    p = (((ax["t"].index(T_) * 16 + ax["g"].index(G_)) * 8 + ax["u"].index(U_)) * 4 + ax["c"].index(C_))
+    kern = np.arange(len(d))
+    pt = np.full(len(d), p, dtype=np.int32)
+    cnt = SD.count_ops(ax, d, kern, pt)
+    us, _, cfg = SD.measure(ax, d, kern, pt, reps=1, launched=True)
+    scaled = np.floor(d["n"].astype(np.float32) * np.float32(SD.COUNT_SCALE) + np.float32(0.5)).astype(np.int64)
+    variants = []
+    for i in range(len(d)):
+        variants.append({"launch": list(map(int, cfg[i])), "us": float(us[i]),
+                         "static_per_thread": scaled[i].tolist(), "d": float(d["d"][i]),
+                         "executed": cnt[i].astype(np.int64).tolist(),
+                         "mix_error_executed": SD.mix_error(scaled[i], cnt[i])})
+    real = {}
+    n = 2048
+    for kind in RK.KINDS:
+        pts = np.array([[128, 1024, 4, 100]], dtype=np.int32)
+        cols = [np.ascontiguousarray(pts[:, j]) for j in range(4)]
+        usr = np.empty(1, np.float32)
+        regs = np.empty(1, np.int32)
+        from paper_1701_08547_gb300 import native
+
+        native.check(native.load().tune_real_measure(RK.KINDS[kind], n, *[c.ctypes.data for c in cols], 1, 1,
+                                                     usr.ctypes.data, regs.ctypes.data, None, None))
+        desc = RK.descriptor(kind, n, int(regs[0]), ax)
+        real[kind] = {"n": n, "launch": [128, 1024, 4, 100], "us": float(usr[0]),
+                      "static_per_item": desc["n"][0].astype(np.int64).tolist(),
+                      "items": n if kind == "matvec" else 2 * n}
+    return {"metric": "static vs dynamic instruction mix (launches for ncu)", "value": None, "unit": None,
+            "classes": ["FP32", "FP64", "INT", "GLDST", "SLDST", "BRANCH", "SFU"],
+            "count_scale": SD.COUNT_SCALE, "variants": variants, "real_kernels": real}
+
+
 def run_topk(args):
     """Segmented top-k over external scores: 100,000 segments x 16,384 float32
     scores (the dense workload's point count), top-10; HBM-bound."""
@@ -1141,6 +1217,10 @@ def main():
         line = run_surtrain(args)
     elif args.workload == "search":
         line = run_search(args)
+    elif args.workload == "mix":
+        line = run_mix(args)
+    elif args.workload == "emit":
+        line = run_emit(args)
     else:
         line = run_ours(args)
     if line is not None:

@@ -29,9 +29,9 @@ from .surrogate import Surrogate
 
 ITEMS = 1                 # work items per thread
 COUNT_SCALE = 1.0 / 1024.0
-# Sub-space sampled for labels: threads >= 64, grid 64 .. 4096 blocks (axis positions), so
-# that every variant finishes within a few milliseconds.
-T_MIN_POS, G_MIN_POS, G_MAX_POS = 1, 6, 12
+# Sub-space sampled for labels: threads >= 64, grid 64 .. 2048 blocks (axis positions), so
+# that every variant finishes within about a millisecond.
+T_MIN_POS, G_MIN_POS, G_MAX_POS = 1, 6, 11
 # Held-out spaces, fully timed: 5 thread counts x 4 grids x unroll {1, 4} x carveout {0, 100}
 EVAL_T, EVAL_G, EVAL_U, EVAL_C = [1, 3, 7, 15, 31], [7, 9, 11, 13], [0, 3], [0, 3]
 # Pruning spaces, fully timed: all 32 thread counts x grids {512, 2048} x unroll 1 x carveout 100
@@ -114,7 +114,7 @@ def per_unit_ns(us, cfg, items=ITEMS):
 
 def sample_points(descs, per_desc, seed):
     """per_desc random canonical point indices per descriptor, restricted to T >= 64 and
-    64 <= G <= 4096."""
+    64 <= G <= 2048."""
     rng = np.random.default_rng(seed)
     skern, spoint = [], []
     for i, d in enumerate(descs):
