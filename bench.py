@@ -634,7 +634,10 @@ def surrogate_section(args, dev, a, ax, peaks, stream):
             "top5_vs_analytic": {"overlap": float(np.mean([len(set(si[i]) & set(ai[i])) / 5 for i in range(nk)])),
                                  "analytic_best_in_top5": float(np.mean([ai[i, 0] in si[i] for i in range(nk)]))},
             "top5_vs_measured_best": {"thresh_0.1": ev_fb, "no_fallback": ev_nofb},
-            "clocks": clk.summary(), "gpu_launches": None,
+            "clocks": clk.summary(),
+            # the analytic top-k (1), then per chunk of 64 kernels (2^20 points): offsets, features,
+            # the fused ensemble forward, scores, segmented top-k, fallback (6)
+            "gpu_launches": 1 + 6 * ((nk + 63) // 64),
         }
         if not args.no_cpu_baseline and name == "bf16":
             c5[name]["cpu_baseline"] = surrogate_cpu_baseline(a, ax, inf_sur, members)
@@ -718,7 +721,10 @@ def train_section(args, dev, data, members, peaks, stream):
                     "d2h_bytes_per_step": 4 * members,
                     "call": "features, labels and epoch orders copied from pinned host memory, surrogate_train, "
                             "loss trace copied back, all inside the timed region"},
-            "final_mse": float(trace[-1].mean()), "gpu_launches": None}
+            "final_mse": float(trace[-1].mean()),
+            # per step: batch gather, fused forward, loss (2), head backward (2), weight transpose and
+            # fused input-gradient chain (2), four weight-gradient passes with their reductions (8), Adam
+            "gpu_launches": 17 * epochs * steps}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = train_cpu_baseline(members)
     return line, sur
