@@ -13,7 +13,7 @@ constexpr int kMaxW = 64;  // warps per SM supported by the tables
 
 enum { CL_FP32 = 0, CL_FP64, CL_INT, CL_GLDST, CL_SLDST, CL_BRANCH, CL_SFU };
 
-__device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 // Compensated (Neumaier) FP32 sum, explicit round-to-nearest operations.
 template <int M>
@@ -58,14 +58,15 @@ __device__ __forceinline__ void unit_costs(const float (&n)[7], float d, int U, 
 // allocation unit; warps the register file holds, rounded down to the warp
 // allocation granularity and clamped to kMaxW; the largest W_B whose block
 // fits the per-block register limit.
-__device__ __forceinline__ void reg_params(const tune_arch& a, int R, int& warps, int& wbmax)
+__host__ __device__ __forceinline__ void reg_params(const tune_arch& a, int R, int& warps, int& wbmax)
 {
     warps = 0;
     wbmax = 0;
     if (a.reg_alloc_mode == 0 && R > 0 && R <= a.regs_thread_max) {
         const int rpw = ceil_div(R * 32, a.reg_alloc_unit) * a.reg_alloc_unit;
         wbmax = a.regs_block_max / rpw;
-        warps = min((a.regs_sm / rpw) / a.warp_alloc_gran * a.warp_alloc_gran, kMaxW);
+        const int w = (a.regs_sm / rpw) / a.warp_alloc_gran * a.warp_alloc_gran;
+        warps = w < kMaxW ? w : kMaxW;
     }
 }
 

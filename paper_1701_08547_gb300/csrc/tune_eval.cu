@@ -26,7 +26,10 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <string.h>
+
 #include <algorithm>
+#include <limits>
 #include <mutex>
 
 #include "eval_common.cuh"
@@ -45,15 +48,6 @@ constexpr unsigned kFull = 0xffffffffu;
 
 constexpr int kMaxArch = 8;  // architecture rows of one launch (blockIdx.y)
 
-struct EvalParams {
-    tune_arch a[kMaxArch];
-    int n_arch;
-    tune_axes x;
-    int64_t n_kernels;
-    int k;
-    int chunk;  // dynamic work queue: kernels per grab (0 = static stride)
-};
-
 struct CtaTables {
     float ipar[kMaxB][16];           // (waves*slots)/(n_sm*G) by (B*-1, g position); +inf padding
     float rcp[8];                    // 1 / IPC per class
@@ -69,6 +63,21 @@ struct CtaTables {
     int cap_lo[4];                   // first capacity index allowed by carveout position c
     int order_safe;                  // 1: distinct ipar values of a row differ by more than 2^-21 relative
     int unit_shift;                  // log2 of the shared-memory allocation unit, or -1
+};
+
+// Parameters of one launch. For a single architecture row the host builds the CTA tables
+// (they depend on the row and the axes only) and passes them here, 6.6 KB of kernel
+// parameters each CTA copies to shared memory; with several rows (blockIdx.y) every CTA
+// builds its row's tables itself.
+struct EvalParams {
+    tune_arch a[kMaxArch];
+    int n_arch;
+    tune_axes x;
+    int64_t n_kernels;
+    int k;
+    int chunk;        // dynamic work queue: kernels per grab (0 = static stride)
+    int host_tables;  // 1: tab holds row 0's tables
+    CtaTables tab;
 };
 
 struct WarpTables {
@@ -89,8 +98,116 @@ struct WarpTables {
     };
 };
 
+// The same tables, built on the host for a single architecture row (IEEE single-precision
+// divisions and multiplications, each rounded to nearest as __fdiv_rn / __fmul_rn round them on
+// the device, so the values are bit for bit those of build_cta_tables below).
+void host_cta_tables(const tune_arch& a, const tune_axes& x, CtaTables& ct)
+{
+    memset(&ct, 0, sizeof(ct));
+    const float inf = std::numeric_limits<float>::infinity();
+    for (int b = 0; b < kMaxB; ++b)
+        for (int g = 0; g < 16; ++g) {
+            float v = inf;
+            if (b < a.max_blocks_sm && g < x.n_g) {
+                const int slots = a.n_sm * (b + 1), G = x.g[g];
+                const int waves = (G + slots - 1) / slots;
+                v = (float)(waves * slots) / (float)(a.n_sm * G);
+            }
+            ct.ipar[b][g] = v;
+        }
+    for (int w = 0; w <= kMaxW; ++w)
+        for (int t = 0; t < 32; ++t) {
+            const int wb = t < x.n_t ? (x.t[t] + 31) / 32 : 1;
+            ct.divt[w][t] = (unsigned char)(w / wb);
+        }
+    ct.order_safe = 1;
+    const int u = a.smem_alloc_unit;
+    ct.unit_shift = (u & (u - 1)) == 0 ? __builtin_ctz((unsigned)u) : -1;
+    for (int b = 0; b < kMaxB; ++b) {
+        float mn = inf;
+        for (int g = 0; g < x.n_g; ++g) mn = std::min(mn, ct.ipar[b][g]);
+        ct.iparmin[b] = mn;
+        unsigned char* ord = ct.perm[b];
+        for (int g = 0; g < x.n_g; ++g) {
+            const float v = ct.ipar[b][g];
+            int j = g;
+            while (j > 0 && ct.ipar[b][ord[j - 1]] > v) {
+                ord[j] = ord[j - 1];
+                --j;
+            }
+            ord[j] = (unsigned char)g;
+        }
+        for (int r = 0; r + 1 < x.n_g; ++r) {
+            const float v1 = ct.ipar[b][ord[r]], v2 = ct.ipar[b][ord[r + 1]];
+            const volatile float gap = v2 - v1, tol = v1 * 0x1p-21f;  // two roundings, no fused form
+            if (v2 != v1 && gap <= tol) ct.order_safe = 0;
+        }
+    }
+    for (int t = 0; t < 32; ++t) {
+        int wb = 1, gw = 0;
+        float ln = 1.0f;
+        if (t < x.n_t) {
+            const int T = x.t[t];
+            wb = (T + 31) / 32;
+            gw = T <= a.max_threads_block ? std::min(a.max_blocks_sm, a.max_warps_sm / wb) : 0;
+            ln = (float)(32 * wb) / (float)T;
+        }
+        ct.wb[t] = wb;
+        ct.gw[t] = gw;
+        ct.lane[t] = ln;
+    }
+    for (int w = 0; w <= kMaxW; ++w) ct.hide[w] = std::max(1.0f, w > 0 ? (float)a.w_sat / (float)w : 1.0f);
+    for (int c = 0; c < 8; ++c) ct.rcp[c] = c < TUNE_NCLASS ? 1.0f / a.ipc[c] : 0.0f;
+    for (int c = 0; c < 4; ++c) {
+        const long long need = c < x.n_c ? (long long)x.c[c] * a.smem_caps[a.n_smem_caps - 1] : 0;
+        int i = 0;
+        while (i < a.n_smem_caps && 100LL * a.smem_caps[i] < need) ++i;
+        ct.cap_lo[c] = i;
+    }
+    for (int R = 0; R < 256; ++R) {
+        int warps, wbmax;
+        reg_params(a, R, warps, wbmax);
+        ct.rwarps[R] = (unsigned short)warps;
+        ct.rwbmax[R] = (unsigned short)std::min(wbmax, 65535);
+    }
+}
+
+// host_cta_tables for the launch's row 0, reusing the last result of the calling thread when the
+// row and the axes are the same (compared byte for byte).
+void fill_host_tables(EvalParams& q)
+{
+    struct Last {
+        bool valid = false;
+        tune_arch a;
+        tune_axes x;
+        CtaTables t;
+    };
+    static thread_local Last last;
+    if (!last.valid || memcmp(&last.a, &q.a[0], sizeof(tune_arch)) != 0 ||
+        memcmp(&last.x, &q.x, sizeof(tune_axes)) != 0) {
+        last.a = q.a[0];
+        last.x = q.x;
+        host_cta_tables(last.a, last.x, last.t);
+        last.valid = true;
+    }
+    q.tab = last.t;
+    q.host_tables = 1;
+}
+
+// Row 0's tables from the launch parameters into shared memory (a word per thread and step).
+__device__ __forceinline__ void copy_cta_tables(const CtaTables& src, CtaTables& ct)
+{
+    const uint32_t* s = reinterpret_cast<const uint32_t*>(&src);
+    uint32_t* d = reinterpret_cast<uint32_t*>(&ct);
+    for (int i = threadIdx.x; i < (int)(sizeof(CtaTables) / 4); i += blockDim.x) d[i] = s[i];
+}
+
 __device__ void build_cta_tables(const EvalParams& p, const tune_arch& a, CtaTables& ct)
 {
+    if (p.host_tables) {
+        copy_cta_tables(p.tab, ct);
+        return;
+    }
     const tune_axes& x = p.x;
     for (int i = threadIdx.x; i < kMaxB * 16; i += blockDim.x) {
         int b = i >> 4, g = i & 15;
@@ -985,7 +1102,9 @@ int launch_thread(const EvalParams& p, const tune_kernel_desc* descs, int32_t* t
     const int64_t need = (p.n_kernels + kThreadsT - 1) / kThreadsT;
     const int64_t cap = (int64_t)sms * per_sm;
     const int grid = (int)(need < cap ? need : cap);
-    kern<<<grid, kThreadsT, 0, s>>>(p, reinterpret_cast<const int4*>(descs), ti, tc, status);
+    EvalParams q = p;
+    fill_host_tables(q);
+    kern<<<grid, kThreadsT, 0, s>>>(q, reinterpret_cast<const int4*>(descs), ti, tc, status);
     TUNE_CUDA_TRY(cudaGetLastError(), "tune_eval: kernel launch");
     return TUNE_OK;
 }
@@ -1010,7 +1129,10 @@ int launch_rows(const EvalParams& p, const tune_kernel_desc* descs, int32_t* ti,
     // By default the queue counters (one per row) follow the status word in the zeroed
     // workspace header.
     if (!queue) queue = reinterpret_cast<unsigned long long*>(status) + 1;
-    kern<<<dim3(grid, p.n_arch), kThreads, 0, s>>>(p, reinterpret_cast<const int4*>(descs), ti, tc, pb, pw, pc, po,
+    EvalParams q = p;
+    q.host_tables = 0;
+    if (!MULTI) fill_host_tables(q);
+    kern<<<dim3(grid, p.n_arch), kThreads, 0, s>>>(q, reinterpret_cast<const int4*>(descs), ti, tc, pb, pw, pc, po,
                                                   status, queue);
     TUNE_CUDA_TRY(cudaGetLastError(), "tune_eval: kernel launch");
     return TUNE_OK;
