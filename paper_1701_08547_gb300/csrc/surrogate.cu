@@ -252,7 +252,16 @@ __global__ void split_reduce(const float* __restrict__ part, float* grad, long l
     if (bpart && blockIdx.x == gridDim.x - 1) {
         const float* b = bpart + (long long)mem * brows * WID + threadIdx.x;
         float s = 0.0f;
-        for (int q = 0; q < brows; ++q) s += b[(long long)q * WID];
+        for (int q0 = 0; q0 < brows; q0 += 16) {
+            // up to 16 rows requested together, then added in row order
+            float t[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (q0 + q < brows) t[q] = __ldg(b + (long long)(q0 + q) * WID);
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (q0 + q < brows) s += t[q];
+        }
         grad[mem * P + off_b + threadIdx.x] = s;
         return;
     }
