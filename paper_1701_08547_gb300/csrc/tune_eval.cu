@@ -42,6 +42,7 @@ using namespace tune_dev;
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kMaxB = 32;  // blocks per SM supported by the tables
+constexpr int kIparStride = 17;  // words per ipar row (16 grid positions and one of padding)
 constexpr unsigned kFull = 0xffffffffu;
 
 
@@ -49,7 +50,9 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxArch = 8;  // architecture rows of one launch (blockIdx.y)
 
 struct CtaTables {
-    float ipar[kMaxB][16];           // (waves*slots)/(n_sm*G) by (B*-1, g position); +inf padding
+    // (waves*slots)/(n_sm*G) by (B*-1, g position); +inf padding. Rows of 17 words, so that a
+    // warp reading one g position of 32 rows (lane = row) touches 32 distinct banks.
+    float ipar[kMaxB][kIparStride];
     float rcp[8];                    // 1 / IPC per class
     float hide[kMaxW + 1];           // max(1, W_sat / W*)
     float lane[32];                  // (32 * W_B) / T by t position
@@ -92,7 +95,7 @@ struct WarpTables {
     union {
         float key[32 * 32];  // ranking pass: each triple's minimum cost, by (row, lane)
         struct {             // emitting pass:
-            float iparc[kMaxB][16];  // ipar rows compacted to the kernel's grid sizes
+            float iparc[kMaxB][kIparStride];  // ipar rows compacted to the kernel's grid sizes
             float4 uc[32];   // by (u rank * n_C + c rank): C_nm, C_m, u rank, G_S
         };
     };
@@ -829,7 +832,7 @@ __global__ void __maxnreg__(64)
                         X = __fmul_rn(__fmaf_rn(ucv.y, ct.hide[W], ucv.x), __int_as_float(ti.y));
                         base = t_r * g_stride + uc_r;
                         if (B > 0) {
-                            const float* row = ipar_rows + (B - 1) * 16;
+                            const float* row = ipar_rows + (B - 1) * kIparStride;
                             any = __fmul_rn(X, w.iparmin[B]) <= tau_c;
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
