@@ -260,7 +260,8 @@ int surrogate_set_params(tune_surrogate* h, const float* host, int64_t n);
 /* Copy to host: what = 0 master weights, 1 gradients of the last step, 2 Adam m, 3 Adam v
  * (members x param_count floats), 4 last loss per member (members floats), 5 last
  * predictions (members x batch), 6 the E4M3 codes of W2..W4 as their values (members x 3
- * x 256 x 256), 7 the per-row scales of those codes (members x 3 x 256). Synchronous. */
+ * x 256 x 256), 7 the scales of those codes (members x 3 x 256: one per matrix, repeated for each
+ * of its rows). Synchronous. */
 int surrogate_get(tune_surrogate* h, int what, float* host, int64_t n);
 /* pred (device, [members, n]) = each member's output for feats (device bf16 [n, 128]).
  * By default one persistent launch runs every member over 128-row tiles with the
@@ -281,8 +282,8 @@ int surrogate_members(const tune_surrogate* h);
 /* Options: 0 = layer-by-layer forward on tcgen05 tensor cores (value 1, the default) or
  * on mma.sync (value 0); 1 = how surrogate_forward / surrogate_infer run the ensemble:
  * 0 layer by layer (option 0 picks the GEMM), 1 fused BF16 (default), 2 fused with
- * layers 2-4 on E4M3 codes: W2..W4 quantised per output row (scale = max |w| / 448,
- * nearest-even, saturating), activations with unit scale, FP32 accumulation;
+ * layers 2-4 on E4M3 codes: each of W2..W4 quantised with one scale (max |w| over the matrix
+ * / 448; codes nearest-even, saturating), activations as codes of 2 h, FP32 accumulation;
  * 2 = training's backward pass: 0 one mma.sync GEMM per input and weight gradient;
  * 1 (default, with option 0 on) the chain dZ4 -> dZ3 -> dZ2 -> dZ1 (products with W4,
  * W3, W2) in one fused tcgen05 launch and the weight gradients on tcgen05 (both

@@ -15,8 +15,8 @@ and the back-propagated dz_l) are rounded to BF16 (via FP32, round-to-nearest-ev
 the same points; all arithmetic stays FP64.
 
 FP8 inference (forward_fp8): layers 2-4 take E4M3 operands (OCP FP8: 4 exponent bits,
-bias 7, 3 mantissa bits, largest finite 448, subnormal spacing 2^-9). Weights are scaled
-per output row: s_n = max_k |W[n][k]| / 448 (1 if the row is zero), code = E4M3(W / s_n),
+bias 7, 3 mantissa bits, largest finite 448, subnormal spacing 2^-9). Each weight matrix
+has one scale: s = max_{n,k} |W[n][k]| / 448 (1 if the matrix is zero), code = E4M3(W / s),
 both steps in FP32 as the kernel takes them (the codes are integers: both sides decide
 them in the same precision); activations are quantised with scale 1/2 (codes of 2 h).
 Rounding to E4M3 is to nearest, ties to even, saturating at +-448.
@@ -67,12 +67,13 @@ def e4m3(x):
     return np.copysign(q, x)
 
 
-def quantize_rows(W):
-    """Per-row E4M3 quantisation of a weight matrix, in FP32 like the kernel: (codes, scales)."""
+def quantize_matrix(W):
+    """E4M3 quantisation of a weight matrix with one scale, in FP32 like the kernel:
+    (codes, scale)."""
     W32 = np.asarray(W, dtype=np.float32)
-    amax = np.max(np.abs(W32), axis=1)
-    s = np.where(amax > 0, amax / np.float32(E4M3_MAX), np.float32(1.0)).astype(np.float32)
-    return e4m3(W32 / s[:, None]), s
+    amax = np.float32(np.max(np.abs(W32)))
+    s = np.float32(amax / np.float32(E4M3_MAX)) if amax > 0 else np.float32(1.0)
+    return e4m3(W32 / s), s
 
 
 def _r(x, on):
@@ -99,8 +100,8 @@ def forward_fp8(p, X):
     z = h @ bf16(p["W1"]).T + np.asarray(p["b1"], np.float64)
     h = gelu(z)
     for l in range(2, 5):
-        q, s = quantize_rows(p[f"W{l}"])
-        z = (e4m3(2.0 * h) @ q.T) * (0.5 * s.astype(np.float64)) + np.asarray(p[f"b{l}"], np.float64)
+        q, s = quantize_matrix(p[f"W{l}"])
+        z = (e4m3(2.0 * h) @ q.T) * (0.5 * np.float64(s)) + np.asarray(p[f"b{l}"], np.float64)
         h = gelu(z)
     return h @ np.asarray(p["w5"], np.float64) + float(p["b5"][0])
 

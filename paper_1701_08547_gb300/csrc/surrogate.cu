@@ -354,24 +354,25 @@ __global__ void transpose_weights(const __nv_bfloat16* __restrict__ wbf, __nv_bf
 // (1 for a zero row), code = E4M3(w / s), nearest-even, saturating. grid (256, 3, members) x 256.
 __global__ void quantize_fp8(const float* __restrict__ master, uint8_t* w8, float* wscale, float* wscale_half)
 {
-    const int row = blockIdx.x, l = blockIdx.y + 1, mem = blockIdx.z;
-    const float w = master[mem * P + OFF_W(l) + (long long)row * WID + threadIdx.x];
+    // block = one matrix W_l of one member; thread t = column t (coalesced row reads)
+    const int l = blockIdx.x + 1, mem = blockIdx.y, t = threadIdx.x;
+    const float* W = master + mem * P + OFF_W(l);
     __shared__ float red[WID / 32];
-    float a = fabsf(w);
+    float a = 0.0f;
+    for (int r = 0; r < WID; ++r) a = fmaxf(a, fabsf(W[(long long)r * WID + t]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    if ((t & 31) == 0) red[t >> 5] = a;
     __syncthreads();
     float amax = 0.0f;
 #pragma unroll
     for (int i = 0; i < WID / 32; ++i) amax = fmaxf(amax, red[i]);
     const float sc = amax > 0.0f ? __fdiv_rn(amax, 448.0f) : 1.0f;
-    const long long r = ((long long)mem * 3 + (l - 1)) * WID + row;
-    w8[r * WID + threadIdx.x] = __nv_cvt_float_to_fp8(__fdiv_rn(w, sc), __NV_SATFINITE, __NV_E4M3);
-    if (threadIdx.x == 0) {
-        wscale[r] = sc;
-        wscale_half[r] = 0.5f * sc;
-    }
+    const long long m0 = ((long long)mem * 3 + (l - 1)) * WID;
+    for (int r = 0; r < WID; ++r)
+        w8[(m0 + r) * WID + t] = __nv_cvt_float_to_fp8(__fdiv_rn(W[(long long)r * WID + t], sc), __NV_SATFINITE, __NV_E4M3);
+    wscale[m0 + t] = sc;  // every row of the matrix carries the matrix's scale
+    wscale_half[m0 + t] = 0.5f * sc;
 }
 
 // Batch gather: xin[r] = feats[order[r]], lbl[r] = labels[order[r]] (rows past n are zero).
@@ -513,7 +514,7 @@ int make_map_nd(CUtensorMap* map, CUtensorMapDataType dt, int rank, const void* 
 int refresh_fp8(tune_surrogate* h, cudaStream_t s)
 {
     if (!h->fp8_stale) return TUNE_OK;
-    quantize_fp8<<<dim3(WID, NL - 1, h->members), WID, 0, s>>>(h->master, h->w8, h->wscale, h->wscale_half);
+    quantize_fp8<<<dim3(NL - 1, h->members), WID, 0, s>>>(h->master, h->w8, h->wscale, h->wscale_half);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: quantize launch");
     h->fp8_stale = false;
     return TUNE_OK;

@@ -26,7 +26,7 @@
 // Precision: layer 1 (K = 128) is BF16 x BF16 in both variants; GELU is
 // evaluated in FP32. The BF16 variant keeps layers 2-4 in BF16; the FP8
 // variant stores E4M3 codes of 2 h (activation scale 1/2) and W2..W4 as E4M3
-// codes with per-row scales, and runs layers 2-4 with kind::f8f6f4.
+// codes with one scale per matrix, and runs layers 2-4 with kind::f8f6f4.
 // The head takes the FP32 values 2 h4 and sums in FP32.
 //
 // Every wait is bounded; on timeout the kernel sets status bit 2, stops
@@ -69,7 +69,7 @@ struct Args {
     long long P;
     long long off_b[kLayers];
     long long off_w5, off_b5;
-    const float* wscale_half;  // FP8: [members][3][256] halves of the per-row scales of W2..W4
+    const float* wscale_half;  // FP8: [members][3][256] halves of the scales of W2..W4 (one per matrix, repeated per row)
     float* pred;            // [members][pred_stride]
     long long pred_stride;  // member stride of pred (n for inference)
     // training (BF16 only): per layer gelu'(z) of the pre-activations (FP16) and the
@@ -393,7 +393,9 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                     if (!(ok = wait_bar(&acc_full[s], (uint32_t)((4 * k + l) & 1), g.status, abort_v))) break;
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     const float* bias = prm + g.off_b[l];
-                    const float* scl = (FP8 && l > 0) ? g.wscale_half + ((long long)mem * 3 + (l - 1)) * kWid : nullptr;
+                    // E4M3 layers: the accumulator times half the matrix's weight scale (one value per
+                    // member and layer, so the epilogue keeps it in a register)
+                    const float sv = (FP8 && l > 0) ? __ldg(g.wscale_half + ((long long)mem * 3 + (l - 1)) * kWid) : 0.0f;
                     const float* w5 = prm + g.off_w5;
                     // Layers 2-4 read 2 h (see the header), so their accumulator is halved here.
                     const float acc_mul = l > 0 ? 0.5f : 1.0f;
@@ -402,9 +404,8 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                     for (int n0 = c_beg; n0 < c_end; n0 += 16) {
                         // the block's parameters are requested before the accumulator wait so that
                         // their latency overlaps it
-                        float bb[16], ss[16], ww[16];
+                        float bb[16], ww[16];
                         ld16(bias + n0, bb);
-                        if (f8) ld16(scl + n0, ss);
                         if (head) ld16(w5 + n0, ww);
                         float v[16];
                         tmem_ld16(taddr + (uint32_t)n0, v);
@@ -434,8 +435,7 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                         } else {
 #pragma unroll
                             for (int i = 0; i < 16; i += 2) {
-                                const float2 z = fma2(make_float2(v[i], v[i + 1]),
-                                                      f8 ? make_float2(ss[i], ss[i + 1]) : f2(acc_mul),
+                                const float2 z = fma2(make_float2(v[i], v[i + 1]), f2(f8 ? sv : acc_mul),
                                                       make_float2(bb[i], bb[i + 1]));
                                 const float2 uu =
                                     mul2(z, fma2(f2(mlp::kGeluK * mlp::kGeluC), mul2(z, z), f2(mlp::kGeluK)));

@@ -113,8 +113,8 @@ def test_fp8_codes_match_oracle(dev):
         scales = s.get(s.GET_FP8_SCALES).reshape(2, 3, 256)
         for m, p in enumerate(L.unpack(master.ravel(), 2)):
             for l in range(3):
-                q, sc = S.quantize_rows(p[f"W{l + 2}"])
-                assert np.array_equal(scales[m, l], sc), (step, m, l)
+                q, sc = S.quantize_matrix(p[f"W{l + 2}"])
+                assert np.array_equal(scales[m, l], np.full(256, sc, np.float32)), (step, m, l)
                 assert np.array_equal(codes[m, l], q), (step, m, l)
         X = to_dev(feats(256, 3), dev)
         t = torch.randn(256, device=dev)
