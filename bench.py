@@ -843,7 +843,7 @@ def run_surfwd(args):
             "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": f"surfwd: {n} rows x 5 members, 128 -> 256 x 4 -> 1, fused BF16 kernel"},
+            "config": {"workload": f"surfwd: {n} rows x 5 members, 64 -> 256 x 4 -> 1, fused BF16 kernel"},
             "roofline": {"bound": "tensor", "achieved": head["tflops"], "peak": bf16_peak, "unit": "TFLOP/s",
                          "frac": head["frac"], "traffic": None, "peak_source": kind},
             "paths": out}
@@ -859,7 +859,7 @@ def train_step_bytes(rows, members):
     from workloads import mlp as L
 
     act = rows * members * L.WID  # elements of one layer's activations
-    x = rows * 128 * 2
+    x = rows * L.IN * 2
     fwd = x + 4 * act * 2 + 4 * act * 2
     head = act * 2 + act * 2 + act * 2
     bwd = act * 2 + 3 * act * 2 + 3 * act * 2
@@ -870,7 +870,7 @@ def train_step_bytes(rows, members):
 
 def run_surtrain(args):
     """Surrogate training throughput: 5 members, 8,192-row batches of 65,536 synthetic rows
-    (48 standard-normal features zero-padded to 128, standard-normal labels), one step =
+    (48 standard-normal features zero-padded to 64, standard-normal labels), one step =
     forward, MSE loss, backward and Adam for every member (tcgen05 path), CUDA events per
     step; against the HBM roofline of the step's algorithmic bytes (the step moves far more
     bytes than its 0.2 TFLOP needs tensor time for)."""
@@ -889,7 +889,7 @@ def run_surtrain(args):
     sur.set_params(L.init_params(members))
     g = torch.Generator(device=dev)
     g.manual_seed(13)
-    X = torch.zeros(n, 128, device=dev)
+    X = torch.zeros(n, L.IN, device=dev)
     X[:, :L.FEATURES] = torch.randn(n, L.FEATURES, generator=g, device=dev)
     X = X.to(torch.bfloat16)
     y = torch.randn(n, generator=g, device=dev)
@@ -919,7 +919,7 @@ def run_surtrain(args):
             "unit": "samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": f"surtrain: {n} rows in {batch}-row steps x {members} members, "
-                                   "128 -> 256 x 4 -> 1, tcgen05 forward and backward, Adam"},
+                                   "64 -> 256 x 4 -> 1, tcgen05 forward and backward, Adam"},
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                          "traffic": None, "algorithmic_bytes_per_step": bytes_step, "peak_source": kind},
             "tflops": tflops, "frac_bf16_peak": tflops / peaks.get("bf16_tflops", 1900.0)}

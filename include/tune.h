@@ -229,21 +229,23 @@ int tune_topk(const float* scores, const int64_t* seg_offsets, int64_t n_seg, in
 
 /* ---- learned surrogate (Section VII: machine learning for the static models) ----
  *
- * An ensemble of MLPs predicting ln(runtime in microseconds) of a tuning
- * point from 48 static features (zero-padded to 128 inputs): 128 -> 256 ->
- * 256 -> 256 -> 256 -> 1 with GELU (tanh form), BF16 weights and activations, FP32
+ * An ensemble of MLPs predicting the logarithm of a tuning point's runtime (in
+ * the labels' unit) from 48 static features (zero-padded to TUNE_SURROGATE_INPUTS
+ * = 64 inputs, one 128-byte BF16 row): 64 -> 256 -> 256 -> 256 -> 256 -> 1 with
+ * GELU (tanh form), BF16 weights and activations, FP32
  * accumulation, FP32 master weights, Adam, MSE loss. All members are trained
  * together on the same batches by the library's BF16 tensor-core kernels.
  * Unlike the tune_* calls, a surrogate handle owns device memory (weights,
  * optimiser state, activations for one batch), allocated by
  * surrogate_create and released by surrogate_free. Feature arrays are BF16
- * (uint16_t bit patterns), [n, 128], row-major, device.
+ * (uint16_t bit patterns), [n, 64], row-major, device.
  *
- * Parameter layout per member (floats; surrogate_param_count() per member,
- * members back to back): W1 [256 x 128] at 0, b1 [256] at 32768, W2 at 33024,
- * b2 at 98560, W3 at 98816, b3 at 164352, W4 at 164608, b4 at 230144,
- * w5 [256] at 230400, b5 at 230656; W[o][i] row-major (output-major).
+ * Parameter layout per member (floats; surrogate_param_count() = 214336 per
+ * member, members back to back): W1 [256 x 64] at 0, b1 [256] at 16384, W2 at
+ * 16640, b2 at 82176, W3 at 82432, b3 at 147968, W4 at 148224, b4 at 213760,
+ * w5 [256] at 214016, b5 at 214272; W[o][i] row-major (output-major).
  */
+#define TUNE_SURROGATE_INPUTS 64
 typedef struct tune_surrogate tune_surrogate;
 typedef struct tune_surrogate_cfg {
     int32_t members; /* ensemble size, 1..16 */
@@ -263,7 +265,7 @@ int surrogate_set_params(tune_surrogate* h, const float* host, int64_t n);
  * x 256 x 256), 7 the scales of those codes (members x 3 x 256: one per matrix, repeated for each
  * of its rows). Synchronous. */
 int surrogate_get(tune_surrogate* h, int what, float* host, int64_t n);
-/* pred (device, [members, n]) = each member's output for feats (device bf16 [n, 128]).
+/* pred (device, [members, n]) = each member's output for feats (device bf16 [n, 64]).
  * By default one persistent launch runs every member over 128-row tiles with the
  * activations kept on chip (option 1). feats must be 16-byte aligned. */
 int surrogate_forward(tune_surrogate* h, const uint16_t* feats, int64_t n, float* pred, tune_stream_t stream);
@@ -295,12 +297,12 @@ int surrogate_set_option(tune_surrogate* h, int option, int value);
 int surrogate_status(tune_surrogate* h);
 
 /*
- * tune_features — the surrogate's 48 input features (zero-padded to 128 BF16
+ * tune_features — the surrogate's 48 input features (zero-padded to 64 BF16
  * columns) of listed tuning points: sample i is point sample_point[i]
  * (canonical index) of descriptor sample_kernel[i]. Features are fixed
  * scalings of the descriptor, the launch parameters and the occupancy and
  * cost internals of Eqs. 3-6 (see csrc/features.cuh for the list). feats:
- * device BF16 [n, 128]. Invalid samples set TUNE_EINVAL in the status word.
+ * device BF16 [n, 64]. Invalid samples set TUNE_EINVAL in the status word.
  */
 int tune_features(const tune_arch* arch, const tune_axes* axes, const tune_kernel_desc* descs,
                   const int64_t* sample_kernel, const int32_t* sample_point, int64_t n, uint16_t* feats,

@@ -81,7 +81,7 @@ def _r(x, on):
 
 
 def forward(p, X, bf=True):
-    """p: one member's parameter dict; X: [n, 128]. Returns (y, cache)."""
+    """p: one member's parameter dict; X: [n, 64]. Returns (y, cache)."""
     h = _r(X, bf)
     cache = {"h0": h}
     for l in range(1, 5):

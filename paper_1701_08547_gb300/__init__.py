@@ -145,13 +145,13 @@ def tune_autotune(arch, axes, descs, k, reps=3, topk_idx=None, topk_cost=None, w
 
 def tune_features(arch, axes, descs, sample_kernel, sample_point, feats=None, workspace_buf=None,
                   stream=None):
-    """Surrogate input features (device bfloat16 [n, 128]) of listed (kernel, point) samples."""
+    """Surrogate input features (device bfloat16 [n, 64]) of listed (kernel, point) samples."""
     torch = _torch()
     L = native.load()
     n = sample_kernel.numel()
     dev = descs.device
     if feats is None:
-        feats = torch.empty((n, 128), dtype=torch.bfloat16, device=dev)
+        feats = torch.empty((n, native.TUNE_SURROGATE_INPUTS), dtype=torch.bfloat16, device=dev)
     if workspace_buf is None:
         workspace_buf = workspace(native.TUNE_CALL_EVAL, 0, 1, dev)
     a = native.make_arch(arch)

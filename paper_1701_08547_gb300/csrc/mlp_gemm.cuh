@@ -6,8 +6,9 @@
 //   A: A_KM = false -> A[m * lda + k] (K contiguous); true -> A[k * lda + m] (M contiguous)
 //   B: B_KN = false -> B[n * ldb + k] (K contiguous); true -> B[k * ldb + n] (N contiguous)
 // Tiles are copied to shared memory in their global orientation; ldmatrix.trans
-// produces the fragments of the transposed orientations. M, N multiples of 128,
-// K a multiple of 32, leading dimensions multiples of 8 elements.
+// produces the fragments of the transposed orientations. M, N multiples of 64 (a
+// tile's rows past M or N are filled with zeros and not stored), K a multiple of 32,
+// leading dimensions multiples of 8 elements.
 #pragma once
 
 #include "gelu.cuh"
@@ -94,9 +95,10 @@ struct Tile<true> {  // [32 k][128 (m or n)]
     static constexpr int ELEMS = GBK * ROW;
 };
 
-// Copy one 128 x 32 operand tile (global orientation kept) with 16-byte cp.async.
+// Copy one 128 x 32 operand tile (global orientation kept) with 16-byte cp.async; rows
+// (m or n) at or past lim are zero-filled instead of read.
 template <bool KM>
-__device__ __forceinline__ void load_tile(__nv_bfloat16* s, const __nv_bfloat16* g, int ld, int row0, int k0)
+__device__ __forceinline__ void load_tile(__nv_bfloat16* s, const __nv_bfloat16* g, int ld, int row0, int k0, int lim)
 {
     const int t = threadIdx.x;
     if (!KM) {  // 128 rows x 32 k: 4 chunks of 8 per row -> 512 chunks
@@ -104,14 +106,22 @@ __device__ __forceinline__ void load_tile(__nv_bfloat16* s, const __nv_bfloat16*
         for (int i = 0; i < 2; ++i) {
             const int c = t + i * kGemmThreads;
             const int r = c >> 2, q = c & 3;
-            cp_async16(s + r * Tile<false>::ROW + q * 8, g + (long long)(row0 + r) * ld + k0 + q * 8);
+            __nv_bfloat16* d = s + r * Tile<false>::ROW + q * 8;
+            if (row0 + r < lim)
+                cp_async16(d, g + (long long)(row0 + r) * ld + k0 + q * 8);
+            else
+                *reinterpret_cast<uint4*>(d) = make_uint4(0u, 0u, 0u, 0u);
         }
     } else {  // 32 k x 128: 16 chunks per k row -> 512 chunks
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int c = t + i * kGemmThreads;
             const int r = c >> 4, q = c & 15;
-            cp_async16(s + r * Tile<true>::ROW + q * 8, g + (long long)(k0 + r) * ld + row0 + q * 8);
+            __nv_bfloat16* d = s + r * Tile<true>::ROW + q * 8;
+            if (row0 + q * 8 < lim)
+                cp_async16(d, g + (long long)(k0 + r) * ld + row0 + q * 8);
+            else
+                *reinterpret_cast<uint4*>(d) = make_uint4(0u, 0u, 0u, 0u);
         }
     }
 }
@@ -171,14 +181,14 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(const __grid_co
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
 
     const int n_k = k_len / GBK;
-    load_tile<A_KM>(sA[0], A, g.lda, m_blk, k_beg);
-    load_tile<B_KN>(sB[0], B, g.ldb, n_blk, k_beg);
+    load_tile<A_KM>(sA[0], A, g.lda, m_blk, k_beg, g.M);
+    load_tile<B_KN>(sB[0], B, g.ldb, n_blk, k_beg, g.N);
     cp_async_commit();
     for (int kt = 0; kt < n_k; ++kt) {
         const int cur = kt & 1;
         if (kt + 1 < n_k) {
-            load_tile<A_KM>(sA[cur ^ 1], A, g.lda, m_blk, k_beg + (kt + 1) * GBK);
-            load_tile<B_KN>(sB[cur ^ 1], B, g.ldb, n_blk, k_beg + (kt + 1) * GBK);
+            load_tile<A_KM>(sA[cur ^ 1], A, g.lda, m_blk, k_beg + (kt + 1) * GBK, g.M);
+            load_tile<B_KN>(sB[cur ^ 1], B, g.ldb, n_blk, k_beg + (kt + 1) * GBK, g.N);
         }
         cp_async_commit();
         cp_async_wait<1>();
@@ -209,6 +219,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(const __grid_co
             for (int h = 0; h < 2; ++h) {
                 const int m = m_blk + wm + i * 16 + gr + h * 8;
                 const int n = n_blk + wn + j * 8 + gc;
+                if (m >= g.M || n >= g.N) continue;  // zero-filled rows of a partial tile
                 const float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
                 const long long off = (long long)m * g.ldc + n;
                 if (EPI == EPI_BIAS_GELU) {

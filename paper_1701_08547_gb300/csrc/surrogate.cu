@@ -1,5 +1,5 @@
 // Learned surrogate of the static cost: an ensemble of MLPs
-// (128 inputs = 48 features + zero padding -> 256 -> 256 -> 256 -> 256 -> 1, GELU in tanh form),
+// (64 inputs = 48 features + zero padding -> 256 -> 256 -> 256 -> 256 -> 1, GELU in tanh form),
 // BF16 weights and activations, FP32 accumulation, FP32 master weights, Adam,
 // trained by this file's kernels (forward, backward, optimiser) on the GPU.
 // Members are batched through the grouped GEMM (blockIdx.z = member).
@@ -26,22 +26,25 @@ using mlp::GemmArgs;
 
 namespace {
 
-constexpr int IN = 128;     // input width (48 features + zeros)
+constexpr int IN = TUNE_SURROGATE_INPUTS;  // input width (48 features + zeros: one 128-byte BF16 row)
 constexpr int WID = 256;    // hidden width
 constexpr int NL = 4;       // hidden layers
 constexpr int KSPLIT = 8;   // split-K for weight gradients over the batch
 
-// Per-member parameter layout (floats): W1 [256 x 128], b1, W2..W4 [256 x 256], b2..b4, w5 [256], b5.
+// Per-member parameter layout (floats): W1 [256 x 64], b1, W2..W4 [256 x 256], b2..b4, w5 [256], b5.
 __host__ __device__ constexpr long long fan_in(int l) { return l == 0 ? IN : WID; }
-__host__ __device__ constexpr long long OFF_W(int l) { return l == 0 ? 0 : 33024 + (l - 1) * 65792LL; }
+__host__ __device__ constexpr long long OFF_W(int l) { return l == 0 ? 0 : WID * IN + WID + (l - 1) * 65792LL; }
 __host__ __device__ constexpr long long OFF_B(int l) { return OFF_W(l) + WID * fan_in(l); }
-constexpr long long OFF_W5 = 230400, OFF_B5 = 230656;
-constexpr long long P_REAL = 230657;
-constexpr long long P = 230720;  // padded per-member stride
+constexpr long long OFF_W5 = 214016, OFF_B5 = 214272;
+constexpr long long P_REAL = 214273;
+constexpr long long P = 214336;  // padded per-member stride (a multiple of 64 floats)
 // bf16 copies of W1..W4 per member
-__host__ __device__ constexpr long long BOFF_W(int l) { return l == 0 ? 0 : 32768 + (l - 1) * 65536LL; }
-constexpr long long PB = 229376;
-static_assert(OFF_B(3) == 230144 && OFF_W5 == OFF_B(3) + WID && BOFF_W(3) + 65536 == PB, "layout");
+__host__ __device__ constexpr long long BOFF_W(int l) { return l == 0 ? 0 : WID * IN + (l - 1) * 65536LL; }
+constexpr long long PB = 212992;
+static_assert(IN == tcm::kIn, "the fused kernels' input width");
+static_assert(OFF_B(3) == 213760 && OFF_W5 == OFF_B(3) + WID && OFF_B5 == OFF_W5 + WID && P_REAL == OFF_B5 + 1 &&
+                  P >= P_REAL && P % 64 == 0 && BOFF_W(3) + 65536 == PB,
+              "layout");
 
 }  // namespace
 
@@ -66,7 +69,7 @@ struct tune_surrogate {
     int bwd_mode = 1;                   // backward: 0 mma.sync GEMMs, 1 fused input gradients + tcgen05 dW
     int wgrad_splits = 0;               // tcgen05 weight gradients: batch splits per member (0: SMs / 2 members)
     uint8_t* w8 = nullptr;              // E4M3 codes of W2..W4 [members][3][256][256]
-    float* wscale = nullptr;            // their per-row scales [members][3][256]
+    float* wscale = nullptr;            // their scales [members][3][256] (one per matrix, repeated per row)
     float* wscale_half = nullptr;       // the scales halved (the fused epilogue's multipliers)
     bool fp8_stale = true;              // master weights changed since the last quantisation
 };
@@ -393,12 +396,14 @@ __global__ void gather_batch(const __nv_bfloat16* __restrict__ feats, const floa
     reinterpret_cast<__nv_bfloat162*>(xin + (long long)r * IN)[c] = val;
 }
 
-// The same gather with 16-byte accesses (feats 16-byte aligned): 16 threads per 256-byte row,
-// 16 rows per block of 256 threads.
+// The same gather with 16-byte accesses (feats 16-byte aligned): kRowU4 threads per row of
+// IN BF16 values, 256 / kRowU4 rows per block of 256 threads.
+constexpr int kRowU4 = IN * 2 / 16;
+constexpr int kGatherRows = 256 / kRowU4;
 __global__ void gather_batch16(const __nv_bfloat16* __restrict__ feats, const float* __restrict__ labels,
                                const int32_t* __restrict__ order, int n, int batch, __nv_bfloat16* xin, float* lbl)
 {
-    const int r = blockIdx.x * 16 + (threadIdx.x >> 4), c = threadIdx.x & 15;
+    const int r = blockIdx.x * kGatherRows + threadIdx.x / kRowU4, c = threadIdx.x % kRowU4;
     if (r >= batch) return;
     uint4 val = make_uint4(0u, 0u, 0u, 0u);
     float lab = 0.0f;
@@ -414,7 +419,7 @@ __global__ void gather_batch16(const __nv_bfloat16* __restrict__ feats, const fl
 template <bool A_KM, bool B_KN, int EPI>
 int gemm(const GemmArgs& g, int batches, cudaStream_t s)
 {
-    dim3 grid(g.N / mlp::GBN, g.M / mlp::GBM, batches * g.k_split);
+    dim3 grid((g.N + mlp::GBN - 1) / mlp::GBN, (g.M + mlp::GBM - 1) / mlp::GBM, batches * g.k_split);
     mlp::gemm_bf16_kernel<A_KM, B_KN, EPI><<<grid, mlp::kGemmThreads, 0, s>>>(g);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: gemm launch");
     return TUNE_OK;
@@ -875,7 +880,8 @@ int load_batch(tune_surrogate* h, const __nv_bfloat16* feats, const float* label
                cudaStream_t s)
 {
     if ((reinterpret_cast<uintptr_t>(feats) & 15) == 0)
-        gather_batch16<<<(h->batch + 15) / 16, 256, 0, s>>>(feats, labels, order, n, h->batch, h->xin, h->lbl);
+        gather_batch16<<<(h->batch + kGatherRows - 1) / kGatherRows, 256, 0, s>>>(feats, labels, order, n, h->batch,
+                                                                                 h->xin, h->lbl);
     else
         gather_batch<<<h->batch, IN / 2, 0, s>>>(feats, labels, order, n, h->batch, h->xin, h->lbl);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: gather launch");

@@ -13,7 +13,7 @@ using namespace tune_dev;
 
 namespace {
 
-constexpr int IN = 128;
+constexpr int IN = TUNE_SURROGATE_INPUTS;  // feature row width (48 features + zeros)
 constexpr int64_t kChunkPoints = 1 << 20;  // points per inference chunk
 
 __device__ __forceinline__ void load_desc(const int4* descs, int64_t kid, Desc& kd)

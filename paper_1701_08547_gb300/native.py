@@ -18,6 +18,7 @@ TUNE_EMIT_POINTS = 0x1
 TUNE_FAULT_COMPILE, TUNE_FAULT_SLOW_REP, TUNE_FAULT_WAIT = 1, 2, 3
 TUNE_SCHED_WARP, TUNE_SCHED_THREAD = 0x10, 0x20
 TUNE_HOST_DIRECT = 0x40
+TUNE_SURROGATE_INPUTS = 64  # surrogate feature row width (48 features + zero padding)
 
 
 def TUNE_SCHED_CHUNK(c):

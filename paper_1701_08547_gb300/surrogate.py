@@ -118,7 +118,7 @@ class Surrogate:
         return out
 
     def forward(self, feats, pred=None, stream=None):
-        """feats: device bfloat16 [n, 128]; returns device float32 [members, n]."""
+        """feats: device bfloat16 [n, 64]; returns device float32 [members, n]."""
         import torch
 
         n = feats.shape[0]

@@ -73,6 +73,22 @@ def test_record_layouts_match_header(tmp_path):
     assert vals[7] == C.sizeof(native.TuneAxes) and vals[8] == native.TuneAxes.c.offset
 
 
+def test_surrogate_layout_matches_header(lib):
+    """The surrogate's input width and per-member parameter count agree between the header,
+    the library, the binding and the parameter format the tests and the oracle use."""
+    from paper_1701_08547_gb300 import native
+    from workloads import mlp as L
+
+    text = open(os.path.join(ROOT, "include", "tune.h")).read()
+    width = int(re.search(r"#define TUNE_SURROGATE_INPUTS (\d+)", text).group(1))
+    assert width == native.TUNE_SURROGATE_INPUTS == L.IN == 64
+    assert lib.surrogate_param_count() == L.P
+    text = re.sub(r"\n\s*\*\s*", " ", text)  # comment lines joined
+    for name, val in (("W1", 0), ("b1", L.OFF_B[0]), ("W2", L.OFF_W[1]), ("b4", L.OFF_B[3]),
+                      ("w5", L.OFF_W5), ("b5", L.OFF_B5)):
+        assert re.search(rf"{name} (\[[^\]]*\] )?at {val}\b", text), name
+
+
 def _call_eval(lib, arch_row, axes, k, ws=1 << 12, flags=0, descs=16):
     from paper_1701_08547_gb300 import native
 

@@ -152,7 +152,7 @@ def test_fallback_decision_at_configured_threshold(dev, oracle):
     off = gen.point_offsets(d)
     members, k, thresh, band = 3, 5, 0.1, 0.015
     flat = L.init_params(members, [61, 62, 63]).reshape(members, L.P)
-    flat[:, L.OFF_W5:L.OFF_W5 + L.WID] *= 2.5  # members disagree by about the threshold
+    flat[:, L.OFF_W5:L.OFF_W5 + L.WID] *= 4.0  # members disagree by about the threshold
     flat = flat.ravel()
     s = Surrogate(members=members, batch=1024)
     s.set_params(flat)

@@ -14,8 +14,9 @@ rate lies at or below the upper end of the ensemble's 95 % Wilson interval. With
 the fallback the ensemble's first pick must be closer to the measured best (median
 slowdown) than the analytic model's.
 
-Sanity case: trained on the analytic model's own costs as labels, the ensemble
-must reproduce the analytic choice: on held-out kernels, one of its top 5 points
+Sanity case: trained on the analytic model's own costs as labels (128 K sampled
+points, 120 epochs: at 60 the fit depended on the initial draws, 0.93-0.965 within
+1 %), the ensemble must reproduce the analytic choice: on held-out kernels, one of its top 5 points
 is within 1 % of the least analytic cost for at least 95 % of them. (The held-out
 spaces hold a median of 4 points within 1 % of the best and 12 within 5 %, and
 exact ties are common; a regression fit to a few % cannot order points that
@@ -68,7 +69,7 @@ def test_surrogate_trained_on_analytic_labels_reproduces_the_analytic_choice(dev
 
     a, ax = archs.arch("sm_103"), gen.axes()
     data = SD.analytic_set(a, ax, gen.descriptors(2000, 44, "dense"), 64, 44, dev)
-    sur, trace = SD.train(data, members=5, epochs=60, dev=dev)
+    sur, trace = SD.train(data, members=5, epochs=120, dev=dev)
     held = SD.eval_spaces(gen.descriptors(200, 45, "dense"))
     off = gen.point_offsets(held)
     dd = T.descs_to_device(held, dev)

@@ -2,18 +2,18 @@
 
 Pure data: the flat per-member layout (the same one include/tune.h documents)
 and Gaussian initial weights drawn with numpy's PCG64 from a per-member seed
-(weights N(0, 1/fan_in), biases 0; the zero-padded inputs 48..127 get zero
+(weights N(0, 1/fan_in), biases 0; the zero-padded inputs 48..63 get zero
 weights). Both the CUDA path and the oracle take these arrays as inputs.
 """
 
 import numpy as np
 
-IN, WID, FEATURES = 128, 256, 48
+IN, WID, FEATURES = 64, 256, 48  # 48 features zero-padded to 64 inputs (one 128-byte row)
 LAYERS = [(IN, WID), (WID, WID), (WID, WID), (WID, WID)]
-OFF_W = [0, 33024, 98816, 164608]
-OFF_B = [32768, 98560, 164352, 230144]
-OFF_W5, OFF_B5 = 230400, 230656
-P = 230720  # floats per member (padded)
+OFF_W = [0, 16640, 82432, 148224]
+OFF_B = [16384, 82176, 147968, 213760]
+OFF_W5, OFF_B5 = 214016, 214272
+P = 214336  # floats per member (padded)
 
 
 def init_params(members, seeds=None):
