@@ -231,6 +231,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 
 // grid: min(SMs, units) persistent CTAs; CTA b runs units b, b + gridDim.x, ...;
 // its j-th unit goes to chain j % 2. Unit u = (tile u / members, member u % members).
+// 96 registers per thread: the 18 warps spread over the SM's four sub-partitions of 16,384
+// registers, five on the fullest (5 x 32 x 96 = 15,360; at 104 the launch does not fit).
 template <bool FP8, bool TRAIN = false>
 __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtensorMap tx,
                                                                 const __grid_constant__ CUtensorMap tw1,
@@ -412,25 +414,26 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                         tmem_ld16(taddr + (uint32_t)n0, v);
                         const long long arow = (long long)mem * g.act_stride + (long long)(tile * kRows + r) * kWid + n0;
                         // z = acc * s + b, then 2 gelu(z) = z (1 + tanh u), u = z (K C z^2 + K), in FP32:
-                        // one multi-function-unit tanh per element. Inference works on column pairs
-                        // (packed FP32x2: the scalar operations' results, half the instructions);
-                        // training, at the register limit with gelu'(z) (from the same tanh, kept in
-                        // FP16 for the backward pass) also live, is faster in scalar form.
+                        // one multi-function-unit tanh per element, the rest on column pairs (packed
+                        // FP32x2 operations, half the instructions of the scalar form).
                         uint32_t gd[8];
                         if (TRAIN) {
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) v[i] = fmaf(v[i], acc_mul, bb[i]);
-#pragma unroll
                             for (int i = 0; i < 16; i += 2) {
-                                float dd[2];
-#pragma unroll
-                                for (int k2 = 0; k2 < 2; ++k2) {
-                                    const float z = v[i + k2], z2 = z * z;
-                                    const float t = mlp::tanh_hw(mlp::gelu_u(z, z2));
-                                    dd[k2] = mlp::gelu_grad_t(z, z2, t);
-                                    v[i + k2] = fmaf(z, t, z);
-                                }
-                                const __half2 d2 = __floats2half2_rn(dd[0], dd[1]);
+                                const float2 z = fma2(make_float2(v[i], v[i + 1]), f2(acc_mul), make_float2(bb[i], bb[i + 1]));
+                                const float2 zz = mul2(z, z);
+                                const float2 u = mul2(z, fma2(f2(mlp::kGeluK * mlp::kGeluC), zz, f2(mlp::kGeluK)));
+                                const float2 t = make_float2(mlp::tanh_hw(u.x), mlp::tanh_hw(u.y));
+                                // gelu'(z) = (1 + t) / 2 + z / 2 (1 - t^2) K (1 + 3 C z^2), kept in FP16 for
+                                // the backward pass; with 1 - t^2 = (1 - t)(1 + t) and a = (1 + t) / 2 it is
+                                // a + (z K (1 + 3 C z^2)) (1 - t) a, six packed operations per pair
+                                const float2 a = fma2(t, f2(0.5f), f2(0.5f));
+                                const float2 w = mul2(z, fma2(f2(3.0f * mlp::kGeluK * mlp::kGeluC), zz, f2(mlp::kGeluK)));
+                                const float2 d = fma2(mul2(w, fma2(t, f2(-1.0f), f2(1.0f))), a, a);
+                                const float2 h2 = fma2(z, t, z);
+                                v[i] = h2.x;
+                                v[i + 1] = h2.y;
+                                const __half2 d2 = __floats2half2_rn(d.x, d.y);
                                 gd[i / 2] = *reinterpret_cast<const uint32_t*>(&d2);
                             }
                         } else {
@@ -459,7 +462,10 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                             // training: h = bf16(gelu(z)) = bf16(2 gelu(z)) / 2 exactly
                             uint32_t w[8];
 #pragma unroll
-                            for (int t = 0; t < 8; ++t) w[t] = pack_bf16(0.5f * v[2 * t], 0.5f * v[2 * t + 1]);
+                            for (int t = 0; t < 8; ++t) {
+                                const float2 hh = mul2(make_float2(v[2 * t], v[2 * t + 1]), f2(0.5f));
+                                w[t] = pack_bf16(hh.x, hh.y);
+                            }
                             st_global_v8(g.h_out[l] + arow, w);
                         }
                         if (head) {
