@@ -288,9 +288,10 @@ int surrogate_members(const tune_surrogate* h);
  * / 448; codes nearest-even, saturating), activations as codes of 2 h, FP32 accumulation;
  * 2 = training's backward pass: 0 one mma.sync GEMM per input and weight gradient;
  * 1 (default, with option 0 on) the chain dZ4 -> dZ3 -> dZ2 -> dZ1 (products with W4,
- * W3, W2) in one fused tcgen05 launch and the weight gradients on tcgen05 (both
- * operands MN-major), split over the batch and reduced in split order;
- * 3 = batch splits per member of those weight gradients (0, the default: SMs / (2 members)). */
+ * W3, W2) in one fused tcgen05 launch and the weight and bias gradients of every layer on
+ * tcgen05 in one launch (both operands MN-major, one CTA per 128 x 64 gradient tile and
+ * member accumulating the whole batch; the bias sums by a second MMA with an all-ones
+ * operand). */
 int surrogate_set_option(tune_surrogate* h, int option, int value);
 /* Synchronous: TUNE_ETIMEOUT if a bounded wait inside a surrogate kernel gave up since the
  * last check; the check clears the handle's status word. */

@@ -67,7 +67,6 @@ struct tune_surrogate {
     int use_tc = 1;                     // forward layers on tcgen05 (1) or mma.sync (0)
     int fwd_mode = 1;                   // surrogate_forward: 0 layer by layer, 1 fused BF16, 2 fused FP8
     int bwd_mode = 1;                   // backward: 0 mma.sync GEMMs, 1 fused input gradients + tcgen05 dW
-    int wgrad_splits = 0;               // tcgen05 weight gradients: batch splits per member (0: SMs / 2 members)
     uint8_t* w8 = nullptr;              // E4M3 codes of W2..W4 [members][3][256][256]
     float* wscale = nullptr;            // their scales [members][3][256] (one per matrix, repeated per row)
     float* wscale_half = nullptr;       // the scales halved (the fused epilogue's multipliers)
@@ -678,49 +677,46 @@ int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaS
     return TUNE_OK;
 }
 
-// Weight and bias gradients of layer l on tcgen05 (tc_wgrad.cuh): one CTA per (batch
-// split, output half, member) with both operands MN-major, then the split reduction into grad.
-int wgrad_tc(tune_surrogate* h, int l, int n_pad, const __nv_bfloat16* dz, cudaStream_t s)
+// Weight and bias gradients of every layer on tcgen05 in one launch (tc_wgrad.cuh): one CTA
+// per 128 x 64 gradient tile and member, both operands MN-major, the whole batch in one TMEM
+// accumulator. dz[l]: dZ of layer l ([members][batch][256]).
+int wgrad_tc(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaStream_t s)
 {
-    const int kin = (int)fan_in(l), M = h->members;
-    const int chunks = n_pad / tcw::kChunkRows;
-    // default: one CTA per SM, two (the output halves) per split
-    int splits = h->wgrad_splits > 0 ? h->wgrad_splits : tune::device_sm_count() / (2 * M);
-    // the weight partials [M][splits][WID][kin] and the bias partials [M][splits][4][WID]
-    // share the partial buffer
-    const long long cap = (long long)h->part_slices * WID * WID / ((long long)M * WID * (kin + tcw::kBiasRows));
-    splits = std::max(1, (int)std::min<long long>(std::min(splits, chunks), cap));
-    CUtensorMap ta, tb;
+    const int M = h->members;
+    tcw::Maps maps;
+    tcw::Args g;
+    memset(&g, 0, sizeof(g));
     const auto u64 = CU_TENSOR_MAP_DATA_TYPE_UINT64;
     const cuuint32_t box[3] = {16, tcw::kChunkRows, 1};
     const cuuint64_t da[3] = {WID * 2 / 8, (cuuint64_t)n_pad, (cuuint64_t)M};
     const cuuint64_t sa[2] = {WID * 2, (cuuint64_t)h->batch * WID * 2};
-    int rc = make_map_nd(&ta, u64, 3, dz, da, sa, box);
-    if (rc) return rc;
-    if (l == 0) {
-        const cuuint64_t db[3] = {IN * 2 / 8, (cuuint64_t)n_pad, 1};
-        const cuuint64_t sb[2] = {IN * 2, (cuuint64_t)n_pad * IN * 2};
-        rc = make_map_nd(&tb, u64, 3, h->xin, db, sb, box);
-    } else {
-        rc = make_map_nd(&tb, u64, 3, h->H[l - 1], da, sa, box);
+    g.n_items = NL;
+    for (int j = 0; j < NL; ++j) {
+        const int l = NL - 1 - j;  // layers 4, 3, 2, 1
+        int rc = make_map_nd(&maps.ta[j], u64, 3, dz[l], da, sa, box);
+        if (rc) return rc;
+        if (l == 0) {
+            const cuuint64_t db[3] = {IN * 2 / 8, (cuuint64_t)n_pad, 1};
+            const cuuint64_t sb[2] = {IN * 2, (cuuint64_t)n_pad * IN * 2};
+            rc = make_map_nd(&maps.tb[j], u64, 3, h->xin, db, sb, box);
+        } else {
+            rc = make_map_nd(&maps.tb[j], u64, 3, h->H[l - 1], da, sa, box);
+        }
+        if (rc) return rc;
+        g.kin[j] = (int)fan_in(l);
+        g.b_batched[j] = l != 0;
+        g.grad_w[j] = OFF_W(l);
+        g.grad_b[j] = OFF_B(l);
     }
-    if (rc) return rc;
-    tcw::Args g;
-    g.kin = kin;
-    g.chunks = chunks;
-    g.splits = splits;
-    g.part = h->part;
-    g.bpart = h->part + (long long)M * splits * WID * kin;
+    g.grad_stride = P;
+    g.chunks = n_pad / tcw::kChunkRows;
+    g.grad = h->grad;
     g.status = h->status;
     static std::atomic<uint64_t> attr{0};
-    rc = smem_attr(tcw::wgrad_kernel, tcw::kSmem, attr, "surrogate: weight-gradient smem attribute");
+    const int rc = smem_attr(tcw::wgrad_kernel, tcw::kSmem, attr, "surrogate: weight-gradient smem attribute");
     if (rc) return rc;
-    tcw::wgrad_kernel<<<dim3(2 * splits, M), tcw::kThreads, tcw::kSmem, s>>>(ta, tb, g, l != 0);
+    tcw::wgrad_kernel<<<dim3(tcw::tiles_per_member(g), M), tcw::kThreads, tcw::kSmem, s>>>(maps, g);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: weight-gradient launch");
-    split_reduce<<<dim3((WID * kin / 4 + 255) / 256 + 1, M), 256, 0, s>>>(
-        h->part, h->grad, OFF_W(l), kin, splits, (long long)splits * WID * kin, (long long)WID * kin, g.bpart, OFF_B(l),
-        tcw::kBiasRows * splits);
-    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: split reduce launch");
     return TUNE_OK;
 }
 
@@ -820,28 +816,22 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
     slices_reduce<<<dim3((WID + 1 + 31) / 32, h->members), 32 * kRedWarps, 0, s>>>(h->part, h->grad, OFF_W5,
                                                                                   WID + 1, hslices);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: head backward launch");
-    if (fused) {
+    if (fused) {  // input gradients dZ3..dZ1, then every layer's weight and bias gradients
         int rc = fused_backward(h, n_pad, dzl, s);
         if (rc) return rc;
+        return wgrad_tc(h, n_pad, dzl, s);
     }
+    // mma.sync backward: per layer the weight gradient, the bias gradient and the input gradient
     for (int l = NL - 1; l >= 0; --l) {
         const __nv_bfloat16* dz = dzl[l];
         const int kin = (int)fan_in(l);
         // weight gradient: dW[o][i] = sum_r dZ[r][o] * Hprev[r][i]   (split over the batch)
-        if (fused) {
-            const int rc = wgrad_tc(h, l, n_pad, dz, s);
-            if (rc) return rc;
-        } else {
-            const int rc = wgrad_mma(h, l, n_pad, dz, s);
-            if (rc) return rc;
-        }
-        if (!fused) {  // the tcgen05 weight-gradient pass forms the bias gradient too
-            bias_partial<<<dim3(slices, h->members), WID, 0, s>>>(dz, h->part, n_pad, B, slices);
-            slices_reduce<<<dim3(WID / 32, h->members), 32 * kRedWarps, 0, s>>>(h->part, h->grad, OFF_B(l), WID,
-                                                                                slices);
-            TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: reduce launch");
-        }
-        if (l == 0 || fused) continue;
+        int rc = wgrad_mma(h, l, n_pad, dz, s);
+        if (rc) return rc;
+        bias_partial<<<dim3(slices, h->members), WID, 0, s>>>(dz, h->part, n_pad, B, slices);
+        slices_reduce<<<dim3(WID / 32, h->members), 32 * kRedWarps, 0, s>>>(h->part, h->grad, OFF_B(l), WID, slices);
+        TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: reduce launch");
+        if (l == 0) continue;
         // input gradient of layer l, times gelu' of layer l-1: dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1})
         GemmArgs d = gargs();
         d.A = dz;
@@ -858,7 +848,7 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
         d.H = dzl[l - 1];
         d.sH = (long long)B * WID;
         d.ldc = WID;
-        const int rc = gemm<false, true, mlp::EPI_GELU_GRAD>(d, h->members, s);
+        rc = gemm<false, true, mlp::EPI_GELU_GRAD>(d, h->members, s);
         if (rc) return rc;
     }
     return TUNE_OK;
@@ -912,11 +902,6 @@ int surrogate_set_option(tune_surrogate* h, int option, int value)
     if (option == 2) {
         if (value < 0 || value > 1) return tune::fail(TUNE_EINVAL, "surrogate_set_option: backward mode outside 0..1");
         h->bwd_mode = value;
-        return TUNE_OK;
-    }
-    if (option == 3) {
-        if (value < 0 || value > 1024) return tune::fail(TUNE_EINVAL, "surrogate_set_option: splits outside 0..1024");
-        h->wgrad_splits = value;
         return TUNE_OK;
     }
     return tune::fail(TUNE_EINVAL, "surrogate_set_option: unknown option %d", option);

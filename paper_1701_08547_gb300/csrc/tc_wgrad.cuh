@@ -1,63 +1,90 @@
-// Weight and bias gradients of surrogate training on tcgen05:
-//   dW_l[o][i] = sum over batch rows r of dZ_l[r][o] * Hprev[r][i],   db_l[o] = sum over r of dZ_l[r][o]
+// Weight and bias gradients of surrogate training on tcgen05, every layer in one launch:
+//   dW_l[o][i] = sum over batch rows r of dZ_l[r][o] * Hprev_l[r][i],   db_l[o] = sum over r of dZ_l[r][o]
 // (Hprev = the layer's input: the previous layer's activations, or the feature rows).
+//
+// Output-stationary: CTA (t, m) owns one 128 x 64 tile of member m's weight gradients
+// (output rows o in [128 h, 128 h + 128) and input columns [64 c, 64 c + 64) of one layer)
+// and runs the whole batch through one TMEM accumulator, so every gradient element is one
+// MMA accumulation chain over the batch, written once, with no partial sums in memory.
+// Tile t enumerates the layers in the order of Args::kin, each as (o half, column block);
+// a member has 2 (64 / 64 + 3 x 256 / 64) = 26 tiles, all of the same cost.
+//
 // The contraction runs over the batch, the index along which neither operand is
 // contiguous, so both operands are fed to the MMA MN-major: TMA copies boxes of
-// 64 rows x 64 BF16 columns with 128-byte swizzle, which is the MN-major swizzle
-// atom (8 rows of K by 64 elements of M or N, 1 KB) repeated 8 times along K
-// (1 KB apart) and, box by box, along M or N (8 KB apart).
+// 128 rows x 64 BF16 columns with 128-byte swizzle, which is the MN-major swizzle atom
+// (8 rows of K by 64 elements of M or N, 1 KB) repeated 16 times along K (1 KB apart)
+// and, box by box, along M (16 KB apart). A stage holds 128 batch rows: two dZ boxes
+// (the tile's 128 output columns) and one Hprev box (its 64 input columns). The stages
+// are that deep because the MMA issuer's fixed cost per stage (barrier wait, fences,
+// commit: about 0.2 us) outweighed the eight 128 x 64 x 16 products of a 64-row stage.
 //
-// Grid (2 splits, members): CTA (2 s + h, m) sums a contiguous range of 64-row chunks
-// for output rows o in [128 h, 128 h + 128) of member m and writes its FP32 partial
-// [128][kin] into part[m][s] (the two halves of a split fill one [256][kin] slice);
-// split_reduce adds the partials in split order (deterministic). The two halves of a
-// split read the same Hprev rows at about the same time, so the second read is
-// served from L2. The bias gradient comes from the same pass: the epilogue warps, idle
-// until the last MMA, add up each stage's dZ columns from shared memory before the
-// stage is released. Roles: warp 0 issues the TMA copies through a ring of four 48 KB
-// stages, warp 1 issues the MMAs (one 128 x kin x 16 product per 16-row K step), warps
-// 2-9 read the accumulator back (thread = output row, two warps per TMEM lane quarter,
-// one per column half) and store the partial, row-contiguous through shared memory.
+// The bias gradient of the tiles with c = 0 comes from the same MMAs: their B operand is
+// 80 columns wide, the tile's 64 Hprev columns and 16 columns of a constant all-ones
+// block (a second MN atom, which the descriptor's leading byte offset points at), so
+// accumulator columns 64-79 each hold sum over r of dZ[r][o].
+//
+// Roles (192 threads): warp 0 issues the TMA copies through a ring of four 48 KB
+// stages, warp 1 issues the MMAs, warps 2-5 read the accumulator back (thread = output
+// row, one warp per TMEM lane quarter) and store the gradient rows.
 //
 // Every wait is bounded; on timeout the kernel sets status bit 2, stops issuing work,
-// waits (bounded) for the copies and MMAs it issued, frees its tensor memory and
-// returns.
+// waits (bounded) for the copies and MMAs it issued, frees its tensor memory and returns.
 #pragma once
 
 #include "tc_mlp.cuh"
 
 namespace tcw {
 
-constexpr int kChunkRows = 64;                 // batch rows (K) per stage
-constexpr int kBox = kChunkRows * 128;         // one TMA box: 64 rows x 64 BF16 columns
-constexpr int kStageA = 2 * kBox;              // dZ: the CTA's 128 output columns
-constexpr int kStageB = 4 * kBox;              // Hprev: up to 256 input columns
-constexpr int kStage = kStageA + kStageB;
+constexpr int kChunkRows = 128;                // batch rows (K) per stage
+constexpr int kBox = kChunkRows * 128;         // one TMA box: 128 rows x 64 BF16 columns
+constexpr int kStageA = 2 * kBox;              // dZ: the tile's 128 output columns
+constexpr int kStage = kStageA + kBox;         // and Hprev: its 64 input columns
 constexpr int kStages = 4;
-constexpr int kSmem = 1024 + kStages * kStage;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 4;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
-constexpr int kBiasRows = 4;                   // row quarters of a chunk in the bias sums
-static_assert(kSmem <= 227 * 1024, "shared memory");
-static_assert(kEpiWarps * 32 * 33 * 4 <= kStages * kStage, "read-back tiles fit in the stage ring");
+constexpr int kOnes = kBox;                    // all-ones MN atom: 128 K rows x 64 BF16
+constexpr int kSmem = 1024 + kStages * kStage + kOnes;
+constexpr int kTileCols = 64;                  // input columns of a tile
+constexpr int kBiasCols = 16;                  // accumulator columns of the bias sums
+constexpr int kMaxItems = 4;                   // layers of one launch
+constexpr int kTmemCols = 128;                 // the tile's accumulator and the bias columns
+static_assert(kSmem <= 227 * 1024 - 256, "shared memory");
 
 struct Args {
-    int kin;          // input columns: 128 or 256
-    int chunks;       // batch rows / 64
-    int splits;       // CTA pairs per member; split s sums chunks [s chunks / splits, (s + 1) chunks / splits)
-    float* part;      // [members][splits][256][kin]
-    float* bpart;     // [members][splits][kBiasRows][256]: column sums of dZ over the split's rows
+    int n_items;                     // layers of this launch
+    int kin[kMaxItems];              // input columns of item j's layer: 64 or 256
+    int b_batched[kMaxItems];        // Hprev has a member coordinate (0: one input for all members)
+    long long grad_w[kMaxItems];     // offsets of dW and db of item j's layer in a member's gradient
+    long long grad_b[kMaxItems];
+    long long grad_stride;           // floats per member in grad
+    int chunks;                      // batch rows / 128
+    float* grad;
     int* status;
 };
 
+// ta[j]: item j's dZ as 8-byte elements {64, rows, members}, box {16, 128, 1};
+// tb[j]: its Hprev as 8-byte elements {kin / 4, rows, members or 1}, box {16, 128, 1}.
+struct Maps {
+    CUtensorMap ta[kMaxItems];
+    CUtensorMap tb[kMaxItems];
+};
+
+// Tiles of one member for the layers of `g` (2 x kin / 64 per layer).
+__host__ __device__ inline int tiles_per_member(const Args& g)
+{
+    int t = 0;
+    for (int j = 0; j < g.n_items; ++j) t += 2 * (g.kin[j] / kTileCols);
+    return t;
+}
+
 // MN-major operand, 128-byte swizzle: leading byte offset = distance between atoms
-// adjacent in M or N (one box, 8 KB), stride byte offset = distance between atoms
+// adjacent in M or N (one box, 16 KB), stride byte offset = distance between atoms
 // adjacent in K (8 rows of 128 bytes).
-__device__ __forceinline__ uint64_t sdesc_mn(const void* p)
+__device__ __forceinline__ uint64_t sdesc_mn(const void* p, uint32_t lbo = kBox)
 {
     const uint64_t addr = tc::sa(p);
-    return ((addr >> 4) & 0x3fffull) | ((uint64_t)(kBox >> 4) << 16) | ((1024ull >> 4) << 32) | (1ull << 46) |
-           (2ull << 61);
+    return ((addr >> 4) & 0x3fffull) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) | ((1024ull >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
 }
 
 // kind::f16 instruction descriptor with A and B MN-major.
@@ -66,12 +93,9 @@ __host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N)
     return tc::idesc_bf16(M, N) | (1u << 15) | (1u << 16);
 }
 
-// ta: dZ as 8-byte elements {64, rows, members}, box {16, 64, 1};
-// tb: Hprev as 8-byte elements {kin / 4, rows, members or 1}, box {16, 64, 1}; b_batched
-// selects the member coordinate (0: one input shared by all members).
-__global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constant__ CUtensorMap ta,
-                                                            const __grid_constant__ CUtensorMap tb,
-                                                            const __grid_constant__ Args g, int b_batched)
+// grid: (tiles_per_member(g), members), one CTA per tile.
+__global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constant__ Maps maps,
+                                                            const __grid_constant__ Args g)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full[kStages], empty[kStages], acc_full, drain;
@@ -79,29 +103,40 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
     __shared__ int abort_flag;
 
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* ones = smem + kStages * kStage;  // 1 KB aligned, after every stage
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int half = blockIdx.x & 1, split = blockIdx.x >> 1, mem = blockIdx.y;
-    const int c_beg = (int)((long long)split * g.chunks / g.splits);
-    const int c_end = (int)((long long)(split + 1) * g.chunks / g.splits);
-    const int n = c_end - c_beg;
-    const int nb = g.kin / 64;  // B boxes per stage
+    const int mem = blockIdx.y;
+    // tile -> (layer item j, output half, input column block)
+    int j = 0, tt = blockIdx.x;
+    while (j < g.n_items && tt >= 2 * (g.kin[j] / kTileCols)) {
+        tt -= 2 * (g.kin[j] / kTileCols);
+        ++j;
+    }
+    if (j >= g.n_items) return;  // past the last tile (the whole CTA leaves before any barrier)
+    const int kin = g.kin[j], nb = kin / kTileCols;
+    const int half = tt / nb, cb = tt - (tt / nb) * nb;
+    const bool bias = cb == 0;  // this tile also forms the bias gradient of its 128 rows
+    const int n = g.chunks;
     volatile int* abort_v = &abort_flag;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc::sa(&tmem_base)),
-                     "r"(256));
+                     "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (threadIdx.x == 32) {
         for (int i = 0; i < kStages; ++i) {
             tc::mbar_init(&full[i], 1);
-            tc::mbar_init(&empty[i], 1 + kEpiWarps);  // the MMAs' commit and each epilogue warp
+            tc::mbar_init(&empty[i], 1);
         }
         tc::mbar_init(&acc_full, 1);
         tc::mbar_init(&drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         abort_flag = 0;
     }
+    // the all-ones block (BF16 1.0 = 0x3f80), made visible to the tensor cores' proxy
+    for (int i = threadIdx.x; i < kOnes / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(ones)[i] = 0x3f803f80u;
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -109,20 +144,18 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
 
     if (warp == 0) {
         // ---- producer ----
-        if (lane == 0) {
+        if (lane == 0 && n > 0) {
             int i = 0;
             bool ok = true;
             for (; i < n; ++i) {
                 const int st = i % kStages, use = i / kStages;
-                if (use > 0 && !(ok = tcm::wait_bar(&empty[st], (uint32_t)((use - 1) & 1), g.status, abort_v)))
-                    break;
+                if (use > 0 && !(ok = tcm::wait_bar(&empty[st], (uint32_t)((use - 1) & 1), g.status, abort_v))) break;
                 uint8_t* a = smem + st * kStage;
-                uint8_t* b = a + kStageA;
-                const int r0 = (c_beg + i) * kChunkRows;
-                tc::mbar_expect_tx(&full[st], (uint32_t)(kStageA + nb * kBox));
-                for (int j = 0; j < 2; ++j) tc::tma_load_3d(a + j * kBox, &ta, (2 * half + j) * 16, r0, mem, &full[st]);
-                for (int j = 0; j < nb; ++j)
-                    tc::tma_load_3d(b + j * kBox, &tb, j * 16, r0, b_batched ? mem : 0, &full[st]);
+                const int r0 = i * kChunkRows;
+                tc::mbar_expect_tx(&full[st], (uint32_t)kStage);
+                for (int q = 0; q < 2; ++q)
+                    tc::tma_load_3d(a + q * kBox, &maps.ta[j], (2 * half + q) * 16, r0, mem, &full[st]);
+                tc::tma_load_3d(a + kStageA, &maps.tb[j], cb * 16, r0, g.b_batched[j] ? mem : 0, &full[st]);
             }
             if (!ok)  // let the copies in flight land before the CTA exits
                 for (int q = i - kStages; q < i; ++q)
@@ -130,84 +163,57 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
         }
     } else if (warp == 1) {
         // ---- MMA issuer ----
-        if (lane == 0) {
-            const uint32_t idesc = idesc_bf16_mn(128, g.kin);
+        if (lane == 0 && n > 0) {
+            // bias tiles: N = 64 Hprev columns + 16 all-ones columns (the atom at ones)
+            const uint32_t idesc = idesc_bf16_mn(128, bias ? kTileCols + kBiasCols : kTileCols);
             bool ok = true;
             for (int i = 0; i < n && ok; ++i) {
                 const int st = i % kStages;
                 if (!(ok = tcm::wait_bar(&full[st], (uint32_t)((i / kStages) & 1), g.status, abort_v))) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint8_t* a = smem + st * kStage;
-                const uint8_t* b = a + kStageA;
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)  // 16 batch rows = two K atoms per step
-                    tc::mma_bf16(tmem, sdesc_mn(a + kk * 2048), sdesc_mn(b + kk * 2048), idesc, (i | kk) != 0);
+                for (int kk = 0; kk < kChunkRows / 16; ++kk)  // 16 batch rows = two K atoms per step
+                    tc::mma_bf16(tmem, sdesc_mn(a + kk * 2048),
+                                 sdesc_mn(a + kStageA + kk * 2048, (uint32_t)(ones - (a + kStageA))), idesc, (i | kk) != 0);
                 tc::mma_commit(&empty[st]);
             }
-            if (ok && n > 0) tc::mma_commit(&acc_full);
-            tc::mma_commit(&drain);
+            if (ok) tc::mma_commit(&acc_full);
+            tc::mma_commit(&drain);  // arrives when every MMA issued above has completed
             tc::mbar_wait(&drain, 0, g.status);
         }
     } else {
-        // ---- epilogue warps, while the MMAs run: column sums of dZ (the bias gradient) from
-        // each stage's two dZ boxes; thread et sums local columns c, c + 1 (c = 2 (et % 64))
-        // over rows 16 (et / 64) .. + 15 of every chunk, then releases the stage with its warp ----
-        const int et = threadIdx.x - 64;
-        const int bc = 2 * (et & 63), rq = et >> 6;
-        {
-            float s0 = 0.0f, s1 = 0.0f;
-            const int unit = (bc & 63) >> 3, byte = (bc & 7) * 2;
-            for (int i = 0; i < n; ++i) {
-                const int st = i % kStages;
-                if (!tcm::wait_bar(&full[st], (uint32_t)((i / kStages) & 1), g.status, abort_v)) break;
-                const uint8_t* box = smem + st * kStage + (bc >> 6) * kBox;
-#pragma unroll 8
-                for (int rr = 0; rr < kChunkRows / kBiasRows; ++rr) {
-                    const int r = (kChunkRows / kBiasRows) * rq + rr;
-                    // 128-byte swizzle: 16-byte unit u of row r sits at unit u ^ (r % 8)
-                    const uint32_t w = *reinterpret_cast<const uint32_t*>(box + r * 128 + ((unit ^ (r & 7)) << 4) + byte);
-                    s0 += __uint_as_float(w << 16);
-                    s1 += __uint_as_float(w & 0xffff0000u);
-                }
-                __syncwarp();
-                if (lane == 0) tcm::mbar_arrive(&empty[st]);
-            }
-            *reinterpret_cast<float2*>(g.bpart + (((long long)mem * g.splits + split) * kBiasRows + rq) * 256 +
-                                       128 * half + bc) = make_float2(s0, s1);
-        }
-        // the accumulator read-back below reuses the stage ring: every epilogue warp has
-        // finished reading it (all 256 epilogue threads reach this barrier once, on every path)
-        asm volatile("bar.sync 1, %0;\n" ::"n"(32 * kEpiWarps) : "memory");
-        // ---- then partial[o][c] for o = 128 half + 32 q + lane ----
-        const int e = warp - 2, q = warp & 3, ch = e >> 2;
-        const int ncol = g.kin / 2, col0 = ch * ncol;
-        const int o0 = 128 * half + 32 * q;
-        float* out = g.part + ((long long)mem * g.splits + split) * 256 * g.kin;
-        if (n == 0) {  // an empty split (more splits than chunks) contributes zeros
-            for (int c = col0; c < col0 + ncol; ++c) out[(long long)(o0 + lane) * g.kin + c] = 0.0f;
+        // ---- epilogue warps ----
+        // the tile: thread = output row o (warp % 4 = its TMEM lane quarter)
+        const int q = warp & 3;
+        const int o = 128 * half + 32 * q + lane;
+        float* grow = g.grad + (long long)mem * g.grad_stride + g.grad_w[j] + (long long)o * kin + cb * kTileCols;
+        float* gb = g.grad + (long long)mem * g.grad_stride + g.grad_b[j] + o;
+        if (n == 0) {
+            for (int c = 0; c < kTileCols; c += 4) *reinterpret_cast<float4*>(grow + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (bias) *gb = 0.0f;
         } else if (tcm::wait_bar(&acc_full, 0, g.status, abort_v)) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            // Every MMA has completed, so the stage ring is free: each warp turns its 32 x 32
-            // accumulator blocks around in a padded 32 x 33 tile there, so that every global
-            // store writes 128 contiguous bytes of one output row.
-            float* tile = reinterpret_cast<float*>(smem) + e * 32 * 33;
-            for (int c = col0; c < col0 + ncol; c += 32) {
-                float v[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+            const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16);
 #pragma unroll
-                for (int t = 0; t < 32; ++t) tile[lane * 33 + t] = v[t];
-                __syncwarp();
-                float* dst = out + (long long)o0 * g.kin + c + lane;
-#pragma unroll 8
-                for (int rr = 0; rr < 32; ++rr) dst[(long long)rr * g.kin] = tile[rr * 33 + lane];
-                __syncwarp();
+            for (int c0 = 0; c0 < kTileCols; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(tb + (uint32_t)c0, v);
+#pragma unroll
+                for (int c = 0; c < 32; c += 4)
+                    *reinterpret_cast<float4*>(grow + c0 + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+            }
+            if (bias) {
+                float v[16];
+                tcm::tmem_ld16(tb + (uint32_t)kTileCols, v);
+                *gb = v[0];
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(256));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
 }
 
 }  // namespace tcw

@@ -95,10 +95,6 @@ class Surrogate:
         the tcgen05 option)."""
         self.set_option(2, mode)
 
-    def set_wgrad_splits(self, splits):
-        """Batch splits per member of the tcgen05 weight gradients (0: SMs / (2 members))."""
-        self.set_option(3, splits)
-
     def check(self):
         native.check(self.L.surrogate_status(self.h))
 
