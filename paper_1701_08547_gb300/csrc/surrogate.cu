@@ -166,40 +166,61 @@ __global__ void loss_reduce(const float* __restrict__ lpart, float* loss, int bl
 constexpr int kRowSlice = 64;
 constexpr int kRedWarps = 32;  // warps per block of the slice sums
 
-// Head backward in one pass over a slice of srows rows (block = (slice, member), 128
-// threads, two columns each; short slices so that enough rows are in flight): dZ4[i][j] = bf16(dy[i] * w5[j] * G4[i][j]) with G4 = gelu'(Z4),
-// and part[.][.][j] = sum over the slice of dy[i] H4[i][j] (j < 256) and of dy[i] (j = 256),
-// four independent partial sums (rows i mod 4) added at the end.
-__global__ void head_bwd(const float* __restrict__ dy, const float* __restrict__ master,
-                         const __half* __restrict__ G4, const __nv_bfloat16* __restrict__ H4, __nv_bfloat16* dZ,
-                         float* part, int rows, int batch, int slices, int srows)
+// Head backward in one pass over a slice of srows rows (block = (slice, member), 256 threads:
+// eight row groups of 32 threads, each thread eight columns with 16-byte accesses):
+// dZ4[i][j] = bf16(dy[i] * w5[j] * G4[i][j]) with G4 = gelu'(Z4), and part[.][.][j] = sum over
+// the slice of dy[i] H4[i][j] (j < 256) and of dy[i] (j = 256). Row group q takes rows
+// i0 + q, i0 + q + 8, ...; its sums are added to the other groups' in group order.
+constexpr int kHeadGroups = 8;
+__global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ dy, const float* __restrict__ master,
+                                                const __half* __restrict__ G4, const __nv_bfloat16* __restrict__ H4,
+                                                __nv_bfloat16* dZ, float* part, int rows, int batch, int slices,
+                                                int srows)
 {
-    const int mem = blockIdx.y, sl = blockIdx.x, j = 2 * threadIdx.x;
+    __shared__ float red[kHeadGroups][WID + 1];
+    const int mem = blockIdx.y, sl = blockIdx.x;
+    const int q = threadIdx.x >> 5, j = 8 * (threadIdx.x & 31);
     const float* d = dy + (long long)mem * batch;
     const long long base = (long long)mem * batch * WID + j;
-    const float2 w = *reinterpret_cast<const float2*>(master + mem * P + OFF_W5 + j);
-    float s0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, s1[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float w[8];
+    {
+        const float4 a = *reinterpret_cast<const float4*>(master + mem * P + OFF_W5 + j);
+        const float4 b = *reinterpret_cast<const float4*>(master + mem * P + OFF_W5 + j + 4);
+        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+    }
+    float sh[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, sb = 0.0f;
     const int i0 = sl * srows, i1 = min(rows, i0 + srows);
-    auto row = [&](int i, int q) {
+#pragma unroll 2
+    for (int i = i0 + q; i < i1; i += kHeadGroups) {
         const float di = d[i];
         const long long o = base + (long long)i * WID;
-        const float2 g = __half22float2(*reinterpret_cast<const __half2*>(G4 + o));
-        const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(H4 + o));
-        *reinterpret_cast<__nv_bfloat162*>(dZ + o) = __floats2bfloat162_rn(di * w.x * g.x, di * w.y * g.y);
-        s0[q] = fmaf(di, h.x, s0[q]);
-        s1[q] = fmaf(di, h.y, s1[q]);
-        sb[q] += di;
-    };
-    int i = i0;
-    for (; i + 4 <= i1; i += 4) {
+        const uint4 gv = __ldg(reinterpret_cast<const uint4*>(G4 + o));
+        const uint4 hv = __ldg(reinterpret_cast<const uint4*>(H4 + o));
+        const uint32_t gw[4] = {gv.x, gv.y, gv.z, gv.w}, hw[4] = {hv.x, hv.y, hv.z, hv.w};
+        uint32_t out[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) row(i + q, q);
+        for (int t = 0; t < 4; ++t) {
+            const float2 g = __half22float2(*reinterpret_cast<const __half2*>(&gw[t]));
+            const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hw[t]));
+            const __nv_bfloat162 z = __floats2bfloat162_rn(di * w[2 * t] * g.x, di * w[2 * t + 1] * g.y);
+            out[t] = *reinterpret_cast<const uint32_t*>(&z);
+            sh[2 * t] = fmaf(di, h.x, sh[2 * t]);
+            sh[2 * t + 1] = fmaf(di, h.y, sh[2 * t + 1]);
+        }
+        *reinterpret_cast<uint4*>(dZ + o) = make_uint4(out[0], out[1], out[2], out[3]);
+        sb += di;
     }
-    for (; i < i1; ++i) row(i, 0);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) red[q][j + t] = sh[t];
+    if (j == 0) red[q][WID] = sb;
+    __syncthreads();
     float* o = part + ((long long)mem * slices + sl) * (WID + 1);
-    o[j] = (s0[0] + s0[1]) + (s0[2] + s0[3]);
-    o[j + 1] = (s1[0] + s1[1]) + (s1[2] + s1[3]);
-    if (j == 0) o[WID] = (sb[0] + sb[1]) + (sb[2] + sb[3]);
+    for (int c = threadIdx.x; c <= WID; c += blockDim.x) {
+        float v = red[0][c];
+#pragma unroll
+        for (int g = 1; g < kHeadGroups; ++g) v += red[g][c];
+        o[c] = v;
+    }
 }
 
 // part[.][.][j] = sum over the slice of dZ[i][j] (four independent partial sums)
@@ -806,13 +827,13 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
     __nv_bfloat16* dzl[NL];
     for (int l = 0; l < NL; ++l) dzl[l] = h->dZ[fused ? l : (l & 1)];
     // the head's weight and bias gradients (slices, then their sum) and dZ4 in one pass
-    // (16-row slices, longer where their partials would not fit the partial buffer)
-    int hrows = 16;
+    // (64-row slices, longer where their partials would not fit the partial buffer)
+    int hrows = 64;
     while ((long long)h->members * ((n_pad + hrows - 1) / hrows) * (WID + 1) > (long long)h->part_slices * WID * WID)
         hrows *= 2;
     const int hslices = (n_pad + hrows - 1) / hrows;
-    head_bwd<<<dim3(hslices, h->members), WID / 2, 0, s>>>(h->dy, h->master, h->G[NL - 1], h->H[NL - 1],
-                                                         dzl[NL - 1], h->part, n_pad, B, hslices, hrows);
+    head_bwd<<<dim3(hslices, h->members), 32 * kHeadGroups, 0, s>>>(h->dy, h->master, h->G[NL - 1], h->H[NL - 1],
+                                                                  dzl[NL - 1], h->part, n_pad, B, hslices, hrows);
     slices_reduce<<<dim3((WID + 1 + 31) / 32, h->members), 32 * kRedWarps, 0, s>>>(h->part, h->grad, OFF_W5,
                                                                                   WID + 1, hslices);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: head backward launch");
