@@ -58,7 +58,6 @@ struct tune_surrogate {
     __half* G[NL] = {};                 // gelu' of each layer's pre-activations, FP16 [members][batch x WID]
     __nv_bfloat16* H[NL] = {};          // [members][batch x WID]
     __nv_bfloat16* dZ[NL] = {};         // [members][batch x WID]: dZ of layer l (fused chain) or ping-pong
-    __nv_bfloat16* wbfT = nullptr;      // W2..W4 transposed, [members][3][WID][WID] (fused input gradients)
     float *y = nullptr, *dy = nullptr, *lbl = nullptr, *loss = nullptr;  // [members][batch] / [members]
     float* part = nullptr;              // split-K partials: part_slices x [WID x WID]
     int part_slices = 0;                // at least members x KSPLIT and the SM count
@@ -358,21 +357,6 @@ __global__ void cast_weights(const float* master, __nv_bfloat16* wbf, int member
     wbf[e] = __float2bfloat16_rn(master[mem * P + OFF_W(l) + (q - BOFF_W(l))]);
 }
 
-// wbfT[mem][l - 1][i][o] = wbf[mem][W_l][o][i] for l = 1..3 (W2..W4): the K-major B operands
-// of the fused input-gradient chain. 32 x 32 tiles through shared memory; grid (8, 8, 3 members)
-// x (32, 8).
-__global__ void transpose_weights(const __nv_bfloat16* __restrict__ wbf, __nv_bfloat16* wbfT)
-{
-    __shared__ __nv_bfloat16 t[32][33];
-    const int mem = blockIdx.z / (NL - 1), l = blockIdx.z % (NL - 1) + 1;
-    const __nv_bfloat16* src = wbf + (long long)mem * PB + BOFF_W(l);
-    __nv_bfloat16* dst = wbfT + ((long long)mem * (NL - 1) + (l - 1)) * WID * WID;
-    const int o0 = blockIdx.y * 32, i0 = blockIdx.x * 32;
-    for (int y = threadIdx.y; y < 32; y += 8) t[y][threadIdx.x] = src[(o0 + y) * WID + i0 + threadIdx.x];
-    __syncthreads();
-    for (int y = threadIdx.y; y < 32; y += 8) dst[(i0 + y) * WID + o0 + threadIdx.x] = t[threadIdx.x][y];
-}
-
 // Per-row E4M3 quantisation of W2..W4 (FP32, as the oracle mirrors it): s = max |w| / 448
 // (1 for a zero row), code = E4M3(w / s), nearest-even, saturating. grid (256, 3, members) x 256.
 __global__ void quantize_fp8(const float* __restrict__ master, uint8_t* w8, float* wscale, float* wscale_half)
@@ -664,19 +648,19 @@ int fused_train_forward(tune_surrogate* h, int n_pad, cudaStream_t s)
 int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaStream_t s)
 {
     if (n_pad % tcm::kRows) return tune::fail(TUNE_EINVAL, "surrogate: fused backward needs whole 128-row tiles");
-    transpose_weights<<<dim3(WID / 32, WID / 32, (NL - 1) * h->members), dim3(32, 8), 0, s>>>(h->wbf, h->wbfT);
-    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: transpose launch");
-    CUtensorMap tdz, twt;
+    CUtensorMap tdz, tw;
     const auto u64 = CU_TENSOR_MAP_DATA_TYPE_UINT64;
     const cuuint64_t dd[3] = {WID * 2 / 8, (cuuint64_t)n_pad, (cuuint64_t)h->members};
     const cuuint64_t ds[2] = {WID * 2, (cuuint64_t)h->batch * WID * 2};
     const cuuint32_t db[3] = {16, tcm::kRows, 1};
     int rc = make_map_nd(&tdz, u64, 3, dz[NL - 1], dd, ds, db);
     if (rc) return rc;
+    // W2..W4 as the forward pass reads them ([o][i] rows), 64 rows o per box: the kernel reads
+    // them MN-major, no transposed copy
     const cuuint64_t dw[4] = {WID * 2 / 8, WID, NL - 1, (cuuint64_t)h->members};
-    const cuuint64_t sw[3] = {WID * 2, WID * WID * 2, (NL - 1) * WID * WID * 2};
-    const cuuint32_t bw[4] = {16, WID, 1, 1};
-    rc = make_map_nd(&twt, u64, 4, h->wbfT, dw, sw, bw);
+    const cuuint64_t sw[3] = {WID * 2, WID * WID * 2, PB * 2};
+    const cuuint32_t bw[4] = {16, 64, 1, 1};
+    rc = make_map_nd(&tw, u64, 4, h->wbf + BOFF_W(1), dw, sw, bw);
     if (rc) return rc;
     tcm::BwdArgs g;
     g.members = h->members;
@@ -693,7 +677,7 @@ int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaS
     if (rc) return rc;
     const long long sms = tune::device_sm_count();
     const unsigned grid = (unsigned)(g.units < sms ? g.units : sms);
-    tcm::mlp_bwd_kernel<<<grid, tcm::kThreads, smem, s>>>(tdz, twt, g);
+    tcm::mlp_bwd_kernel<<<grid, tcm::kThreads, smem, s>>>(tdz, tw, g);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: fused backward launch");
     return TUNE_OK;
 }
@@ -962,7 +946,6 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     for (int l = 0; l < NL; ++l) add(M * B * WID * 2);
     for (int l = 0; l < NL; ++l) add(M * B * WID * 2);
     for (int l = 0; l < NL; ++l) add(M * B * WID * 2);
-    add(M * (NL - 1) * WID * WID * 2);
     add(M * B * 4);
     add(M * B * 4);
     add(B * 4);
@@ -989,7 +972,6 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     for (int l = 0; l < NL; ++l) h->G[l] = carve<__half>(p, M * B * WID);
     for (int l = 0; l < NL; ++l) h->H[l] = carve<__nv_bfloat16>(p, M * B * WID);
     for (int l = 0; l < NL; ++l) h->dZ[l] = carve<__nv_bfloat16>(p, M * B * WID);
-    h->wbfT = carve<__nv_bfloat16>(p, M * (NL - 1) * WID * WID);
     h->y = carve<float>(p, M * B);
     h->dy = carve<float>(p, M * B);
     h->lbl = carve<float>(p, B);

@@ -10,10 +10,11 @@
 // The structure is the inference kernel's (tc_mlp.cuh): warp 0 streams the unit's
 // dZ4 rows and 32 KB K chunks of the weights with TMA, warp 1 issues the MMAs of two
 // chains alternately, warps 2-17 run the epilogues (thread = accumulator row, four
-// warps per TMEM lane quarter, one per 64-column quarter). The MMA needs W_l as a
-// K-major [input][output] operand, so the weights come from a transposed BF16 copy
-// W_l^T, [members][3][256][256] (layers 2..4), made from the same BF16 values the
-// forward pass uses.
+// warps per TMEM lane quarter, one per 64-column quarter). The product's B operand is
+// W_l with the contraction over its output index o, i.e. W_l as stored ([o][i], i
+// contiguous) read MN-major: a 32 KB stage holds 64 rows o of W_l as four boxes of 64
+// inputs (the MN-major 128-byte-swizzle atoms, 8 KB apart along N), from the same BF16
+// copy the forward pass uses.
 //
 // Every wait is bounded; on timeout the kernel sets status bit 2, stops issuing
 // work, waits (bounded) for the copies and MMAs it issued, frees its tensor memory
@@ -25,6 +26,16 @@
 namespace tcm {
 
 constexpr int kBwdStages = kLayers - 1;  // products with W4, W3, W2
+
+// MN-major B operand of a weight stage, 128-byte swizzle: leading byte offset = distance
+// between the 64-input atoms along N (one 64-row box, 8 KB), stride byte offset = distance
+// between 8-row groups along K (1 KB).
+__device__ __forceinline__ uint64_t sdesc_w_mn(const void* p)
+{
+    const uint64_t addr = tc::sa(p);
+    return ((addr >> 4) & 0x3fffull) | ((uint64_t)((64 * 128) >> 4) << 16) | ((1024ull >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
 
 struct BwdArgs {
     int members;
@@ -39,9 +50,9 @@ struct BwdArgs {
 // grid: min(SMs, units) persistent CTAs; CTA b runs units b, b + gridDim.x, ...; its
 // j-th unit goes to chain j % 2. Unit u = (tile u / members, member u % members).
 // tdz: dZ4 as 8-byte elements {64, rows, members}, box {16, 128, 1};
-// twt: W^T as 8-byte elements {64, 256, 3, members}, box {16, 256, 1, 1}.
+// tw: W2..W4 as 8-byte elements {64 (inputs), 256 (outputs), 3, members}, box {16, 64, 1, 1}.
 __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorMap tdz,
-                                               const __grid_constant__ CUtensorMap twt,
+                                               const __grid_constant__ CUtensorMap tw,
                                                const __grid_constant__ BwdArgs g)
 {
     using C = Cfg<false>;
@@ -123,8 +134,11 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
                                                            abort_v)))
                                 break;
                             tc::mbar_expect_tx(&w_full[st], kChunkW);
-                            // stage l multiplies by W_{4-l}: transposed copy number 2 - l
-                            tma_load_4d(ring + st * kChunkW, &twt, c * 16, 0, kBwdStages - 1 - l, mem, &w_full[st]);
+                            // stage l multiplies by W_{4-l} (matrix 2 - l of W2..W4): rows o of K
+                            // chunk c, four boxes of 64 inputs
+                            for (int q = 0; q < kChunkW / (64 * 128); ++q)
+                                tma_load_4d(ring + st * kChunkW + q * (64 * 128), &tw, q * 16, c * 64,
+                                            kBwdStages - 1 - l, mem, &w_full[st]);
                         }
                     }
                 }
@@ -142,7 +156,8 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
         if (lane == 0) {
             long long seq = 0;
             bool ok = true;
-            const uint32_t idesc = tc::idesc_bf16(kRows, kWid);
+            // A (the dZ rows) K-major, B (W as stored) MN-major
+            const uint32_t idesc = tc::idesc_bf16(kRows, kWid) | (1u << 16);
             for (long long j = 0; j < my_units && ok; j += 2) {
                 for (int l = 0; l < kBwdStages && ok; ++l) {
                     for (int s = 0; s < 2 && ok; ++s) {
@@ -165,7 +180,7 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk) {
                                 const uint64_t a = tc::sdesc(act + c * kChunkA + kk * 32);
-                                const uint64_t b = tc::sdesc(ring + st * kChunkW + kk * 32);
+                                const uint64_t b = sdesc_w_mn(ring + st * kChunkW + kk * 2048);
                                 tc::mma_bf16(d, a, b, idesc, (c | kk) != 0);
                             }
                             tc::mma_commit(&w_empty[st]);
