@@ -36,6 +36,16 @@ __device__ __forceinline__ float gelu_grad_t(float z, float z2, float t)
     return fmaf(0.5f * z * du, fmaf(-t, t, 1.0f), 0.5f * (1.0f + t));
 }
 
+// gelu'(Z) of the training forward passes (FP16, [members][rows][256]) is kept in 128-row
+// tiles, within a tile in blocks of 16 columns, each block row-major [128 rows][16 columns]:
+// a warp whose lanes are 32 consecutive rows (the TMEM lane layout of the epilogues that write
+// and read it) then covers 1 KB of contiguous memory with one 32-byte access per lane.
+// Offset of (row, column) within one member's array.
+__host__ __device__ __forceinline__ long long gprime_at(long long row, int col)
+{
+    return ((row >> 7) << 15) + ((long long)(col >> 4) << 11) + ((row & 127) << 4) + (col & 15);
+}
+
 __device__ __forceinline__ float gelu_grad(float z)
 {
     const float z2 = z * z;

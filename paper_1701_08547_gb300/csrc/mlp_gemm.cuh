@@ -36,13 +36,14 @@ struct GemmArgs {
     // epilogue operands (per-batch strides in elements)
     const float* bias;
     long long sBias;
-    __half* G;         // EPI_BIAS_GELU: gelu'(pre-activation) out (may be null); EPI_GELU_GRAD: its input
+    __half* G;         // EPI_BIAS_GELU: gelu'(pre-activation) out (may be null); EPI_GELU_GRAD: its input;
+                       // N = 256 columns in the tiled layout of gprime_at (ldc does not apply)
     long long sG;
     __nv_bfloat16* H;  // bf16 output
     long long sH;
     float* F;          // fp32 output
     long long sF;
-    int ldc;           // leading dimension of G / H / F
+    int ldc;           // leading dimension of H / F
     int k_split;       // split-K: blockIdx.z = batch * k_split + split; F gets [split] slices
     long long sSplit;  // stride between split slices of F
 };
@@ -226,12 +227,12 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(const __grid_co
                     const float z0 = v0 + g.bias[batch * g.sBias + n];
                     const float z1 = v1 + g.bias[batch * g.sBias + n + 1];
                     if (g.G)
-                        *reinterpret_cast<__half2*>(g.G + batch * g.sG + off) =
+                        *reinterpret_cast<__half2*>(g.G + batch * g.sG + gprime_at(m, n)) =
                             __floats2half2_rn(gelu_grad(z0), gelu_grad(z1));
                     *reinterpret_cast<__nv_bfloat162*>(g.H + batch * g.sH + off) =
                         __floats2bfloat162_rn(gelu(z0), gelu(z1));
                 } else if (EPI == EPI_GELU_GRAD) {
-                    const float2 d = __half22float2(*reinterpret_cast<const __half2*>(g.G + batch * g.sG + off));
+                    const float2 d = __half22float2(*reinterpret_cast<const __half2*>(g.G + batch * g.sG + gprime_at(m, n)));
                     *reinterpret_cast<__nv_bfloat162*>(g.H + batch * g.sH + off) =
                         __floats2bfloat162_rn(v0 * d.x, v1 * d.y);
                 } else {

@@ -55,7 +55,7 @@ struct tune_surrogate {
     float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     __nv_bfloat16* wbf = nullptr;
     __nv_bfloat16* xin = nullptr;       // [batch x IN]
-    __half* G[NL] = {};                 // gelu' of each layer's pre-activations, FP16 [members][batch x WID]
+    __half* G[NL] = {};                 // gelu' of each layer's pre-activations, FP16 [members][batch x WID], tiled (mlp::gprime_at)
     __nv_bfloat16* H[NL] = {};          // [members][batch x WID]
     __nv_bfloat16* dZ[NL] = {};         // [members][batch x WID]: dZ of layer l (fused chain) or ping-pong
     float *y = nullptr, *dy = nullptr, *lbl = nullptr, *loss = nullptr;  // [members][batch] / [members]
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ dy, co
     for (int i = i0 + q; i < i1; i += kHeadGroups) {
         const float di = d[i];
         const long long o = base + (long long)i * WID;
-        const uint4 gv = __ldg(reinterpret_cast<const uint4*>(G4 + o));
+        const uint4 gv = __ldg(reinterpret_cast<const uint4*>(G4 + (long long)mem * batch * WID + mlp::gprime_at(i, j)));
         const uint4 hv = __ldg(reinterpret_cast<const uint4*>(H4 + o));
         const uint32_t gw[4] = {gv.x, gv.y, gv.z, gv.w}, hw[4] = {hv.x, hv.y, hv.z, hv.w};
         uint32_t out[4];

@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kThreads) gemm_fwd_kernel(const __grid_constan
         const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
         const float* bias = g.bias + member * g.sBias;
         __nv_bfloat16* H = g.H + member * g.sH + (long long)row * g.N;
-        __half* G = g.G ? g.G + member * g.sG + (long long)row * g.N : nullptr;
+        __half* G = g.G ? g.G + member * g.sG : nullptr;  // tiled layout (mlp::gprime_at), N = 256
         const int c_beg = half * (g.N / 2), c_end = c_beg + g.N / 2;
         for (int c0 = c_beg; c0 < c_end; c0 += 32) {
             float v[32];
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) gemm_fwd_kernel(const __grid_constan
                         const __half2 d = __floats2half2_rn(mlp::gelu_grad(v[i + 2 * t]), mlp::gelu_grad(v[i + 2 * t + 1]));
                         q[t] = *reinterpret_cast<const uint32_t*>(&d);
                     }
-                    *reinterpret_cast<uint4*>(G + c0 + i) = pk;
+                    *reinterpret_cast<uint4*>(G + mlp::gprime_at(row, c0 + i)) = pk;
                 }
             }
 #pragma unroll

@@ -73,9 +73,9 @@ struct Args {
     const float* wscale_half;  // FP8: [members][3][256] halves of the scales of W2..W4 (one per matrix, repeated per row)
     float* pred;            // [members][pred_stride]
     long long pred_stride;  // member stride of pred (n for inference)
-    // training (BF16 only): per layer gelu'(z) of the pre-activations (FP16) and the
-    // activations h = gelu(z) (BF16) of every row < n, [members][act_stride] with rows of
-    // 256; null: not kept
+    // training (BF16 only): per layer gelu'(z) of the pre-activations (FP16, in the tiled
+    // layout of mlp::gprime_at) and the activations h = gelu(z) (BF16, rows of 256) of every
+    // row < n, [members][act_stride]; null: not kept
     __half* g_out[kLayers];
     __nv_bfloat16* h_out[kLayers];
     long long act_stride;
@@ -449,7 +449,8 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                                 v[i + 1] = h2.y;
                             }
                         }
-                        if (TRAIN && !FP8 && g.g_out[l]) st_global_v8(g.g_out[l] + arow, gd);
+                        if (TRAIN && !FP8 && g.g_out[l])  // tiled layout (mlp::gprime_at): one 1 KB run per warp
+                            st_global_v8(g.g_out[l] + (long long)mem * g.act_stride + mlp::gprime_at(tile * kRows + r, n0), gd);
                         if (FP8 && !head) {
                             // E4M3 codes of 2 h: 16 columns = one 16-byte unit
                             uint32_t w[4];

@@ -40,7 +40,7 @@ __device__ __forceinline__ uint64_t sdesc_w_mn(const void* p)
 struct BwdArgs {
     int members;
     long long units;                  // rows / 128 * members (rows a multiple of 128: every unit's rows exist)
-    const __half* g[kBwdStages];      // stage j: gelu'(Z_{3-j}), [members][act_stride]
+    const __half* g[kBwdStages];      // stage j: gelu'(Z_{3-j}), [members][act_stride], tiled (mlp::gprime_at)
     __nv_bfloat16* dz[kBwdStages];    // stage j: dZ_{3-j}, same layout
     long long act_stride;             // member stride of z and dz (elements); rows of 256
     int* status;
@@ -212,7 +212,7 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
                     const int tile = (int)(u / g.members), mem = (int)(u % g.members);
                     const int row = tile * kRows + r;
                     const long long arow = (long long)mem * g.act_stride + (long long)row * kWid;
-                    const __half* gr = g.g[l] + arow;
+                    const __half* gr = g.g[l] + (long long)mem * g.act_stride;  // tiled (mlp::gprime_at)
                     __nv_bfloat16* dzr = g.dz[l] + arow;
                     uint8_t* act = smem + s * C::act_bytes;
                     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * kWid);
@@ -221,7 +221,7 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
                     // before the accumulator wait
                     uint32_t gw[kWid / 4 / 16][8];
 #pragma unroll
-                    for (int b = 0; b < kWid / 4 / 16; ++b) ld_global_v8u(gr + c_beg + 16 * b, gw[b]);
+                    for (int b = 0; b < kWid / 4 / 16; ++b) ld_global_v8u(gr + mlp::gprime_at(row, c_beg + 16 * b), gw[b]);
                     if (!(ok = wait_bar(&acc_full[s], (uint32_t)((kBwdStages * k + l) & 1), g.status, abort_v)))
                         break;
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
