@@ -16,6 +16,7 @@
 #include <cudaTypedefs.h>
 
 #include "mlp_gemm.cuh"
+#include "pdl.cuh"
 #include "tc_gemm.cuh"
 #include "tc_mlp.cuh"
 #include "tc_mlp_bwd.cuh"
@@ -126,6 +127,7 @@ __global__ void head_fwd(const __nv_bfloat16* __restrict__ H4, const float* __re
 __global__ void loss_grad(const float* __restrict__ y, const float* __restrict__ t, float* dy, float* lpart, int n,
                           int batch)
 {
+    pdl::grid_dep_enter();  // a step of the training chain: wait for the launch before it
     const int mem = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     __shared__ float red[8];
@@ -153,6 +155,7 @@ __global__ void loss_grad(const float* __restrict__ y, const float* __restrict__
 // loss[mem] = (sum of the blocks' partial sums, in block order) / n
 __global__ void loss_reduce(const float* __restrict__ lpart, float* loss, int blocks, int n)
 {
+    pdl::grid_dep_enter();  // a step of the training chain: wait for the launch before it
     const int mem = blockIdx.x;
     if (threadIdx.x != 0 || !loss) return;
     float s = 0.0f;
@@ -176,6 +179,7 @@ __global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ dy, co
                                                 __nv_bfloat16* dZ, float* part, int rows, int batch, int slices,
                                                 int srows)
 {
+    pdl::grid_dep_enter();  // a step of the training chain: wait for the launch before it
     __shared__ float red[kHeadGroups][WID + 1];
     const int mem = blockIdx.y, sl = blockIdx.x;
     const int q = threadIdx.x >> 5, j = 8 * (threadIdx.x & 31);
@@ -243,6 +247,7 @@ __global__ void bias_partial(const __nv_bfloat16* __restrict__ dZ, float* part, 
 // partial sums are added in warp order (deterministic).
 __global__ void slices_reduce(const float* __restrict__ part, float* grad, long long off, int cols, int slices)
 {
+    pdl::grid_dep_enter();  // a step of the training chain: wait for the launch before it
     // block = 32 columns x kRedWarps warps; warp w adds slices w, w + kRedWarps, ..., then
     // the warps' sums are added in warp order
     const int mem = blockIdx.y, w = threadIdx.x >> 5;
@@ -315,6 +320,7 @@ __global__ void split_reduce(const float* __restrict__ part, float* grad, long l
 __global__ void adam_update(float* master, const float* grad, float* m, float* v, __nv_bfloat16* wbf, int members,
                             float lr, float b1, float b2, float eps, float c1, float c2)
 {
+    pdl::grid_dep_enter();  // a step of the training chain: wait for the launch before it
     const long long e = 4 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
     if (e >= (long long)members * P) return;
     const long long p = e % P;
@@ -386,6 +392,7 @@ __global__ void quantize_fp8(const float* __restrict__ master, uint8_t* w8, floa
 __global__ void gather_batch(const __nv_bfloat16* __restrict__ feats, const float* __restrict__ labels,
                              const int32_t* __restrict__ order, int n, int batch, __nv_bfloat16* xin, float* lbl)
 {
+    pdl::grid_dep_enter();  // a step of the training chain: wait for the launch before it
     const int r = blockIdx.x;
     const int c = threadIdx.x;  // 64 threads x 2 elements
     const __nv_bfloat162 z = __floats2bfloat162_rn(0.0f, 0.0f);
@@ -407,6 +414,7 @@ constexpr int kGatherRows = 256 / kRowU4;
 __global__ void gather_batch16(const __nv_bfloat16* __restrict__ feats, const float* __restrict__ labels,
                                const int32_t* __restrict__ order, int n, int batch, __nv_bfloat16* xin, float* lbl)
 {
+    pdl::grid_dep_enter();  // a step of the training chain: wait for the launch before it
     const int r = blockIdx.x * kGatherRows + threadIdx.x / kRowU4, c = threadIdx.x % kRowU4;
     if (r >= batch) return;
     uint4 val = make_uint4(0u, 0u, 0u, 0u);
@@ -537,7 +545,12 @@ int launch_fused(const CUtensorMap& tx, const CUtensorMap& tw1, const CUtensorMa
     static std::atomic<uint64_t> attr{0};
     const int rc = smem_attr(tcm::mlp_infer_kernel<FP8, TRAIN>, smem, attr, "surrogate: fused smem attribute");
     if (rc) return rc;
-    tcm::mlp_infer_kernel<FP8, TRAIN><<<grid, tcm::kThreads, smem, s>>>(tx, tw1, tw, g);
+    if constexpr (TRAIN)  // a step of the training chain (pdl.cuh)
+        TUNE_CUDA_TRY(pdl::launch_dep(tcm::mlp_infer_kernel<FP8, TRAIN>, dim3(grid), dim3(tcm::kThreads), smem, s, tx,
+                                      tw1, tw, g),
+                      "surrogate: fused launch");
+    else
+        tcm::mlp_infer_kernel<FP8, TRAIN><<<grid, tcm::kThreads, smem, s>>>(tx, tw1, tw, g);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: fused launch");
     return TUNE_OK;
 }
@@ -677,8 +690,8 @@ int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaS
     if (rc) return rc;
     const long long sms = tune::device_sm_count();
     const unsigned grid = (unsigned)(g.units < sms ? g.units : sms);
-    tcm::mlp_bwd_kernel<<<grid, tcm::kThreads, smem, s>>>(tdz, tw, g);
-    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: fused backward launch");
+    TUNE_CUDA_TRY(pdl::launch_dep(tcm::mlp_bwd_kernel, dim3(grid), dim3(tcm::kThreads), smem, s, tdz, tw, g),
+                  "surrogate: fused backward launch");
     return TUNE_OK;
 }
 
@@ -720,8 +733,9 @@ int wgrad_tc(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaStream_
     static std::atomic<uint64_t> attr{0};
     const int rc = smem_attr(tcw::wgrad_kernel, tcw::kSmem, attr, "surrogate: weight-gradient smem attribute");
     if (rc) return rc;
-    tcw::wgrad_kernel<<<dim3(tcw::tiles_per_member(g), M), tcw::kThreads, tcw::kSmem, s>>>(maps, g);
-    TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: weight-gradient launch");
+    TUNE_CUDA_TRY(pdl::launch_dep(tcw::wgrad_kernel, dim3(tcw::tiles_per_member(g), M), dim3(tcw::kThreads), tcw::kSmem,
+                                  s, maps, g),
+                  "surrogate: weight-gradient launch");
     return TUNE_OK;
 }
 
@@ -802,8 +816,12 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
 {
     const int B = h->batch;
     const int lblocks = (B + 255) / 256;
-    loss_grad<<<dim3(lblocks, h->members), 256, 0, s>>>(h->y, h->lbl, h->dy, h->part, n, B);
-    loss_reduce<<<h->members, 32, 0, s>>>(h->part, h->loss, lblocks, n);
+    // the loss, the head's backward and its slice sums: steps of the training chain (pdl.cuh)
+    TUNE_CUDA_TRY(pdl::launch_dep(loss_grad, dim3(lblocks, h->members), dim3(256), 0, s, h->y, h->lbl, h->dy, h->part,
+                                  n, B),
+                  "surrogate: loss launch");
+    TUNE_CUDA_TRY(pdl::launch_dep(loss_reduce, dim3(h->members), dim3(32), 0, s, h->part, h->loss, lblocks, n),
+                  "surrogate: loss launch");
     const int slices = (n_pad + kRowSlice - 1) / kRowSlice;
     // dZ of layer l: a buffer per layer when the input-gradient chain runs fused, else two
     // buffers in turn (each is consumed by its weight gradient before it is overwritten)
@@ -816,10 +834,12 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
     while ((long long)h->members * ((n_pad + hrows - 1) / hrows) * (WID + 1) > (long long)h->part_slices * WID * WID)
         hrows *= 2;
     const int hslices = (n_pad + hrows - 1) / hrows;
-    head_bwd<<<dim3(hslices, h->members), 32 * kHeadGroups, 0, s>>>(h->dy, h->master, h->G[NL - 1], h->H[NL - 1],
-                                                                  dzl[NL - 1], h->part, n_pad, B, hslices, hrows);
-    slices_reduce<<<dim3((WID + 1 + 31) / 32, h->members), 32 * kRedWarps, 0, s>>>(h->part, h->grad, OFF_W5,
-                                                                                  WID + 1, hslices);
+    TUNE_CUDA_TRY(pdl::launch_dep(head_bwd, dim3(hslices, h->members), dim3(32 * kHeadGroups), 0, s, h->dy, h->master,
+                                  h->G[NL - 1], h->H[NL - 1], dzl[NL - 1], h->part, n_pad, B, hslices, hrows),
+                  "surrogate: head backward launch");
+    TUNE_CUDA_TRY(pdl::launch_dep(slices_reduce, dim3((WID + 1 + 31) / 32, h->members), dim3(32 * kRedWarps), 0, s,
+                                  h->part, h->grad, OFF_W5, WID + 1, hslices),
+                  "surrogate: head backward launch");
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: head backward launch");
     if (fused) {  // input gradients dZ3..dZ1, then every layer's weight and bias gradients
         int rc = fused_backward(h, n_pad, dzl, s);
@@ -864,8 +884,9 @@ int adam(tune_surrogate* h, cudaStream_t s)
     h->step += 1;
     const float c1 = 1.0f - powf(h->b1, (float)h->step), c2 = 1.0f - powf(h->b2, (float)h->step);
     const long long total = (long long)h->members * P;
-    adam_update<<<(unsigned)((total / 4 + 255) / 256), 256, 0, s>>>(h->master, h->grad, h->m, h->v, h->wbf,
-                                                                     h->members, h->lr, h->b1, h->b2, h->eps, c1, c2);
+    TUNE_CUDA_TRY(pdl::launch_dep(adam_update, dim3((unsigned)((total / 4 + 255) / 256)), dim3(256), 0, s, h->master,
+                                  h->grad, h->m, h->v, h->wbf, h->members, h->lr, h->b1, h->b2, h->eps, c1, c2),
+                  "surrogate: adam launch");
     h->fp8_stale = true;
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: adam launch");
     return TUNE_OK;
@@ -875,10 +896,13 @@ int load_batch(tune_surrogate* h, const __nv_bfloat16* feats, const float* label
                cudaStream_t s)
 {
     if ((reinterpret_cast<uintptr_t>(feats) & 15) == 0)
-        gather_batch16<<<(h->batch + kGatherRows - 1) / kGatherRows, 256, 0, s>>>(feats, labels, order, n, h->batch,
-                                                                                 h->xin, h->lbl);
+        TUNE_CUDA_TRY(pdl::launch_dep(gather_batch16, dim3((h->batch + kGatherRows - 1) / kGatherRows), dim3(256), 0, s,
+                                      feats, labels, order, n, h->batch, h->xin, h->lbl),
+                      "surrogate: gather launch");
     else
-        gather_batch<<<h->batch, IN / 2, 0, s>>>(feats, labels, order, n, h->batch, h->xin, h->lbl);
+        TUNE_CUDA_TRY(pdl::launch_dep(gather_batch, dim3(h->batch), dim3(IN / 2), 0, s, feats, labels, order, n,
+                                      h->batch, h->xin, h->lbl),
+                      "surrogate: gather launch");
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: gather launch");
     return TUNE_OK;
 }

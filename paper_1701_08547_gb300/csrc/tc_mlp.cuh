@@ -41,6 +41,7 @@
 #include <stdint.h>
 
 #include "gelu.cuh"
+#include "pdl.cuh"
 #include "tc_gemm.cuh"
 
 namespace tcm {
@@ -253,6 +254,7 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
     const long long my_units = g.units > (long long)blockIdx.x ? (g.units - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     volatile int* abort_v = &abort_flag;
 
+    pdl::grid_dep_enter();  // launched after the batch gather in a training step
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc::sa(&tmem_base)),
                      "r"(512));

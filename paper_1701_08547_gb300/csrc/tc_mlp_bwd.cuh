@@ -69,6 +69,7 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
     const long long my_units = g.units > (long long)blockIdx.x ? (g.units - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     volatile int* abort_v = &abort_flag;
 
+    pdl::grid_dep_enter();  // launched after the head backward in a training step
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc::sa(&tmem_base)),
                      "r"(512));

@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const __grid_constan
     uint8_t* ones = smem + kStages * kStage;  // 1 KB aligned, after every stage
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mem = blockIdx.y;
+    pdl::grid_dep_enter();  // launched after the input-gradient chain in a training step
     // tile -> (layer item j, output half, input column block)
     int j = 0, tt = blockIdx.x;
     while (j < g.n_items && tt >= 2 * (g.kin[j] / kTileCols)) {

@@ -54,6 +54,7 @@ struct CtaTables {
     // warp reading one g position of 32 rows (lane = row) touches 32 distinct banks.
     float ipar[kMaxB][kIparStride];
     float rcp[8];                    // 1 / IPC per class
+    float rcpn[33];                  // 1 / n for n = 1..32 (axis-subset sizes; [0] unused)
     float hide[kMaxW + 1];           // max(1, W_sat / W*)
     float lane[32];                  // (32 * W_B) / T by t position
     int wb[32];                      // W_B = ceil(T / 32) by t position
@@ -161,6 +162,7 @@ void host_cta_tables(const tune_arch& a, const tune_axes& x, CtaTables& ct)
     }
     for (int w = 0; w <= kMaxW; ++w) ct.hide[w] = std::max(1.0f, w > 0 ? (float)a.w_sat / (float)w : 1.0f);
     for (int c = 0; c < 8; ++c) ct.rcp[c] = c < TUNE_NCLASS ? 1.0f / a.ipc[c] : 0.0f;
+    for (int n = 1; n <= 32; ++n) ct.rcpn[n] = 1.0f / (float)n;
     for (int c = 0; c < 4; ++c) {
         const long long need = c < x.n_c ? (long long)x.c[c] * a.smem_caps[a.n_smem_caps - 1] : 0;
         int i = 0;
@@ -290,6 +292,7 @@ __device__ void build_cta_tables(const EvalParams& p, const tune_arch& a, CtaTab
         ct.rwarps[R] = (unsigned short)warps;
         ct.rwbmax[R] = (unsigned short)min(wbmax, 65535);
     }
+    if (tid < 33) ct.rcpn[tid] = tid > 0 ? __frcp_rn((float)tid) : 0.0f;
 }
 
 // q = floor(n / d) for 0 <= n < 2^25 and 1 <= d < 2^25: a single-precision estimate
@@ -527,14 +530,20 @@ __global__ void __maxnreg__(64)
             if (lane < kMaxB) {
                 if (g_dense) {
                     w.iparmin[lane + 1] = ct.iparmin[lane];
-                } else {
+                } else if (EMIT) {
                     float mn = kInf;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const float f = j < nG ? ct.ipar[lane][w.gpos[j]] : kInf;
-                        if (EMIT) w.iparc[lane][j] = f;
+                        w.iparc[lane][j] = f;
                         mn = fminf(mn, f);
                     }
+                    w.iparmin[lane + 1] = mn;
+                } else {
+                    // the kernel's nG grid sizes only (a warp-uniform trip count)
+                    const float* row = ct.ipar[lane];
+                    float mn = kInf;
+                    for (int j = 0; j < nG; ++j) mn = fminf(mn, row[w.gpos[j]]);
                     w.iparmin[lane + 1] = mn;
                 }
             }
@@ -594,8 +603,7 @@ __global__ void __maxnreg__(64)
                 const int nP = nT * nU;
                 const int n_prow = (nP + 31) >> 5;
                 const int n_blk = (nP * nC + 127) >> 7;  // blocks of 128 triples for the scan
-                const float rcp_u = __frcp_rn((float)nU), rcp_c = __frcp_rn((float)nC);
-                const float rcp_uc = __frcp_rn((float)nUC);
+                const float rcp_u = ct.rcpn[nU], rcp_c = ct.rcpn[nC], rcp_uc = ct.rcpn[nUC];
                 {  // tail of the last block: no triple (NaN)
                     const float nan = __int_as_float(0x7fc00000);
                     *reinterpret_cast<float4*>(&w.key[((n_blk - 1) << 7) + 4 * lane]) = make_float4(nan, nan, nan, nan);
