@@ -538,8 +538,8 @@ int refresh_fp8(tune_surrogate* h, cudaStream_t s)
 }
 
 template <bool FP8, bool TRAIN = false>
-int launch_fused(const CUtensorMap& tx, const CUtensorMap& tw1, const CUtensorMap& tw, const tcm::Args& g,
-                 unsigned grid, cudaStream_t s)
+int launch_fused(const CUtensorMap& tx, const CUtensorMap& tw1, const CUtensorMap& tw, const CUtensorMap& th,
+                 const tcm::Args& g, unsigned grid, cudaStream_t s)
 {
     constexpr int smem = tcm::Cfg<FP8>::smem;
     static std::atomic<uint64_t> attr{0};
@@ -547,10 +547,10 @@ int launch_fused(const CUtensorMap& tx, const CUtensorMap& tw1, const CUtensorMa
     if (rc) return rc;
     if constexpr (TRAIN)  // a step of the training chain (pdl.cuh)
         TUNE_CUDA_TRY(pdl::launch_dep(tcm::mlp_infer_kernel<FP8, TRAIN>, dim3(grid), dim3(tcm::kThreads), smem, s, tx,
-                                      tw1, tw, g),
+                                      tw1, tw, th, g),
                       "surrogate: fused launch");
     else
-        tcm::mlp_infer_kernel<FP8, TRAIN><<<grid, tcm::kThreads, smem, s>>>(tx, tw1, tw, g);
+        tcm::mlp_infer_kernel<FP8, TRAIN><<<grid, tcm::kThreads, smem, s>>>(tx, tw1, tw, th, g);
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: fused launch");
     return TUNE_OK;
 }
@@ -609,7 +609,8 @@ int fused_forward(tune_surrogate* h, const __nv_bfloat16* feats, int64_t n, floa
     g.status = h->status;
     const long long sms = tune::device_sm_count();
     const unsigned grid = (unsigned)(g.units < sms ? g.units : sms);
-    return fp8 ? launch_fused<true>(tx, tw1, tw, g, grid, s) : launch_fused<false>(tx, tw1, tw, g, grid, s);
+    // (the activation map is used by the training variant only)
+    return fp8 ? launch_fused<true>(tx, tw1, tw, tx, g, grid, s) : launch_fused<false>(tx, tw1, tw, tx, g, grid, s);
 }
 
 // Training forward of rows [0, n_pad) of h->xin through the fused kernel (BF16), keeping
@@ -632,6 +633,17 @@ int fused_train_forward(tune_surrogate* h, int n_pad, cudaStream_t s)
     const cuuint64_t sw[3] = {WID * 2, WID * WID * 2, PB * 2};
     rc = make_map_nd(&tw, u64, 4, h->wbf + BOFF_W(1), dw, sw, bw);
     if (rc) return rc;
+    // H of layers 1-3 as the kernel stores them from its activation buffer: 128-row boxes of one
+    // 128-byte column chunk, dimension 3 = layer (the H buffers are carved at a constant stride)
+    const long long hstride = (const char*)h->H[1] - (const char*)h->H[0];
+    if ((const char*)h->H[2] - (const char*)h->H[1] != hstride || hstride <= 0 || hstride % 16)
+        return tune::fail(TUNE_EINVAL, "surrogate: activation buffers are not evenly spaced");
+    CUtensorMap th;
+    const cuuint64_t hd[4] = {WID * 2 / 8, (cuuint64_t)n_pad, (cuuint64_t)h->members, NL - 1};
+    const cuuint64_t hs[3] = {WID * 2, (cuuint64_t)h->batch * WID * 2, (cuuint64_t)hstride};
+    const cuuint32_t hb[4] = {16, tcm::kRows, 1, 1};
+    rc = make_map_nd(&th, u64, 4, h->H[0], hd, hs, hb);
+    if (rc) return rc;
     tcm::Args g;
     g.n = n_pad;
     g.members = h->members;
@@ -652,7 +664,7 @@ int fused_train_forward(tune_surrogate* h, int n_pad, cudaStream_t s)
     g.status = h->status;
     const long long sms = tune::device_sm_count();
     const unsigned grid = (unsigned)(g.units < sms ? g.units : sms);
-    return launch_fused<false, true>(tx, tw1, tw, g, grid, s);
+    return launch_fused<false, true>(tx, tw1, tw, th, g, grid, s);
 }
 
 // Input gradients of layers 4, 3 and 2 in one persistent launch (tc_mlp_bwd.cuh):
@@ -675,12 +687,24 @@ int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaS
     const cuuint32_t bw[4] = {16, 64, 1, 1};
     rc = make_map_nd(&tw, u64, 4, h->wbf + BOFF_W(1), dw, sw, bw);
     if (rc) return rc;
+    // dZ1..dZ3 as the kernel stores dZ3 and dZ2 from its activation buffer: 128-row boxes of one
+    // 128-byte column chunk, dimension 3 = layer (the buffers must be evenly spaced)
+    const long long zstride = (const char*)dz[1] - (const char*)dz[0];
+    if ((const char*)dz[2] - (const char*)dz[1] != zstride || zstride <= 0 || zstride % 16)
+        return tune::fail(TUNE_EINVAL, "surrogate: gradient buffers are not evenly spaced");
+    CUtensorMap tdzs;
+    const cuuint64_t zd[4] = {WID * 2 / 8, (cuuint64_t)n_pad, (cuuint64_t)h->members, NL - 1};
+    const cuuint64_t zs[3] = {WID * 2, (cuuint64_t)h->batch * WID * 2, (cuuint64_t)zstride};
+    const cuuint32_t zb[4] = {16, tcm::kRows, 1, 1};
+    rc = make_map_nd(&tdzs, u64, 4, dz[0], zd, zs, zb);
+    if (rc) return rc;
     tcm::BwdArgs g;
     g.members = h->members;
     g.units = (long long)(n_pad / tcm::kRows) * h->members;
     for (int j = 0; j < tcm::kBwdStages; ++j) {
         g.g[j] = h->G[NL - 2 - j];
         g.dz[j] = dz[NL - 2 - j];
+        g.dz_coord[j] = NL - 2 - j;
     }
     g.act_stride = (long long)h->batch * WID;
     g.status = h->status;
@@ -690,7 +714,7 @@ int fused_backward(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaS
     if (rc) return rc;
     const long long sms = tune::device_sm_count();
     const unsigned grid = (unsigned)(g.units < sms ? g.units : sms);
-    TUNE_CUDA_TRY(pdl::launch_dep(tcm::mlp_bwd_kernel, dim3(grid), dim3(tcm::kThreads), smem, s, tdz, tw, g),
+    TUNE_CUDA_TRY(pdl::launch_dep(tcm::mlp_bwd_kernel, dim3(grid), dim3(tcm::kThreads), smem, s, tdz, tw, tdzs, g),
                   "surrogate: fused backward launch");
     return TUNE_OK;
 }

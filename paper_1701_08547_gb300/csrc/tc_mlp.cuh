@@ -21,7 +21,11 @@
 // The epilogue stores 2 gelu(z) = z (1 + tanh u), one operation fewer than
 // gelu itself, and the next layer (or the head) takes half its accumulator.
 // In BF16 this is exact: doubling commutes with rounding, so the results are
-// those of storing gelu(z).
+// those of storing gelu(z). The training variant keeps h = gelu(z) itself in
+// act, because act is also the activations H1..H3 the backward pass reads: the
+// MMA issuer copies each layer's act to global memory with bulk tensor stores
+// while that layer's MMAs read it, and waits for the copy to have read act
+// before the epilogue may overwrite it.
 //
 // Precision: layer 1 (K = 64) is BF16 x BF16 in both variants; GELU is
 // evaluated in FP32. The BF16 variant keeps layers 2-4 in BF16; the FP8
@@ -76,7 +80,8 @@ struct Args {
     long long pred_stride;  // member stride of pred (n for inference)
     // training (BF16 only): per layer gelu'(z) of the pre-activations (FP16, in the tiled
     // layout of mlp::gprime_at) and the activations h = gelu(z) (BF16, rows of 256) of every
-    // row < n, [members][act_stride]; null: not kept
+    // row < n, [members][act_stride]; null: not kept. The kernel stores H4 through h_out[3];
+    // H1..H3 go through the tensor map `th` (the same rows, layer = its last coordinate).
     __half* g_out[kLayers];
     __nv_bfloat16* h_out[kLayers];
     long long act_stride;
@@ -101,6 +106,24 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(tc::sa(bar))
         : "memory");
 }
+
+// Bulk tensor store of one box from shared memory into the issuing thread's bulk group (all
+// coordinates non-negative, x a multiple of 16 bytes).
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int x, int y, int z, int w)
+{
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(tc::sa(src)), "r"(x), "r"(y), "r"(z), "r"(w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+
+// The thread's committed bulk stores have read their shared-memory sources.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+
+// The thread's committed bulk stores are complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* b)
 {
@@ -238,6 +261,7 @@ template <bool FP8, bool TRAIN = false>
 __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtensorMap tx,
                                                                 const __grid_constant__ CUtensorMap tw1,
                                                                 const __grid_constant__ CUtensorMap tw,
+                                                                const __grid_constant__ CUtensorMap th,
                                                                 const __grid_constant__ Args g)
 {
     using C = Cfg<FP8>;
@@ -348,6 +372,15 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                             break;
                         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                         const uint8_t* act = smem + s * C::act_bytes;
+                        if (TRAIN && l > 0) {
+                            // act holds H of layer l - 1 (BF16 h, rows of this unit's tile): copied to
+                            // global memory by the tensor-store unit while the MMAs below read it
+                            const long long u = blockIdx.x + jj * gridDim.x;
+                            const int tile = (int)(u / g.members), mem = (int)(u % g.members);
+                            for (int c = 0; c < kWid * 2 / 128; ++c)
+                                tma_store_4d(&th, act + c * kChunkA, c * 16, tile * kRows, mem, l - 1);
+                            bulk_commit();
+                        }
                         const uint32_t d = tmem + (uint32_t)(s * kWid);
                         const bool f8 = FP8 && l > 0;
                         const uint32_t idesc = f8 ? idesc_e4m3(kRows, kWid) : tc::idesc_bf16(kRows, kWid);
@@ -367,12 +400,14 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                             }
                             tc::mma_commit(&w_empty[st]);
                         }
+                        if (TRAIN && l > 0) bulk_wait_read();  // the epilogue rewrites act after acc_full
                         if (!ok) break;
                         tc::mma_commit(&acc_full[s]);
                         if (l == kLayers - 1) tc::mma_commit(&act_free[s]);
                     }
                 }
             }
+            if (TRAIN) bulk_wait_all();
             tc::mma_commit(&drain);  // arrives when every MMA issued above has completed
             tc::mbar_wait(&drain, 0, g.status);
         }
@@ -402,8 +437,9 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                     // member and layer, so the epilogue keeps it in a register)
                     const float sv = (FP8 && l > 0) ? __ldg(g.wscale_half + ((long long)mem * 3 + (l - 1)) * kWid) : 0.0f;
                     const float* w5 = prm + g.off_w5;
-                    // Layers 2-4 read 2 h (see the header), so their accumulator is halved here.
-                    const float acc_mul = l > 0 ? 0.5f : 1.0f;
+                    // Layers 2-4 read 2 h (see the header), so their accumulator is halved here; in
+                    // training act holds h itself (it is also the H the backward pass reads).
+                    const float acc_mul = (l > 0 && !TRAIN) ? 0.5f : 1.0f;
                     const bool f8 = FP8 && l > 0, head = l == kLayers - 1;
                     float yh = 0.0f;
                     for (int n0 = c_beg; n0 < c_end; n0 += 16) {
@@ -432,9 +468,10 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                                 const float2 a = fma2(t, f2(0.5f), f2(0.5f));
                                 const float2 w = mul2(z, fma2(f2(3.0f * mlp::kGeluK * mlp::kGeluC), zz, f2(mlp::kGeluK)));
                                 const float2 d = fma2(mul2(w, fma2(t, f2(-1.0f), f2(1.0f))), a, a);
-                                const float2 h2 = fma2(z, t, z);
-                                v[i] = h2.x;
-                                v[i + 1] = h2.y;
+                                // h itself (2 h halved, exact): act, H and the head all take h in training
+                                const float2 hh = mul2(fma2(z, t, z), f2(0.5f));
+                                v[i] = hh.x;
+                                v[i + 1] = hh.y;
                                 const __half2 d2 = __floats2half2_rn(d.x, d.y);
                                 gd[i / 2] = *reinterpret_cast<const uint32_t*>(&d2);
                             }
@@ -461,22 +498,19 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                             st_shared_v4(act + (n0 >> 7) * kChunkA + swz(r, (n0 & 127) >> 4), w[0], w[1], w[2], w[3]);
                             continue;
                         }
-                        if (TRAIN && !FP8 && g.h_out[l]) {
-                            // training: h = bf16(gelu(z)) = bf16(2 gelu(z)) / 2 exactly
+                        if (TRAIN && head && g.h_out[l]) {
+                            // H4 has no act copy: stored from here (H1..H3 leave from act, see the MMA issuer)
                             uint32_t w[8];
 #pragma unroll
-                            for (int t = 0; t < 8; ++t) {
-                                const float2 hh = mul2(make_float2(v[2 * t], v[2 * t + 1]), f2(0.5f));
-                                w[t] = pack_bf16(hh.x, hh.y);
-                            }
+                            for (int t = 0; t < 8; ++t) w[t] = pack_bf16(v[2 * t], v[2 * t + 1]);
                             st_global_v8(g.h_out[l] + arow, w);
                         }
                         if (head) {
-                            // head on 2 h4; the sum is halved with b5 added below
+                            // head on 2 h4 (h4 in training); the sum is halved with b5 added below
 #pragma unroll
                             for (int i = 0; i < 16; ++i) yh = fmaf(ww[i], v[i], yh);
                         } else {
-                            // BF16(2 h): 16 columns = two 16-byte units of chunk n0/64
+                            // BF16(2 h) (BF16(h) in training): 16 columns = two 16-byte units of chunk n0/64
                             uint8_t* base = act + (n0 >> 6) * kChunkA;
                             const int j0 = (n0 & 63) >> 3;
 #pragma unroll
@@ -502,7 +536,8 @@ __global__ void __maxnreg__(96) mlp_infer_kernel(const __grid_constant__ CUtenso
                         if (!(ok = wait_bar(&head_bar[s], (uint32_t)(k & 1), g.status, abort_v))) break;
                         const int row = tile * kRows + r;
                         const float sum = ((yh + head_part[s][0][r]) + head_part[s][1][r]) + head_part[s][2][r];
-                        if (row < g.n) g.pred[(long long)mem * g.pred_stride + row] = fmaf(sum, 0.5f, prm[g.off_b5]);
+                        if (row < g.n)
+                            g.pred[(long long)mem * g.pred_stride + row] = fmaf(sum, TRAIN ? 1.0f : 0.5f, prm[g.off_b5]);
                     }
                 }
             }

@@ -3,7 +3,10 @@
 // and 2 of a member without re-reading its own outputs from global memory:
 //   dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1}),   l = 4, 3, 2,
 // every dZ rounded to BF16 (the operand precision of the next product) and stored
-// for the weight gradients. Work unit = (tile of 128 rows, member); stage j of a unit
+// for the weight gradients: dZ3 and dZ2 leave from the chain's activation buffer,
+// where they are the next product's A operand, with bulk tensor stores the MMA
+// issuer starts before that product (and waits to have read before the epilogue
+// may overwrite the buffer); dZ1 is stored by the epilogue threads. Work unit = (tile of 128 rows, member); stage j of a unit
 // is the product with W_{4-j} followed by the epilogue that multiplies in gelu'(Z_{3-j})
 // (FP16, kept by the training forward pass) and writes dZ_{3-j}.
 //
@@ -42,6 +45,7 @@ struct BwdArgs {
     long long units;                  // rows / 128 * members (rows a multiple of 128: every unit's rows exist)
     const __half* g[kBwdStages];      // stage j: gelu'(Z_{3-j}), [members][act_stride], tiled (mlp::gprime_at)
     __nv_bfloat16* dz[kBwdStages];    // stage j: dZ_{3-j}, same layout
+    int dz_coord[kBwdStages];         // stage j: the layer coordinate of dz[j] in the map tdzs
     long long act_stride;             // member stride of z and dz (elements); rows of 256
     int* status;
 };
@@ -50,9 +54,11 @@ struct BwdArgs {
 // grid: min(SMs, units) persistent CTAs; CTA b runs units b, b + gridDim.x, ...; its
 // j-th unit goes to chain j % 2. Unit u = (tile u / members, member u % members).
 // tdz: dZ4 as 8-byte elements {64, rows, members}, box {16, 128, 1};
-// tw: W2..W4 as 8-byte elements {64 (inputs), 256 (outputs), 3, members}, box {16, 64, 1, 1}.
+// tw: W2..W4 as 8-byte elements {64 (inputs), 256 (outputs), 3, members}, box {16, 64, 1, 1};
+// tdzs: the dZ buffers as 8-byte elements {64, rows, members, layers}, box {16, 128, 1, 1}.
 __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorMap tdz,
                                                const __grid_constant__ CUtensorMap tw,
+                                               const __grid_constant__ CUtensorMap tdzs,
                                                const __grid_constant__ BwdArgs g)
 {
     using C = Cfg<false>;
@@ -172,6 +178,15 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
                             break;
                         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                         const uint8_t* act = smem + s * C::act_bytes;
+                        if (l > 0) {
+                            // act holds the previous stage's dZ (this unit's rows): copied to global
+                            // memory by the tensor-store unit while the MMAs below read it
+                            const long long u = blockIdx.x + jj * gridDim.x;
+                            const int tile = (int)(u / g.members), mem = (int)(u % g.members);
+                            for (int c = 0; c < kChunks; ++c)
+                                tma_store_4d(&tdzs, act + c * kChunkA, c * 16, tile * kRows, mem, g.dz_coord[l - 1]);
+                            bulk_commit();
+                        }
                         const uint32_t d = tmem + (uint32_t)(s * kWid);
                         for (int c = 0; c < kChunks; ++c, ++seq) {
                             const int st = (int)(seq % C::stages);
@@ -186,12 +201,14 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
                             }
                             tc::mma_commit(&w_empty[st]);
                         }
+                        if (l > 0) bulk_wait_read();  // the epilogue rewrites act after acc_full
                         if (!ok) break;
                         tc::mma_commit(&acc_full[s]);
                         if (l == kBwdStages - 1) tc::mma_commit(&act_free[s]);
                     }
                 }
             }
+            bulk_wait_all();
             tc::mma_commit(&drain);
             tc::mbar_wait(&drain, 0, g.status);
         }
@@ -237,8 +254,9 @@ __global__ void __maxnreg__(96) mlp_bwd_kernel(const __grid_constant__ CUtensorM
                             const float2 d = __half22float2(*reinterpret_cast<const __half2*>(&gw[b][i]));
                             w[i] = pack_bf16(v[2 * i] * d.x, v[2 * i + 1] * d.y);
                         }
-                        st_global_v8(dzr + n0, w);
-                        if (!last) {
+                        if (last) {
+                            st_global_v8(dzr + n0, w);
+                        } else {
                             // 16 columns = two 16-byte units of K chunk n0 / 64
                             uint8_t* base = act + (n0 >> 6) * kChunkA;
                             const int j0 = (n0 & 63) >> 3;
