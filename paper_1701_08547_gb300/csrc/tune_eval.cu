@@ -14,9 +14,10 @@
 //    two table lookups and a min (grid size does not enter Eqs. 1-5); every
 //    grid size G of a triple costs X(T,U,C) * ipar(B*, G), and since a product
 //    by X > 0 is monotone under round-to-nearest the triple's cheapest point
-//    is exactly X * min_G ipar(B*, G): one FP32 multiply per triple. The k-th
-//    smallest triple minimum bounds the kernel's k-th best cost (tau0); each
-//    triple's minimum is kept in shared memory;
+//    is exactly X * min_G ipar(B*, G): one FP32 multiply per triple. A value
+//    that k distinct triple minima do not exceed (tau0, from each lane's two
+//    smallest (T, U)-pair minima counted with their multiplicities) bounds the
+//    kernel's k-th best cost; each triple's minimum is kept in shared memory;
 //  * main pass: lanes scan the minima; only triples that can still beat the
 //    bound are re-evaluated, and the warp merges their grid sizes in
 //    increasing (cost, index) order into a warp-wide exact top-k list (lane j
@@ -349,7 +350,6 @@ __device__ __forceinline__ bool key_less(float c, int i, float c2, int i2)
     return c < c2 || (c == c2 && i < i2);
 }
 
-constexpr int kListDepth = 2;  // smallest triple minima each lane keeps for the bound tau0 (2 or 4)
 
 template <int N>
 struct IntC {
@@ -569,6 +569,14 @@ __global__ void __maxnreg__(64)
                 auto advance = [&]() {
                     hc = kInf;
                     hi = 0x7fffffff;
+                    if (g_dense) {  // every axis grid size present: rank = position
+                        if (r < x.n_g) {
+                            const int g = ct.perm[B - 1][r++];
+                            hc = __fmul_rn(X, ct.ipar[B - 1][g]);
+                            hi = base + g * nUC;
+                        }
+                        return;
+                    }
                     while (r < x.n_g) {
                         const int g = ct.perm[B - 1][r++];
                         if ((gm >> g) & 1u) {
@@ -595,11 +603,15 @@ __global__ void __maxnreg__(64)
                 // ---- pre-pass over (T, U) pairs, lane = pair rank mod 32, carveouts inner.
                 // Every grid size G of a triple costs X(T,U,C) * ipar(B*, G); a product by
                 // X > 0 is monotone under round-to-nearest, so the triple's cheapest point
-                // is exactly X * min_G ipar(B*, G). Each lane keeps its kListDepth smallest
-                // triple minima; the k-th smallest over the warp bounds the kernel's k-th best
-                // cost (k distinct triples each own a point <= tau0). Each minimum is also
-                // stored at its triple rank (t rank * nUC + u rank * nC + c rank), so that
-                // the carveouts of one (T, U) pair sit in neighbouring lanes of the scan.
+                // is exactly X * min_G ipar(B*, G). Each lane keeps the two smallest pair minima
+                // (the smallest triple minimum over a (T, U) pair's carveouts) of its pairs, each
+                // with its multiplicity (the pair's carveouts whose minimum equals it: the
+                // carveouts of a pair often share B* and so their cost); tau0 is the smallest
+                // value at which these entries, in increasing order, count k triples, and so
+                // bounds the kernel's k-th best cost (k distinct triples each own a point
+                // <= tau0). Each minimum is also stored at its triple rank (t rank * nUC +
+                // u rank * nC + c rank), so that the carveouts of one (T, U) pair sit in
+                // neighbouring lanes of the scan.
                 const int nP = nT * nU;
                 const int n_prow = (nP + 31) >> 5;
                 const int n_blk = (nP * nC + 127) >> 7;  // blocks of 128 triples for the scan
@@ -609,7 +621,8 @@ __global__ void __maxnreg__(64)
                     *reinterpret_cast<float4*>(&w.key[((n_blk - 1) << 7) + 4 * lane]) = make_float4(nan, nan, nan, nan);
                 }
                 __syncwarp();
-                float m0 = kInf, m1 = kInf, m2 = kInf, m3 = kInf;
+                float m0 = kInf, m1 = kInf;  // this lane's two smallest pair minima, ascending
+                int c0 = 0, c1 = 0;          // their multiplicities
                 // one body per carveout count, so that G_S stays in registers and a pair's
                 // minima are stored with one vector store
                 auto pairs = [&](auto nc_tag) {
@@ -633,27 +646,27 @@ __global__ void __maxnreg__(64)
                         const int gwr = block_limit(t_r, ti, u_r);
                         const float cnm = w.cnm[u_r], cmv = w.cm[u_r];
                         float key[NC];
+                        float pm = kInf;
 #pragma unroll
                         for (int c = 0; c < NC; ++c) {
                             // branch-free: a triple without a valid configuration (B* = 0) reads
                             // hide[0] and iparmin[0] = NaN, so it is keyed NaN (never a
-                            // candidate) and ranked +inf (no effect on the bound); W* = B* W_B
-                            // <= W_mp <= kMaxW for a valid triple. X is finite (counts <= 2^40).
+                            // candidate, not counted in the bound); W* = B* W_B <= W_mp <= kMaxW
+                            // for a valid triple. X is finite (counts <= 2^40).
                             const int B = min(gwr, gs[c]);
                             const float X = __fmul_rn(__fmaf_rn(cmv, ct.hide[B * wb], cnm), ln);
                             key[c] = __fmul_rn(X, w.iparmin[B]);
-                            float m = fminf(key[c], kInf);
-                            {
-                                float lo;
-                                lo = fminf(m0, m); m = fmaxf(m0, m); m0 = lo;
-                                if (kListDepth == 4) {
-                                    lo = fminf(m1, m); m = fmaxf(m1, m); m1 = lo;
-                                    lo = fminf(m2, m); m = fmaxf(m2, m); m2 = lo;
-                                    m3 = fminf(m3, m);
-                                } else {
-                                    m1 = fminf(m1, m);
-                                }
-                            }
+                            pm = fminf(pm, key[c]);
+                        }
+                        int mult = 0;
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) mult += key[c] == pm ? 1 : 0;
+                        {
+                            const bool lt0 = pm < m0, lt1 = pm < m1;
+                            m1 = lt0 ? m0 : (lt1 ? pm : m1);
+                            c1 = lt0 ? c0 : (lt1 ? mult : c1);
+                            m0 = lt0 ? pm : m0;
+                            c0 = lt0 ? mult : c0;
                         }
                         float* krow = &w.key[pr * NC];
                         if constexpr (NC == 4) {
@@ -673,16 +686,20 @@ __global__ void __maxnreg__(64)
                     default: pairs(IntC<4>{}); break;
                 }
                 __syncwarp();
-                for (int r = 0; r < k; ++r) {
+                // entries in increasing order until they count k triples (at most 64 rounds; a
+                // finite entry counts at least one triple; +inf: fewer than k valid triples)
+                for (int need = k;;) {
                     const unsigned mb = __reduce_min_sync(kFull, __float_as_uint(m0));
                     tau0 = __uint_as_float(mb);
                     if (mb >= 0x7f800000u) break;
-                    const unsigned who = __ballot_sync(kFull, __float_as_uint(m0) == mb);
-                    const bool me = lane == __ffs(who) - 1;  // the lane whose smallest was taken
+                    const int src = __ffs(__ballot_sync(kFull, __float_as_uint(m0) == mb)) - 1;
+                    need -= __shfl_sync(kFull, c0, src);
+                    if (need <= 0) break;
+                    const bool me = lane == src;  // the lane whose smallest was taken
                     m0 = me ? m1 : m0;
-                    m1 = me ? m2 : m1;
-                    m2 = me ? m3 : m2;
-                    m3 = me ? kInf : m3;
+                    c0 = me ? c1 : c0;
+                    m1 = me ? kInf : m1;
+                    c1 = me ? 0 : c1;
                 }
 
                 // ---- candidates: the triples whose minimum does not exceed tau0 (every point
