@@ -179,11 +179,15 @@ __device__ __forceinline__ void st_shared_v4(uint8_t* p, uint32_t a, uint32_t b,
                  : "memory");
 }
 
+// 16 parameters (biases or head weights, read again by every unit): kept in L1 with priority.
 __device__ __forceinline__ void ld16(const float* p, float (&x)[16])
 {
 #pragma unroll
     for (int i = 0; i < 16; i += 4) {
-        const float4 q = __ldg(reinterpret_cast<const float4*>(p + i));
+        float4 q;
+        asm volatile("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                     : "=f"(q.x), "=f"(q.y), "=f"(q.z), "=f"(q.w)
+                     : "l"(p + i));
         x[i] = q.x;
         x[i + 1] = q.y;
         x[i + 2] = q.z;
@@ -215,10 +219,11 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b)
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
-// 256-bit global store of eight 32-bit words (address 32-byte aligned).
+// 256-bit global store of eight 32-bit words (address 32-byte aligned), not kept in L1 (what the
+// epilogues store is read by later launches only).
 __device__ __forceinline__ void st_global_v8(void* p, const uint32_t (&w)[8])
 {
-    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"l"(p), "r"(w[0]), "r"(w[1]),
+    asm volatile("st.global.L1::no_allocate.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"l"(p), "r"(w[0]), "r"(w[1]),
                  "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
                  : "memory");
 }
