@@ -59,7 +59,7 @@ struct tune_surrogate {
     __half* G[NL] = {};                 // gelu' of each layer's pre-activations, FP16 [members][batch x WID], tiled (mlp::gprime_at)
     __nv_bfloat16* H[NL] = {};          // [members][batch x WID]
     __nv_bfloat16* dZ[NL] = {};         // [members][batch x WID]: dZ of layer l (fused chain) or ping-pong
-    float *y = nullptr, *dy = nullptr, *lbl = nullptr, *loss = nullptr;  // [members][batch] / [members]
+    float *y = nullptr, *lbl = nullptr, *loss = nullptr;  // [members][batch], [batch], [members]
     float* part = nullptr;              // split-K partials: part_slices x [WID x WID]
     int part_slices = 0;                // at least members x KSPLIT and the SM count
     void* block = nullptr;              // the one device allocation
@@ -123,67 +123,31 @@ __global__ void head_fwd(const __nv_bfloat16* __restrict__ H4, const float* __re
     if (lane == 0) y[(long long)mem * batch + row] = s + master[mem * P + OFF_B5];
 }
 
-// dy = 2 (y - t) / n, one row per thread; lpart[mem][block] = the block's sum of (y - t)^2
-__global__ void loss_grad(const float* __restrict__ y, const float* __restrict__ t, float* dy, float* lpart, int n,
-                          int batch)
-{
-    pdl::grid_dep_enter();  // a step of the training chain: wait for the launch before it
-    const int mem = blockIdx.y;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    __shared__ float red[8];
-    float s = 0.0f;
-    if (i < batch) {
-        float g = 0.0f;
-        if (i < n) {
-            const float e = y[(long long)mem * batch + i] - t[i];
-            s = e * e;
-            g = 2.0f * e / (float)n;
-        }
-        dy[(long long)mem * batch + i] = g;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float b = 0.0f;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) b += red[q];
-        lpart[mem * gridDim.x + blockIdx.x] = b;
-    }
-}
-
-// loss[mem] = (sum of the blocks' partial sums, in block order) / n
-__global__ void loss_reduce(const float* __restrict__ lpart, float* loss, int blocks, int n)
-{
-    pdl::grid_dep_enter();  // a step of the training chain: wait for the launch before it
-    const int mem = blockIdx.x;
-    if (threadIdx.x != 0 || !loss) return;
-    float s = 0.0f;
-    for (int b = 0; b < blocks; ++b) s += lpart[mem * blocks + b];
-    loss[mem] = s / (float)n;
-}
-
 // Column sums over rows in two stages (deterministic): stage 1 sums slices of
 // kRowSlice rows into part[mem][slice][WID + 1]; stage 2 adds the slices.
 constexpr int kRowSlice = 64;
 constexpr int kRedWarps = 32;  // warps per block of the slice sums
 
-// Head backward in one pass over a slice of srows rows (block = (slice, member), 256 threads:
-// eight row groups of 32 threads, each thread eight columns with 16-byte accesses):
+// Loss gradient and head backward in one pass over a slice of srows rows (block = (slice,
+// member), 256 threads: eight row groups of 32 threads, each thread eight columns with 16-byte
+// accesses): dy[i] = 2 (y[i] - lbl[i]) / n for the n labelled rows (0 past them),
 // dZ4[i][j] = bf16(dy[i] * w5[j] * G4[i][j]) with G4 = gelu'(Z4), and part[.][.][j] = sum over
-// the slice of dy[i] H4[i][j] (j < 256) and of dy[i] (j = 256). Row group q takes rows
-// i0 + q, i0 + q + 8, ...; its sums are added to the other groups' in group order.
+// the slice of dy[i] H4[i][j] (j < 256), of dy[i] (j = 256) and of (y[i] - lbl[i])^2 (j = 257;
+// rows of kHeadStride floats). Row group q takes rows i0 + q, i0 + q + 8, ...; its sums are
+// added to the other groups' in group order.
 constexpr int kHeadGroups = 8;
-__global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ dy, const float* __restrict__ master,
-                                                const __half* __restrict__ G4, const __nv_bfloat16* __restrict__ H4,
-                                                __nv_bfloat16* dZ, float* part, int rows, int batch, int slices,
-                                                int srows)
+constexpr int kHeadStride = WID + 2;
+__global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ y, const float* __restrict__ lbl, int n,
+                                                const float* __restrict__ master, const __half* __restrict__ G4,
+                                                const __nv_bfloat16* __restrict__ H4, __nv_bfloat16* dZ, float* part,
+                                                int rows, int batch, int slices, int srows)
 {
     pdl::grid_dep_enter();  // a step of the training chain: wait for the launch before it
-    __shared__ float red[kHeadGroups][WID + 1];
+    __shared__ float red[kHeadGroups][kHeadStride];
     const int mem = blockIdx.y, sl = blockIdx.x;
     const int q = threadIdx.x >> 5, j = 8 * (threadIdx.x & 31);
-    const float* d = dy + (long long)mem * batch;
+    const float* yv = y + (long long)mem * batch;
+    const float n_f = (float)n;
     const long long base = (long long)mem * batch * WID + j;
     float w[8];
     {
@@ -191,11 +155,16 @@ __global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ dy, co
         const float4 b = *reinterpret_cast<const float4*>(master + mem * P + OFF_W5 + j + 4);
         w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
     }
-    float sh[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, sb = 0.0f;
+    float sh[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, sb = 0.0f, se = 0.0f;
     const int i0 = sl * srows, i1 = min(rows, i0 + srows);
 #pragma unroll 2
     for (int i = i0 + q; i < i1; i += kHeadGroups) {
-        const float di = d[i];
+        float di = 0.0f;
+        if (i < n) {
+            const float e = yv[i] - lbl[i];
+            di = 2.0f * e / n_f;
+            se += e * e;
+        }
         const long long o = base + (long long)i * WID;
         const uint4 gv = __ldg(reinterpret_cast<const uint4*>(G4 + (long long)mem * batch * WID + mlp::gprime_at(i, j)));
         const uint4 hv = __ldg(reinterpret_cast<const uint4*>(H4 + o));
@@ -214,11 +183,14 @@ __global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ dy, co
         sb += di;
     }
 #pragma unroll
-    for (int t = 0; t < 8; ++t) red[q][j + t] = sh[t];
-    if (j == 0) red[q][WID] = sb;
+    for (int c = 0; c < 8; ++c) red[q][j + c] = sh[c];
+    if (j == 0) {
+        red[q][WID] = sb;
+        red[q][WID + 1] = se;
+    }
     __syncthreads();
-    float* o = part + ((long long)mem * slices + sl) * (WID + 1);
-    for (int c = threadIdx.x; c <= WID; c += blockDim.x) {
+    float* o = part + ((long long)mem * slices + sl) * kHeadStride;
+    for (int c = threadIdx.x; c < kHeadStride; c += blockDim.x) {
         float v = red[0][c];
 #pragma unroll
         for (int g = 1; g < kHeadGroups; ++g) v += red[g][c];
@@ -242,10 +214,13 @@ __global__ void bias_partial(const __nv_bfloat16* __restrict__ dZ, float* part, 
     part[((long long)mem * slices + sl) * (WID + 1) + j] = (s[0] + s[1]) + (s[2] + s[3]);
 }
 
-// grad[mem * P + off + j] = sum over slices of part[mem][slice][j], j < cols. Block =
-// 32 columns x 8 warps; warp w adds slices w, w + 8, ... in order, then the eight
-// partial sums are added in warp order (deterministic).
-__global__ void slices_reduce(const float* __restrict__ part, float* grad, long long off, int cols, int slices)
+// grad[mem * P + off + j] = sum over slices of part[mem][slice][j], j < cols (slice rows of
+// `stride` floats); with `loss`, column cols is the slices' sum of squared errors and
+// loss[mem] = that sum / n. Block = 32 columns x kRedWarps warps; warp w adds slices w,
+// w + kRedWarps, ... in order, then the warps' partial sums are added in warp order
+// (deterministic).
+__global__ void slices_reduce(const float* __restrict__ part, float* grad, long long off, int cols, int slices,
+                              int stride, float* loss, int n)
 {
     pdl::grid_dep_enter();  // a step of the training chain: wait for the launch before it
     // block = 32 columns x kRedWarps warps; warp w adds slices w, w + kRedWarps, ..., then
@@ -253,16 +228,20 @@ __global__ void slices_reduce(const float* __restrict__ part, float* grad, long 
     const int mem = blockIdx.y, w = threadIdx.x >> 5;
     const int j = blockIdx.x * 32 + (threadIdx.x & 31);
     __shared__ float red[kRedWarps][32];
+    const int ncol = cols + (loss ? 1 : 0);
     float s = 0.0f;
-    if (j < cols)
-        for (int q = w; q < slices; q += kRedWarps) s += part[((long long)mem * slices + q) * (WID + 1) + j];
+    if (j < ncol)
+        for (int q = w; q < slices; q += kRedWarps) s += part[((long long)mem * slices + q) * stride + j];
     red[w][threadIdx.x & 31] = s;
     __syncthreads();
-    if (w == 0 && j < cols) {
+    if (w == 0 && j < ncol) {
         float t = red[0][threadIdx.x];
 #pragma unroll
         for (int q = 1; q < kRedWarps; ++q) t += red[q][threadIdx.x];
-        grad[mem * P + off + j] = t;
+        if (j < cols)
+            grad[mem * P + off + j] = t;
+        else
+            loss[mem] = t / (float)n;
     }
 }
 
@@ -839,30 +818,24 @@ int wgrad_mma(tune_surrogate* h, int l, int n_pad, const __nv_bfloat16* dz, cuda
 int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
 {
     const int B = h->batch;
-    const int lblocks = (B + 255) / 256;
-    // the loss, the head's backward and its slice sums: steps of the training chain (pdl.cuh)
-    TUNE_CUDA_TRY(pdl::launch_dep(loss_grad, dim3(lblocks, h->members), dim3(256), 0, s, h->y, h->lbl, h->dy, h->part,
-                                  n, B),
-                  "surrogate: loss launch");
-    TUNE_CUDA_TRY(pdl::launch_dep(loss_reduce, dim3(h->members), dim3(32), 0, s, h->part, h->loss, lblocks, n),
-                  "surrogate: loss launch");
     const int slices = (n_pad + kRowSlice - 1) / kRowSlice;
     // dZ of layer l: a buffer per layer when the input-gradient chain runs fused, else two
     // buffers in turn (each is consumed by its weight gradient before it is overwritten)
     const bool fused = h->use_tc && h->bwd_mode == 1;
     __nv_bfloat16* dzl[NL];
     for (int l = 0; l < NL; ++l) dzl[l] = h->dZ[fused ? l : (l & 1)];
-    // the head's weight and bias gradients (slices, then their sum) and dZ4 in one pass
+    // the loss gradient, the head's weight and bias gradients (slices, then their sum), the
+    // loss and dZ4 in one pass and its reduction: steps of the training chain (pdl.cuh)
     // (64-row slices, longer where their partials would not fit the partial buffer)
     int hrows = 64;
-    while ((long long)h->members * ((n_pad + hrows - 1) / hrows) * (WID + 1) > (long long)h->part_slices * WID * WID)
+    while ((long long)h->members * ((n_pad + hrows - 1) / hrows) * kHeadStride > (long long)h->part_slices * WID * WID)
         hrows *= 2;
     const int hslices = (n_pad + hrows - 1) / hrows;
-    TUNE_CUDA_TRY(pdl::launch_dep(head_bwd, dim3(hslices, h->members), dim3(32 * kHeadGroups), 0, s, h->dy, h->master,
-                                  h->G[NL - 1], h->H[NL - 1], dzl[NL - 1], h->part, n_pad, B, hslices, hrows),
+    TUNE_CUDA_TRY(pdl::launch_dep(head_bwd, dim3(hslices, h->members), dim3(32 * kHeadGroups), 0, s, h->y, h->lbl, n,
+                                  h->master, h->G[NL - 1], h->H[NL - 1], dzl[NL - 1], h->part, n_pad, B, hslices, hrows),
                   "surrogate: head backward launch");
-    TUNE_CUDA_TRY(pdl::launch_dep(slices_reduce, dim3((WID + 1 + 31) / 32, h->members), dim3(32 * kRedWarps), 0, s,
-                                  h->part, h->grad, OFF_W5, WID + 1, hslices),
+    TUNE_CUDA_TRY(pdl::launch_dep(slices_reduce, dim3((kHeadStride + 31) / 32, h->members), dim3(32 * kRedWarps), 0,
+                                  s, h->part, h->grad, OFF_W5, WID + 1, hslices, kHeadStride, h->loss, n),
                   "surrogate: head backward launch");
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: head backward launch");
     if (fused) {  // input gradients dZ3..dZ1, then every layer's weight and bias gradients
@@ -878,7 +851,8 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
         int rc = wgrad_mma(h, l, n_pad, dz, s);
         if (rc) return rc;
         bias_partial<<<dim3(slices, h->members), WID, 0, s>>>(dz, h->part, n_pad, B, slices);
-        slices_reduce<<<dim3(WID / 32, h->members), 32 * kRedWarps, 0, s>>>(h->part, h->grad, OFF_B(l), WID, slices);
+        slices_reduce<<<dim3(WID / 32, h->members), 32 * kRedWarps, 0, s>>>(h->part, h->grad, OFF_B(l), WID, slices,
+                                                                          WID + 1, nullptr, 0);
         TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: reduce launch");
         if (l == 0) continue;
         // input gradient of layer l, times gelu' of layer l-1: dZ_{l-1} = (dZ_l W_l) * gelu'(Z_{l-1})
@@ -995,7 +969,6 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     for (int l = 0; l < NL; ++l) add(M * B * WID * 2);
     for (int l = 0; l < NL; ++l) add(M * B * WID * 2);
     add(M * B * 4);
-    add(M * B * 4);
     add(B * 4);
     add(M * 4);
     const size_t part_slices = std::max<size_t>(M * KSPLIT, (size_t)tune::device_sm_count());
@@ -1021,7 +994,6 @@ int surrogate_create(tune_surrogate** out, const tune_surrogate_cfg* cfg)
     for (int l = 0; l < NL; ++l) h->H[l] = carve<__nv_bfloat16>(p, M * B * WID);
     for (int l = 0; l < NL; ++l) h->dZ[l] = carve<__nv_bfloat16>(p, M * B * WID);
     h->y = carve<float>(p, M * B);
-    h->dy = carve<float>(p, M * B);
     h->lbl = carve<float>(p, B);
     h->loss = carve<float>(p, M);
     h->part = carve<float>(p, part_slices * WID * WID);
