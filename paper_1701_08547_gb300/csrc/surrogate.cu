@@ -60,6 +60,12 @@ struct tune_surrogate {
     __nv_bfloat16* H[NL] = {};          // [members][batch x WID]
     __nv_bfloat16* dZ[NL] = {};         // [members][batch x WID]: dZ of layer l (fused chain) or ping-pong
     float *y = nullptr, *lbl = nullptr, *loss = nullptr;  // [members][batch], [batch], [members]
+    // the training batch being processed: its layer-1 input rows (xb_rows of them; rows past it
+    // read as zeros through the tensor maps) and labels: xin / lbl after a gather, or the
+    // caller's own arrays (fused tcgen05 path, no permutation)
+    const __nv_bfloat16* xb = nullptr;
+    const float* lb = nullptr;
+    int xb_rows = 0;
     float* part = nullptr;              // split-K partials: part_slices x [WID x WID]
     int part_slices = 0;                // at least members x KSPLIT and the SM count
     void* block = nullptr;              // the one device allocation
@@ -592,16 +598,16 @@ int fused_forward(tune_surrogate* h, const __nv_bfloat16* feats, int64_t n, floa
     return fp8 ? launch_fused<true>(tx, tw1, tw, tx, g, grid, s) : launch_fused<false>(tx, tw1, tw, tx, g, grid, s);
 }
 
-// Training forward of rows [0, n_pad) of h->xin through the fused kernel (BF16), keeping
-// every layer's gelu'(Z) (FP16) and activations H for the backward pass and the head
-// outputs in h->y.
+// Training forward of rows [0, n_pad) of the current batch (h->xb) through the fused kernel
+// (BF16), keeping every layer's gelu'(Z) (FP16) and activations H for the backward pass and the
+// head outputs in h->y.
 int fused_train_forward(tune_surrogate* h, int n_pad, cudaStream_t s)
 {
     CUtensorMap tx, tw1, tw;
     const auto u64 = CU_TENSOR_MAP_DATA_TYPE_UINT64;
-    const cuuint64_t xd[2] = {IN * 2 / 8, (cuuint64_t)n_pad}, xs[1] = {IN * 2};
+    const cuuint64_t xd[2] = {IN * 2 / 8, (cuuint64_t)h->xb_rows}, xs[1] = {IN * 2};
     const cuuint32_t xb[2] = {16, tcm::kRows};
-    int rc = make_map_nd(&tx, u64, 2, h->xin, xd, xs, xb);
+    int rc = make_map_nd(&tx, u64, 2, h->xb, xd, xs, xb);
     if (rc) return rc;
     const cuuint64_t d1[3] = {IN * 2 / 8, WID, (cuuint64_t)h->members}, s1[2] = {IN * 2, PB * 2};
     const cuuint32_t b1[3] = {16, WID, 1};
@@ -717,9 +723,9 @@ int wgrad_tc(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaStream_
         int rc = make_map_nd(&maps.ta[j], u64, 3, dz[l], da, sa, box);
         if (rc) return rc;
         if (l == 0) {
-            const cuuint64_t db[3] = {IN * 2 / 8, (cuuint64_t)n_pad, 1};
-            const cuuint64_t sb[2] = {IN * 2, (cuuint64_t)n_pad * IN * 2};
-            rc = make_map_nd(&maps.tb[j], u64, 3, h->xin, db, sb, box);
+            const cuuint64_t db[3] = {IN * 2 / 8, (cuuint64_t)h->xb_rows, 1};
+            const cuuint64_t sb[2] = {IN * 2, (cuuint64_t)h->xb_rows * IN * 2};
+            rc = make_map_nd(&maps.tb[j], u64, 3, h->xb, db, sb, box);
         } else {
             rc = make_map_nd(&maps.tb[j], u64, 3, h->H[l - 1], da, sa, box);
         }
@@ -742,16 +748,18 @@ int wgrad_tc(tune_surrogate* h, int n_pad, __nv_bfloat16* const* dz, cudaStream_
     return TUNE_OK;
 }
 
-// Forward through all members for rows [0, n_pad) of h->xin (n_pad a multiple of 128).
-// x_in: layer-1 input rows (h->xin, or the caller's features on the tcgen05 path);
+// Forward through all members for rows [0, n_pad) (n_pad a multiple of 128).
+// x_in: layer-1 input rows (null: the current training batch; else the caller's features on the
+// tcgen05 path);
 // n_valid rows of it exist; store_z keeps gelu' of the pre-activations for a backward pass.
 int forward(tune_surrogate* h, int n_pad, cudaStream_t s, const __nv_bfloat16* x_in = nullptr, int n_valid = -1,
             bool store_z = true)
 {
+    // training with tcgen05 and the fused forward selected: one launch for all layers and the
+    // head over the current batch (h->xb)
+    if (store_z && h->use_tc && h->fwd_mode == 1 && !x_in) return fused_train_forward(h, n_pad, s);
     if (!x_in) x_in = h->xin;
     if (n_valid < 0) n_valid = n_pad;
-    // training with tcgen05 and the fused forward selected: one launch for all layers and the head
-    if (store_z && h->use_tc && h->fwd_mode == 1 && x_in == h->xin) return fused_train_forward(h, n_pad, s);
     for (int l = 0; l < NL; ++l) {
         if (h->use_tc) {
             int rc = tc_layer(h, l, n_pad, s, x_in, n_valid, store_z);
@@ -783,7 +791,7 @@ int forward(tune_surrogate* h, int n_pad, cudaStream_t s, const __nv_bfloat16* x
     return TUNE_OK;
 }
 
-// Backward for the batch in h->xin / h->lbl (n valid rows, n_pad rows computed); grads into h->grad.
+// Backward for the current batch (h->xb / h->lb; n valid rows, n_pad rows computed); grads into h->grad.
 // Weight gradient of layer l as a split-K mma.sync GEMM (mlp_gemm.cuh) and its reduction into grad.
 int wgrad_mma(tune_surrogate* h, int l, int n_pad, const __nv_bfloat16* dz, cudaStream_t s)
 {
@@ -831,7 +839,7 @@ int backward(tune_surrogate* h, int n, int n_pad, cudaStream_t s)
     while ((long long)h->members * ((n_pad + hrows - 1) / hrows) * kHeadStride > (long long)h->part_slices * WID * WID)
         hrows *= 2;
     const int hslices = (n_pad + hrows - 1) / hrows;
-    TUNE_CUDA_TRY(pdl::launch_dep(head_bwd, dim3(hslices, h->members), dim3(32 * kHeadGroups), 0, s, h->y, h->lbl, n,
+    TUNE_CUDA_TRY(pdl::launch_dep(head_bwd, dim3(hslices, h->members), dim3(32 * kHeadGroups), 0, s, h->y, h->lb, n,
                                   h->master, h->G[NL - 1], h->H[NL - 1], dzl[NL - 1], h->part, n_pad, B, hslices, hrows),
                   "surrogate: head backward launch");
     TUNE_CUDA_TRY(pdl::launch_dep(slices_reduce, dim3((kHeadStride + 31) / 32, h->members), dim3(32 * kRedWarps), 0,
@@ -902,7 +910,24 @@ int load_batch(tune_surrogate* h, const __nv_bfloat16* feats, const float* label
                                       h->batch, h->xin, h->lbl),
                       "surrogate: gather launch");
     TUNE_CUDA_TRY(cudaGetLastError(), "surrogate: gather launch");
+    h->xb = h->xin;
+    h->lb = h->lbl;
+    h->xb_rows = h->batch;
     return TUNE_OK;
+}
+
+// The caller's first n rows and labels as the training batch, without a gather: on the fused
+// tcgen05 path, whose reads of the input rows go through tensor maps (rows past n read as
+// zeros) and whose labels are read for the n labelled rows only; the arrays must be 16-byte
+// (rows) and 4-byte (labels) aligned. Returns false where the gather is needed.
+bool use_batch_in_place(tune_surrogate* h, const __nv_bfloat16* feats, const float* labels, int n)
+{
+    if (!(h->use_tc && h->fwd_mode == 1 && h->bwd_mode == 1)) return false;
+    if ((reinterpret_cast<uintptr_t>(feats) & 15) || (reinterpret_cast<uintptr_t>(labels) & 3)) return false;
+    h->xb = feats;
+    h->lb = labels;
+    h->xb_rows = n;
+    return true;
 }
 
 }  // namespace
@@ -1104,7 +1129,8 @@ int surrogate_train_step(tune_surrogate* h, const uint16_t* feats, const float* 
         return tune::fail(TUNE_EINVAL, "surrogate_train_step: need 1 <= n <= batch and non-NULL data");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int nb = (int)n, n_pad = (nb + 127) / 128 * 128;
-    int rc = load_batch(h, reinterpret_cast<const __nv_bfloat16*>(feats), labels, nullptr, nb, s);
+    const auto* f = reinterpret_cast<const __nv_bfloat16*>(feats);
+    int rc = use_batch_in_place(h, f, labels, nb) ? TUNE_OK : load_batch(h, f, labels, nullptr, nb, s);
     if (!rc) rc = forward(h, n_pad, s);
     if (!rc) rc = backward(h, nb, n_pad, s);
     if (!rc && apply_update) rc = adam(h, s);
