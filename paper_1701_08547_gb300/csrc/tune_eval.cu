@@ -778,27 +778,66 @@ __global__ void __maxnreg__(64)
                     if (!relaxed) {
                         // every lane's walk is in (cost, index) order: the r-th extraction is the
                         // r-th best of the batch (points above tau0 cannot be among the top k)
-                        for (int r = 0; r < k; ++r) {
+                        for (int r = 0; r < k;) {
                             const unsigned mc = __reduce_min_sync(kFull, __float_as_uint(hc));
                             const float mcf = __uint_as_float(mc);
                             if (mc >= 0x7f800000u || mcf > tau0) break;
-                            const unsigned mi = __reduce_min_sync(kFull, hc == mcf ? (unsigned)hi : 0xffffffffu);
-                            lc = lane == r ? mcf : lc;
-                            li = lane == r ? (int)mi : li;
-                            const bool win = hc == mcf && hi == (int)mi;
+                            const bool tie = hc == mcf;
                             if (g_dense) {
-                                // straight-line advance of the winning lane (every lane computes; B
-                                // and the position are clamped into range for the others)
+                                // every lane's next head, straight-line (B and the position are
+                                // clamped into range for lanes without one)
                                 const int Bv = max(B, 1) - 1;
                                 const int g = ct.perm[Bv][min(rg, x.n_g - 1)];
-                                const float nh = __fmul_rn(X, ct.ipar[Bv][g]);
                                 const bool more = rg < x.n_g;
-                                hc = win ? (more ? nh : kInf) : hc;
-                                hi = win ? (more ? base + g * nUC : 0x7fffffff) : hi;
+                                const float nc = more ? __fmul_rn(X, ct.ipar[Bv][g]) : kInf;
+                                const int ni = more ? base + g * nUC : 0x7fffffff;
+                                // Heads of the smallest cost whose index is below every equal-cost
+                                // next head are the next points in (cost, index) order, all of them
+                                // (each walk is in that order). Where their indices rise with the
+                                // lane, as they mostly do (candidates are in triple order), the
+                                // first m go to list positions r.. at once through shared memory.
+                                const unsigned bound =
+                                    __reduce_min_sync(kFull, tie && nc == mcf ? (unsigned)ni : 0xffffffffu);
+                                const bool elig = tie && (unsigned)hi < bound;
+                                const unsigned before = __ballot_sync(kFull, elig) & below;
+                                const int hprev = __shfl_sync(kFull, hi, before ? 31 - __clz(before) : lane);
+                                if (__all_sync(kFull, !elig || !before || hprev < hi)) {
+                                    const int m = min(__popc(__ballot_sync(kFull, elig)), k - r);
+                                    const int rank = __popc(before);
+                                    const bool take = elig && rank < m;
+                                    // w.iparmin is free during the selection: [j] cost, [16 + j] index
+                                    if (take) {
+                                        w.iparmin[rank] = hc;
+                                        w.iparmin[16 + rank] = __int_as_float(hi);
+                                    }
+                                    __syncwarp();
+                                    if (lane >= r && lane < r + m) {
+                                        lc = w.iparmin[lane - r];
+                                        li = __float_as_int(w.iparmin[16 + lane - r]);
+                                    }
+                                    __syncwarp();
+                                    hc = take ? nc : hc;
+                                    hi = take ? ni : hi;
+                                    rg += take ? 1 : 0;
+                                    r += m;
+                                    continue;
+                                }
+                                // indices out of lane order: one point, the lowest index
+                                const unsigned mi = __reduce_min_sync(kFull, tie ? (unsigned)hi : 0xffffffffu);
+                                lc = lane == r ? mcf : lc;
+                                li = lane == r ? (int)mi : li;
+                                const bool win = tie && hi == (int)mi;
+                                hc = win ? nc : hc;
+                                hi = win ? ni : hi;
                                 rg += win ? 1 : 0;
-                            } else if (win) {
-                                advance();
+                                ++r;
+                                continue;
                             }
+                            const unsigned mi = __reduce_min_sync(kFull, tie ? (unsigned)hi : 0xffffffffu);
+                            lc = lane == r ? mcf : lc;
+                            li = lane == r ? (int)mi : li;
+                            if (tie && hi == (int)mi) advance();
+                            ++r;
                         }
                         tau_c = __shfl_sync(kFull, lc, k - 1);
                         tau_i = __shfl_sync(kFull, li, k - 1);
